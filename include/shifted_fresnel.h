@@ -1,0 +1,159 @@
+/*
+ * shifted_fresnel.h -- C ABI of the GB300 (sm_103a) Shifted-Fresnel library.
+ *
+ * Shifted-Fresnel diffraction (Shimobaba et al., Section 2.1, Eqs. 1-5)
+ * reconstructs a view u1 of a hologram u0 at distance z with its own output
+ * pitch and lateral offset:
+ *
+ *   u1[n1][m1] = C sum_{n0,m0} u0[n0][m0] exp(i pi ((x1-x0)^2 + (y1-y0)^2) / (lambda z)),
+ *   C = exp(i k z) / (i lambda z),   k = 2 pi / lambda,
+ *   x0 = ox0 + (m0 - floor(nx0/2)) px0,   x1 = ox1 + (m1 - floor(nx1/2)) px1
+ *   (and the same along y).
+ *
+ * The library evaluates it as Eq. 1 does: per axis, the input chirp of
+ * Eq. 3, a zero-padded FFT convolution with the chirp kernel h of Eq. 4, and
+ * the output chirp and constant of Eq. 2; the view intensity is Eq. 5.  The
+ * paper's offsets O are in pixels and its index origin is -N/2; here offsets
+ * are physical lengths (O = o / p) and the origin is floor(N/2).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: SF_OK (0) on success, a negative SF_ERR_* code on failure.
+ *     No exception or C++ object crosses this interface.
+ *   - Arrays are row-major [rows][cols], x (m) fastest.  "complex64" is an
+ *     interleaved pair of float32 (re, im), 8 bytes per element.
+ *   - A plan is bound to the device it was created on.  Calls are ordered on
+ *     the given stream (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream) and return before the GPU work finishes.
+ *   - The caller owns every input and output buffer; the plan owns its
+ *     workspaces, chirp vectors and kernel spectra.
+ */
+#ifndef SHIFTED_FRESNEL_H
+#define SHIFTED_FRESNEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SF_OK 0
+#define SF_ERR_INVALID_ARG (-1)      /* bad pointer, NaN/Inf, z = 0, lambda/pitch <= 0, size <= 0 ... */
+#define SF_ERR_UNSUPPORTED_SIZE (-2) /* nx0 + nx1 - 1 (or ny0 + ny1 - 1) above SF_MAX_CONV_LENGTH */
+#define SF_ERR_CUDA (-3)             /* a CUDA runtime call or kernel launch failed */
+#define SF_ERR_OOM (-4)              /* device or host allocation failed */
+#define SF_ERR_TIMEOUT (-5)          /* a bounded device-side wait gave up */
+#define SF_ERR_DEVICE_MISMATCH (-6)  /* plan used while another device is current */
+
+/* ---- view flags (sf_view.flags) ---- */
+#define SF_OUT_INTENSITY 1u /* informational: intensity buffers are passed to execute */
+#define SF_OUT_PHASE 2u     /* informational: phase buffers are passed to execute */
+#define SF_NO_PREFACTOR 4u  /* drop the constant exp(ikz)/(i lambda z) of Eq. 2 (the paper's choice for intensity) */
+#define SF_IN_COMPLEX 8u    /* the hologram is complex64 instead of float32 (same for every view of a plan) */
+
+/* ---- precision selector ---- */
+#define SF_PREC_FP32 0 /* FP32 FFT stages on CUDA cores; phases exact (64-bit fixed point) */
+
+/* Longest linear convolution per axis: nx0 + nx1 - 1 <= SF_MAX_CONV_LENGTH. */
+#define SF_MAX_CONV_LENGTH 8192
+
+/*
+ * One view (Section 2.1): wavelength and distance z (metres, z != 0, its
+ * sign is the propagation direction), hologram pitch (px0, py0), view pitch
+ * (px1, py1), physical plane offsets (ox0, oy0) and (ox1, oy1), hologram
+ * size nx0 x ny0 and view size nx1 x ny1.  All views of one plan share the
+ * hologram size, hologram pitch and the SF_IN_COMPLEX flag.
+ */
+typedef struct {
+  double wavelength, z;
+  double px0, py0, px1, py1;
+  double ox0, oy0, ox1, oy1;
+  int32_t nx0, ny0, nx1, ny1;
+  uint32_t flags;
+} sf_view;
+
+typedef struct sf_plan_s* sf_plan;
+
+/*
+ * shifted_fresnel_plan -- prepare n_views views of one hologram (Section 2.2,
+ * steps 5-6: the chirp kernel h of Eq. 4 and its FFT are built here, once per
+ * view and axis, as two 1-D spectra, and reused by every execute call).
+ *
+ *   out        receives the plan handle (set to NULL on failure).
+ *   views      host array of n_views view descriptions (copied; not retained).
+ *   n_views    1 .. 4096.
+ *   precision  SF_PREC_FP32.
+ *   device     CUDA device ordinal the plan is bound to (made current).
+ *   stream     stream for the set-up kernels; the call synchronises it
+ *              before returning.
+ *
+ * Allocates device memory (cudaMalloc): per view 8 * ny0 * nx1 bytes of
+ * workspace plus O(nx0 + nx1 + ny0 + ny1 + L) bytes of vectors.
+ * Errors: SF_ERR_INVALID_ARG, SF_ERR_UNSUPPORTED_SIZE, SF_ERR_OOM, SF_ERR_CUDA.
+ */
+int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int precision,
+                         int device, void* stream);
+
+/*
+ * shifted_fresnel_execute -- reconstruct every view of the plan from one
+ * hologram (Section 2.2, steps 2-10, and Eq. 5).
+ *
+ *   holo       hologram [ny0][nx0], float32 or (SF_IN_COMPLEX) complex64.
+ *   view_out   array of n_views pointers to complex64 [ny1][nx1] views, or
+ *              NULL; single entries may be NULL.
+ *   intensity  array of n_views pointers to float32 [ny1][nx1] |u1|^2 images
+ *              (Eq. 5), or NULL; single entries may be NULL.
+ *   phase      array of n_views pointers to float32 [ny1][nx1] phase images
+ *              atan2(Im u1, Re u1) in (-pi, pi], or NULL.
+ *   stream     stream to run on.
+ *
+ * Each of holo and the output buffers may be device memory or host memory
+ * (pinned or pageable).  Host buffers are staged through plan-owned device
+ * buffers that the first call with a host buffer allocates; their copies are
+ * ordered on the stream, so the caller synchronises the stream before
+ * reading host outputs.  Every view needs at least one non-NULL output.
+ * Errors: SF_ERR_INVALID_ARG, SF_ERR_DEVICE_MISMATCH, SF_ERR_OOM, SF_ERR_CUDA.
+ */
+int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out,
+                            float* const* intensity, float* const* phase, void* stream);
+
+/* shifted_fresnel_destroy -- synchronise the plan's device and free everything it owns. */
+int shifted_fresnel_destroy(sf_plan plan);
+
+/* shifted_fresnel_strerror -- static description of a status code (never NULL). */
+const char* shifted_fresnel_strerror(int status);
+
+/*
+ * shifted_fresnel_plan_query -- sizes the plan chose for one view.
+ *   lx, ly           FFT (convolution) lengths per axis, >= n0 + n1 - 1.
+ *   workspace_bytes  bytes of the view's intermediate buffer.
+ * Any output pointer may be NULL.  Errors: SF_ERR_INVALID_ARG.
+ */
+int shifted_fresnel_plan_query(sf_plan plan, int view, int32_t* lx, int32_t* ly,
+                               size_t* workspace_bytes);
+
+/*
+ * shifted_fresnel_set_profile_events -- attach timing events to a plan.
+ *   events     n_events cudaEvent_t handles (as void*) created by the caller
+ *              on the plan's device, or NULL with n_events = 0 to detach.
+ *   n_events   0 or 3.
+ * While attached, every execute call records events[0] on its stream before
+ * the first x-pass launch, events[1] between the x and y passes and
+ * events[2] after the last y-pass launch, so cudaEventElapsedTime gives the
+ * duration of each pass.  The plan does not own the events.
+ * Errors: SF_ERR_INVALID_ARG.
+ */
+int shifted_fresnel_set_profile_events(sf_plan plan, void* const* events, int n_events);
+
+/*
+ * shifted_fresnel_kernel_launches -- number of CUDA kernels this library has
+ * launched in this process so far (all plans, all devices).
+ */
+uint64_t shifted_fresnel_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHIFTED_FRESNEL_H */

@@ -1,0 +1,425 @@
+// sf_api.cu -- host side of the C ABI declared in include/shifted_fresnel.h.
+//
+// Plan: per view and axis, the phase polynomials of Eqs. 2-4 (Section 2.1)
+// are reduced modulo 2 pi into 64-bit fixed point on the host, and device
+// kernels turn them into the input chirp, the output chirp and the kernel
+// spectrum FFT(h) (Section 2.2, steps 5-6) once.  Execute: one x-pass launch
+// and one y-pass launch per group of views sharing FFT lengths.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "shifted_fresnel.h"
+#include "sf_internal.h"
+
+using namespace sf;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr uint32_t kKnownFlags = SF_OUT_INTENSITY | SF_OUT_PHASE | SF_NO_PREFACTOR | SF_IN_COMPLEX;
+constexpr int kMaxViews = 4096;
+constexpr int kMinFFT = 64;
+
+struct ViewState {
+  sf_view v;
+  AxisCoef ax[2];          // [0] = x, [1] = y; device pointers into the arena
+  float2* work = nullptr;  // [ny0][nx1] intermediate after the x pass
+  float2* st_out = nullptr;  // host-I/O staging (lazily allocated)
+  float* st_int = nullptr;
+  float* st_ph = nullptr;
+};
+
+}  // namespace
+
+struct sf_plan_s {
+  int device = 0;
+  int nx0 = 0, ny0 = 0;
+  bool in_complex = false;
+  std::vector<ViewState> views;
+  std::map<int, float2*> tw;  // twiddle table per FFT length
+  void* arena = nullptr;
+  void* st_holo = nullptr;
+  std::vector<void*> staging;
+  cudaEvent_t prof[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+
+// Reduce a phase coefficient (units of pi) modulo 2 into 64-bit fixed point.
+uint64_t to_fx(double c) {
+  double r = std::fmod(c, 2.0);
+  if (r < 0) r += 2.0;
+  const double s = std::ldexp(r, 63);
+  if (!(s < 18446744073709551616.0)) return 0;
+  return (uint64_t)s;
+}
+
+int next_fft_length(int need) {
+  int L = kMinFFT;
+  while (L < need) L <<= 1;
+  return L;
+}
+
+int validate_view(const sf_view& v) {
+  if (!finite_pos(v.wavelength) || !std::isfinite(v.z) || v.z == 0.0) return SF_ERR_INVALID_ARG;
+  if (!finite_pos(v.px0) || !finite_pos(v.py0) || !finite_pos(v.px1) || !finite_pos(v.py1)) return SF_ERR_INVALID_ARG;
+  if (!std::isfinite(v.ox0) || !std::isfinite(v.oy0) || !std::isfinite(v.ox1) || !std::isfinite(v.oy1))
+    return SF_ERR_INVALID_ARG;
+  if (v.nx0 <= 0 || v.ny0 <= 0 || v.nx1 <= 0 || v.ny1 <= 0) return SF_ERR_INVALID_ARG;
+  if (v.flags & ~kKnownFlags) return SF_ERR_INVALID_ARG;
+  if ((int64_t)v.nx0 + v.nx1 - 1 > SF_MAX_CONV_LENGTH || (int64_t)v.ny0 + v.ny1 - 1 > SF_MAX_CONV_LENGTH)
+    return SF_ERR_UNSUPPORTED_SIZE;
+  return SF_OK;
+}
+
+// Phase polynomials of one axis (units of pi).  With beta = 1/(lambda z),
+// a = o - floor(n/2) p, D = a1 - a0 and S = p0 p1 beta (the S of Eqs. 2-4):
+//   beta (x1 - x0)^2 = S (m1 - m0)^2 + psi_in(m0) + psi_out(m1)
+//   psi_in(m0)  = (beta p0^2 - S) m0^2 - 2 beta p0 D m0
+//   psi_out(m1) = (beta p1^2 - S) m1^2 + 2 beta p1 D m1 + beta D^2
+void axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
+  const double lam = v.wavelength, z = v.z, beta = 1.0 / (lam * z);
+  const int n0 = axis == 0 ? v.nx0 : v.ny0, n1 = axis == 0 ? v.nx1 : v.ny1;
+  const double p0 = axis == 0 ? v.px0 : v.py0, p1 = axis == 0 ? v.px1 : v.py1;
+  const double o0 = axis == 0 ? v.ox0 : v.oy0, o1 = axis == 0 ? v.ox1 : v.oy1;
+  const double a0 = o0 - (double)(n0 / 2) * p0, a1 = o1 - (double)(n1 / 2) * p1;
+  const double D = a1 - a0, S = p0 * p1 * beta;
+  a.n0 = n0;
+  a.n1 = n1;
+  a.L = next_fft_length(n0 + n1 - 1);
+  a.in2 = to_fx(beta * p0 * p0 - S);
+  a.in1 = to_fx(-2.0 * beta * p0 * D);
+  a.in0 = 0;
+  a.out2 = to_fx(beta * p1 * p1 - S);
+  a.out1 = to_fx(2.0 * beta * p1 * D);
+  double c0 = beta * D * D;
+  a.out_scale = 1.0 / (double)a.L;
+  if (axis == 1 && !(v.flags & SF_NO_PREFACTOR)) {
+    // exp(i k z) / (i lambda z) = exp(i pi (2 z / lambda - 1/2)) / (lambda z)
+    c0 = std::fmod(c0, 2.0) + std::fmod(2.0 * (z / lam), 2.0) - 0.5;
+    a.out_scale /= lam * z;
+  }
+  a.out0 = to_fx(c0);
+  a.h2 = to_fx(S);
+}
+
+struct Arena {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+enum PtrKind { PTR_DEVICE, PTR_HOST, PTR_OTHER_DEVICE };
+
+PtrKind classify(const void* p, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_HOST;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+    return at.device == device ? PTR_DEVICE : PTR_OTHER_DEVICE;
+  return PTR_HOST;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void free_plan(sf_plan p) {
+  if (!p) return;
+  for (void* s : p->staging) cudaFree(s);
+  if (p->arena) cudaFree(p->arena);
+  delete p;
+}
+
+int stage_alloc(sf_plan p, void** out, size_t bytes) {
+  if (*out) return SF_OK;
+  if (cudaMalloc(out, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return SF_ERR_OOM;
+  }
+  p->staging.push_back(*out);
+  return SF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* shifted_fresnel_strerror(int status) {
+  switch (status) {
+    case SF_OK: return "success";
+    case SF_ERR_INVALID_ARG: return "invalid argument";
+    case SF_ERR_UNSUPPORTED_SIZE: return "unsupported size: n0 + n1 - 1 exceeds the longest supported convolution";
+    case SF_ERR_CUDA: return "CUDA runtime error";
+    case SF_ERR_OOM: return "out of memory";
+    case SF_ERR_TIMEOUT: return "device-side wait timed out";
+    case SF_ERR_DEVICE_MISMATCH: return "buffer belongs to another device than the plan";
+    default: return "unknown status";
+  }
+}
+
+uint64_t shifted_fresnel_kernel_launches(void) { return g_launches.load(); }
+
+int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int precision, int device,
+                         void* stream) {
+  if (!out) return SF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!views || n_views < 1 || n_views > kMaxViews) return SF_ERR_INVALID_ARG;
+  if (precision != SF_PREC_FP32) return SF_ERR_INVALID_ARG;
+  for (int i = 0; i < n_views; ++i) {
+    int rc = validate_view(views[i]);
+    if (rc) return rc;
+    if (views[i].nx0 != views[0].nx0 || views[i].ny0 != views[0].ny0 ||
+        (views[i].flags & SF_IN_COMPLEX) != (views[0].flags & SF_IN_COMPLEX))
+      return SF_ERR_INVALID_ARG;
+  }
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess) { cudaGetLastError(); return SF_ERR_CUDA; }
+  if (device < 0 || device >= n_dev) return SF_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return SF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  sf_plan p = new (std::nothrow) sf_plan_s();
+  if (!p) return SF_ERR_OOM;
+  p->device = device;
+  p->nx0 = views[0].nx0;
+  p->ny0 = views[0].ny0;
+  p->in_complex = (views[0].flags & SF_IN_COMPLEX) != 0;
+  p->views.resize(n_views);
+
+  // coefficients and arena layout
+  Arena ar;
+  std::map<int, size_t> tw_off;
+  std::vector<size_t> off_cin(2 * n_views), off_cout(2 * n_views), off_H(2 * n_views), off_work(n_views);
+  for (int i = 0; i < n_views; ++i) {
+    ViewState& vs = p->views[i];
+    vs.v = views[i];
+    for (int a = 0; a < 2; ++a) {
+      axis_coefficients(vs.v, a, vs.ax[a]);
+      const AxisCoef& c = vs.ax[a];
+      if (!tw_off.count(c.L)) tw_off[c.L] = ar.take(sizeof(float2) * c.L);
+      off_cin[2 * i + a] = ar.take(sizeof(float2) * c.n0);
+      off_cout[2 * i + a] = ar.take(sizeof(float2) * c.n1);
+      off_H[2 * i + a] = ar.take(sizeof(float2) * c.L);
+    }
+    off_work[i] = ar.take(sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1);
+  }
+  const size_t off_axes = ar.take(sizeof(AxisCoef) * 2 * n_views);
+  if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    return SF_ERR_OOM;
+  }
+  char* base = static_cast<char*>(p->arena);
+  for (auto& kv : tw_off) p->tw[kv.first] = reinterpret_cast<float2*>(base + kv.second);
+
+  // axes sorted by FFT length so each length's spectra are built by one launch
+  std::vector<AxisCoef> axes;
+  axes.reserve(2 * n_views);
+  int max_n = 1;
+  for (int i = 0; i < n_views; ++i) {
+    ViewState& vs = p->views[i];
+    vs.work = reinterpret_cast<float2*>(base + off_work[i]);
+    for (int a = 0; a < 2; ++a) {
+      AxisCoef& c = vs.ax[a];
+      c.cin = reinterpret_cast<float2*>(base + off_cin[2 * i + a]);
+      c.cout = reinterpret_cast<float2*>(base + off_cout[2 * i + a]);
+      c.H = reinterpret_cast<float2*>(base + off_H[2 * i + a]);
+      axes.push_back(c);
+      max_n = std::max(max_n, std::max(c.n0, c.n1));
+    }
+  }
+  std::stable_sort(axes.begin(), axes.end(), [](const AxisCoef& x, const AxisCoef& y) { return x.L < y.L; });
+  AxisCoef* axes_dev = reinterpret_cast<AxisCoef*>(base + off_axes);
+
+  cudaError_t e = cudaMemcpyAsync(axes_dev, axes.data(), sizeof(AxisCoef) * axes.size(), cudaMemcpyHostToDevice, s);
+  for (auto& kv : p->tw)
+    if (e == cudaSuccess) { e = launch_twiddles(kv.second, kv.first, s); ++g_launches; }
+  if (e == cudaSuccess) { e = launch_chirps(axes_dev, (int)axes.size(), max_n, s); ++g_launches; }
+  for (size_t i = 0; i < axes.size() && e == cudaSuccess;) {
+    size_t j = i;
+    while (j < axes.size() && axes[j].L == axes[i].L) ++j;
+    e = launch_hspec(axes[i].L, axes_dev + i, (int)(j - i), p->tw[axes[i].L], s);
+    ++g_launches;
+    i = j;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    return e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA;
+  }
+  *out = p;
+  return SF_OK;
+}
+
+int shifted_fresnel_plan_query(sf_plan plan, int view, int32_t* lx, int32_t* ly, size_t* workspace_bytes) {
+  if (!plan || view < 0 || view >= (int)plan->views.size()) return SF_ERR_INVALID_ARG;
+  const ViewState& vs = plan->views[view];
+  if (lx) *lx = vs.ax[0].L;
+  if (ly) *ly = vs.ax[1].L;
+  if (workspace_bytes) *workspace_bytes = sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1;
+  return SF_OK;
+}
+
+int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out, float* const* intensity,
+                            float* const* phase, void* stream) {
+  if (!plan || !holo) return SF_ERR_INVALID_ARG;
+  const int nv = (int)plan->views.size();
+  for (int i = 0; i < nv; ++i) {
+    const bool any = (view_out && view_out[i]) || (intensity && intensity[i]) || (phase && phase[i]);
+    if (!any) return SF_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return SF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+
+  // hologram: device pointer used in place, host memory staged
+  const size_t holo_bytes = (plan->in_complex ? sizeof(float2) : sizeof(float)) * (size_t)plan->nx0 * plan->ny0;
+  const void* src = holo;
+  switch (classify(holo, plan->device)) {
+    case PTR_OTHER_DEVICE: return SF_ERR_DEVICE_MISMATCH;
+    case PTR_HOST: {
+      int rc = stage_alloc(plan, &plan->st_holo, holo_bytes);
+      if (rc) return rc;
+      e = cudaMemcpyAsync(plan->st_holo, holo, holo_bytes, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) { cudaGetLastError(); return SF_ERR_CUDA; }
+      src = plan->st_holo;
+      break;
+    }
+    default: break;
+  }
+
+  // outputs: resolve staging for host buffers
+  struct Copy { void* dst; const void* src; size_t bytes; };
+  std::vector<Copy> d2h;
+  std::vector<float2*> dout(nv, nullptr);
+  std::vector<float*> dint(nv, nullptr), dph(nv, nullptr);
+  for (int i = 0; i < nv; ++i) {
+    ViewState& vs = plan->views[i];
+    const size_t npx = (size_t)vs.v.nx1 * vs.v.ny1;
+    auto resolve = [&](void* user, void** stage, size_t bytes, void** dev) -> int {
+      if (!user) return SF_OK;
+      switch (classify(user, plan->device)) {
+        case PTR_OTHER_DEVICE: return SF_ERR_DEVICE_MISMATCH;
+        case PTR_HOST: {
+          int rc = stage_alloc(plan, stage, bytes);
+          if (rc) return rc;
+          d2h.push_back({user, *stage, bytes});
+          *dev = *stage;
+          return SF_OK;
+        }
+        default: *dev = user; return SF_OK;
+      }
+    };
+    int rc = resolve(view_out ? view_out[i] : nullptr, (void**)&vs.st_out, sizeof(float2) * npx, (void**)&dout[i]);
+    if (!rc) rc = resolve(intensity ? (void*)intensity[i] : nullptr, (void**)&vs.st_int, sizeof(float) * npx, (void**)&dint[i]);
+    if (!rc) rc = resolve(phase ? (void*)phase[i] : nullptr, (void**)&vs.st_ph, sizeof(float) * npx, (void**)&dph[i]);
+    if (rc) return rc;
+  }
+
+  // x passes then y passes, each grouped by FFT length
+  if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);
+  for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
+    if (axis == 1 && plan->prof[1]) e = cudaEventRecord(plan->prof[1], s);
+    std::vector<int> order(nv);
+    for (int i = 0; i < nv; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return plan->views[a].ax[axis].L < plan->views[b].ax[axis].L; });
+    for (int i = 0; i < nv && e == cudaSuccess;) {
+      const int L = plan->views[order[i]].ax[axis].L;
+      PassBatch b;
+      std::memset(&b, 0, sizeof(b));
+      int max_rows = 0;
+      while (i < nv && b.count < kMaxPassBatch && plan->views[order[i]].ax[axis].L == L) {
+        const int vi = order[i++];
+        ViewState& vs = plan->views[vi];
+        const AxisCoef& c = vs.ax[axis];
+        PassDesc& d = b.d[b.count++];
+        d.cin = c.cin;
+        d.cout = c.cout;
+        d.H = c.H;
+        d.n0 = c.n0;
+        d.n1 = c.n1;
+        if (axis == 0) {
+          d.src = src;
+          d.dst = vs.work;
+          d.rows = vs.v.ny0;
+          d.src_ld = vs.v.nx0;
+          d.dst_ld = vs.v.nx1;
+        } else {
+          d.src = vs.work;
+          d.dst = dout[vi];
+          d.inten = dint[vi];
+          d.phase = dph[vi];
+          d.rows = vs.v.nx1;
+          d.src_ld = vs.v.nx1;
+          d.dst_ld = vs.v.nx1;
+        }
+        max_rows = std::max(max_rows, d.rows);
+      }
+      const int G = pass_rows_per_cta(L);
+      const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
+      e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
+      ++g_launches;
+    }
+  }
+  if (e == cudaSuccess && plan->prof[2]) e = cudaEventRecord(plan->prof[2], s);
+  for (const Copy& c : d2h)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+int shifted_fresnel_set_profile_events(sf_plan plan, void* const* events, int n_events) {
+  if (!plan) return SF_ERR_INVALID_ARG;
+  if (n_events == 0) {
+    plan->prof[0] = plan->prof[1] = plan->prof[2] = nullptr;
+    return SF_OK;
+  }
+  if (n_events != 3 || !events || !events[0] || !events[1] || !events[2]) return SF_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i) plan->prof[i] = (cudaEvent_t)events[i];
+  return SF_OK;
+}
+
+int shifted_fresnel_destroy(sf_plan plan) {
+  if (!plan) return SF_ERR_INVALID_ARG;
+  DeviceGuard guard(plan->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  free_plan(plan);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// sf_fft.cuh -- in-register / shared-memory FFT building blocks for sm_103a.
+//
+// The zero-padded FFT convolution of Eq. 1 (Section 2.1) is done per row
+// by one thread group of T = L / E threads, each holding E complex values in
+// registers.  The length-L transform is an in-place decimation-in-frequency
+// network of radix-E stages (the last stage takes the remaining factor):
+//
+//   stage s, sub-length M' = L / (R_0 ... R_{s-1}), radix R = R_s, M = M' / R:
+//   for every butterfly (K, n), K < L / M', n < M, the R values at positions
+//   K M' + n + j M (j < R) are replaced by  y_k = W_{M'}^{n k} sum_j x_j W_R^{j k}
+//   at positions K M' + n + k M.
+//
+// After the last stage position p holds frequency f(p), the mixed-radix digit
+// reversal of p.  The convolution never needs natural frequency order: the
+// kernel spectrum is produced by the same network (so it sits in the same
+// positions), multiplied in registers, and the exact adjoint network (stages
+// in reverse order, conjugated twiddles applied before an inverse radix-R DFT)
+// returns L times the circular convolution in natural order.
+//
+// Between stages the values move through a shared-memory row buffer with an
+// XOR swizzle on the low four position bits, which keeps 8-byte accesses of
+// 16 consecutive lanes on distinct bank pairs for every stage pattern used.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sf {
+
+// ---------------------------------------------------------------- complex ops
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Multiplication by W_4 = exp(-+ 2 pi i / 4): -i for the forward transform, +i for the inverse.
+template <bool INV>
+__device__ __forceinline__ float2 mul_w4(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// Twiddle constants W_16^e = exp(-2 pi i e / 16) (conjugated for the inverse).
+constexpr float kC1 = 0.92387953251128676f;  // cos(pi/8)
+constexpr float kS1 = 0.38268343236508977f;  // sin(pi/8)
+constexpr float kR2 = 0.70710678118654752f;  // cos(pi/4)
+
+template <bool INV, int E16>
+__device__ __forceinline__ float2 mul_w16(float2 a) {
+  constexpr int e = E16 & 15;
+  if constexpr (e == 0) return a;
+  else if constexpr (e == 4) return mul_w4<INV>(a);
+  else if constexpr (e == 8) return make_float2(-a.x, -a.y);
+  else if constexpr (e == 12) return mul_w4<!INV>(a);
+  else if constexpr (e == 2 || e == 6 || e == 10 || e == 14) {
+    // (+-c, +-c) with c = cos(pi/4): two adds and two multiplies
+    constexpr float wr = (e == 2 || e == 14) ? kR2 : -kR2;
+    constexpr float wi0 = (e == 2 || e == 6) ? -kR2 : kR2;
+    constexpr float wi = INV ? -wi0 : wi0;
+    return make_float2(wr * a.x - wi * a.y, wr * a.y + wi * a.x);
+  } else {
+    constexpr float cs[16] = {1.f, kC1, kR2, kS1, 0.f, -kS1, -kR2, -kC1, -1.f, -kC1, -kR2, -kS1, 0.f, kS1, kR2, kC1};
+    constexpr float wr = cs[e];
+    constexpr float wi0 = -cs[(e + 12) & 15];  // -sin(2 pi e / 16)
+    constexpr float wi = INV ? -wi0 : wi0;
+    return make_float2(fmaf(wr, a.x, -wi * a.y), fmaf(wr, a.y, wi * a.x));
+  }
+}
+
+// ------------------------------------------------------------- radix-R DFTs
+// In place, natural order in and out: x[k] <- sum_j x[j] W_R^{j k}
+// (W_R = exp(-2 pi i / R); exp(+2 pi i / R) for INV, no 1/R scaling).
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s0 = cadd(a0, a2), d0 = csub(a0, a2);
+  float2 s1 = cadd(a1, a3), d1 = mul_w4<INV>(csub(a1, a3));
+  a0 = cadd(s0, s1);
+  a2 = csub(s0, s1);
+  a1 = cadd(d0, d1);
+  a3 = csub(d0, d1);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* x) {
+  // even / odd halves, then combine with W_8^k = W_16^{2k}
+  float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = mul_w16<INV, 2>(o1);
+  o2 = mul_w16<INV, 4>(o2);
+  o3 = mul_w16<INV, 6>(o3);
+  x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
+  x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
+  x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+  x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* x) {
+  // 4 x 4: j = 4 j1 + j2, k = k1 + 4 k2
+  float2 b[16];
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) {
+    float2 a0 = x[j2], a1 = x[4 + j2], a2 = x[8 + j2], a3 = x[12 + j2];
+    dft4<INV>(a0, a1, a2, a3);  // over j1 -> k1
+    b[4 * j2 + 0] = a0; b[4 * j2 + 1] = a1; b[4 * j2 + 2] = a2; b[4 * j2 + 3] = a3;
+  }
+  // twiddle W_16^{j2 k1}
+  b[4 * 1 + 1] = mul_w16<INV, 1>(b[4 * 1 + 1]);
+  b[4 * 1 + 2] = mul_w16<INV, 2>(b[4 * 1 + 2]);
+  b[4 * 1 + 3] = mul_w16<INV, 3>(b[4 * 1 + 3]);
+  b[4 * 2 + 1] = mul_w16<INV, 2>(b[4 * 2 + 1]);
+  b[4 * 2 + 2] = mul_w16<INV, 4>(b[4 * 2 + 2]);
+  b[4 * 2 + 3] = mul_w16<INV, 6>(b[4 * 2 + 3]);
+  b[4 * 3 + 1] = mul_w16<INV, 3>(b[4 * 3 + 1]);
+  b[4 * 3 + 2] = mul_w16<INV, 6>(b[4 * 3 + 2]);
+  b[4 * 3 + 3] = mul_w16<INV, 9>(b[4 * 3 + 3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 a0 = b[k1], a1 = b[4 + k1], a2 = b[8 + k1], a3 = b[12 + k1];
+    dft4<INV>(a0, a1, a2, a3);  // over j2 -> k2
+    x[k1 + 0] = a0; x[k1 + 4] = a1; x[k1 + 8] = a2; x[k1 + 12] = a3;
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* x) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<INV>(x[0], x[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (R == 8) {
+    dft8<INV>(x);
+  } else if constexpr (R == 16) {
+    dft16<INV>(x);
+  } else {
+    static_assert(R == 16, "unsupported radix");
+  }
+}
+
+// ------------------------------------------------------------- stage layout
+constexpr int stage_count(int L, int E) {
+  int s = 0, M = L;
+  while (M > 1) { M /= (M > E ? E : M); ++s; }
+  return s;
+}
+// sub-length M' entering stage s
+constexpr int stage_mprev(int L, int E, int s) {
+  int M = L;
+  for (int i = 0; i < s; ++i) M /= (M > E ? E : M);
+  return M;
+}
+constexpr int stage_radix(int L, int E, int s) {
+  return stage_mprev(L, E, s) > E ? E : stage_mprev(L, E, s);
+}
+
+// Shared-memory swizzle of a row position (8-byte elements).
+__device__ __forceinline__ int swz(int p) { return p ^ ((p >> 4) & 15); }
+
+// Position of element j of butterfly u (u < E / R) of thread t in stage s.
+template <int L, int E, int S>
+struct Stage {
+  static constexpr int T = L / E;
+  static constexpr int MP = stage_mprev(L, E, S);
+  static constexpr int R = stage_radix(L, E, S);
+  static constexpr int M = MP / R;
+  static constexpr int NB = E / R;
+  static_assert(E % R == 0, "radix must divide the per-thread element count");
+  __device__ __forceinline__ static int base(int t, int u) {
+    int b = t + T * u;
+    return (b / M) * MP + (b % M);
+  }
+  __device__ __forceinline__ static int nidx(int t, int u) { return (t + T * u) % M; }
+};
+
+// Forward stage s on registers (values enter at the stage's read positions
+// and leave at the same positions with k in place of j).
+template <int L, int E, int S>
+__device__ __forceinline__ void stage_fwd(float2* v, int t, const float2* __restrict__ tw) {
+  using St = Stage<L, E, S>;
+#pragma unroll
+  for (int u = 0; u < St::NB; ++u) {
+    dft<St::R, false>(v + u * St::R);
+    if constexpr (St::M > 1) {
+      const int n = St::nidx(t, u);
+#pragma unroll
+      for (int k = 1; k < St::R; ++k) {
+        // W_{M'}^{n k} = tw[n k L / M'] with tw[i] = exp(-2 pi i i / L)
+        const int e = (n * k * (L / St::MP)) & (L - 1);
+        v[u * St::R + k] = cmul(v[u * St::R + k], __ldg(tw + e));
+      }
+    }
+  }
+}
+
+// Adjoint of stage_fwd: conjugate twiddles, then the inverse radix-R DFT.
+template <int L, int E, int S>
+__device__ __forceinline__ void stage_inv(float2* v, int t, const float2* __restrict__ tw) {
+  using St = Stage<L, E, S>;
+#pragma unroll
+  for (int u = 0; u < St::NB; ++u) {
+    if constexpr (St::M > 1) {
+      const int n = St::nidx(t, u);
+#pragma unroll
+      for (int k = 1; k < St::R; ++k) {
+        const int e = (n * k * (L / St::MP)) & (L - 1);
+        v[u * St::R + k] = cmulc(v[u * St::R + k], __ldg(tw + e));
+      }
+    }
+    dft<St::R, true>(v + u * St::R);
+  }
+}
+
+template <int L, int E, int S>
+__device__ __forceinline__ void stage_store(const float2* v, int t, float2* buf) {
+  using St = Stage<L, E, S>;
+#pragma unroll
+  for (int u = 0; u < St::NB; ++u) {
+    const int b0 = St::base(t, u);
+#pragma unroll
+    for (int k = 0; k < St::R; ++k) buf[swz(b0 + k * St::M)] = v[u * St::R + k];
+  }
+}
+
+template <int L, int E, int S>
+__device__ __forceinline__ void stage_load(float2* v, int t, const float2* buf) {
+  using St = Stage<L, E, S>;
+#pragma unroll
+  for (int u = 0; u < St::NB; ++u) {
+    const int b0 = St::base(t, u);
+#pragma unroll
+    for (int k = 0; k < St::R; ++k) v[u * St::R + k] = buf[swz(b0 + k * St::M)];
+  }
+}
+
+// Full forward network.  Input: v[j] = x[t + T j] (stage 0 layout).
+// Output: the last stage's positions.  buf: this group's L-element row buffer.
+// Barrier: every thread of the CTA calls this the same number of times.
+template <int L, int E, int S = 0>
+__device__ __forceinline__ void fft_forward(float2* v, int t, float2* buf, const float2* __restrict__ tw) {
+  constexpr int NS = stage_count(L, E);
+  stage_fwd<L, E, S>(v, t, tw);
+  if constexpr (S + 1 < NS) {
+    __syncthreads();  // previous readers of buf are done
+    stage_store<L, E, S>(v, t, buf);
+    __syncthreads();
+    stage_load<L, E, S + 1>(v, t, buf);
+    fft_forward<L, E, S + 1>(v, t, buf, tw);
+  }
+}
+
+// Adjoint network: from the last stage's positions back to v[j] = x[t + T j].
+template <int L, int E, int S = stage_count(L, E) - 1>
+__device__ __forceinline__ void fft_inverse(float2* v, int t, float2* buf, const float2* __restrict__ tw) {
+  stage_inv<L, E, S>(v, t, tw);
+  if constexpr (S > 0) {
+    __syncthreads();
+    stage_store<L, E, S>(v, t, buf);
+    __syncthreads();
+    stage_load<L, E, S - 1>(v, t, buf);
+    fft_inverse<L, E, S - 1>(v, t, buf, tw);
+  }
+}
+
+// Register e of thread t after fft_forward sits at position last_pos(t, e).
+template <int L, int E>
+__device__ __forceinline__ int last_pos(int t, int e) {
+  using St = Stage<L, E, stage_count(L, E) - 1>;
+  const int u = e / St::R, k = e % St::R;
+  return St::base(t, u) + k * St::M;
+}
+
+}  // namespace sf

@@ -1,0 +1,58 @@
+// sf_internal.h -- types shared by the host library and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sf {
+
+constexpr int kMaxPassBatch = 16;  // (view, axis) passes per launch
+constexpr int kE = 16;             // complex values per thread in the FFT network
+
+enum PassKind : int { PASS_X_REAL = 0, PASS_X_CPLX = 1, PASS_Y = 2 };
+
+// One separable half of one view (Section 2.2, steps 2-9 along one axis).
+//   X pass: src = hologram rows [rows = ny0][src_ld = nx0], dst = workspace [ny0][dst_ld = nx1]
+//   Y pass: src = workspace, column `row` read with stride src_ld = nx1;
+//           dst = view [ny1][nx1] written down column `row` (stride dst_ld = nx1)
+struct PassDesc {
+  const void* src;
+  float2* dst;        // complex output (Y: may be null)
+  float* inten;       // Y only, may be null
+  float* phase;       // Y only, may be null
+  const float2* cin;  // input chirp, n0 entries
+  const float2* cout; // output chirp (with 1/L and, on Y, the constant of Eq. 2), n1 entries
+  const float2* H;    // kernel spectrum in register order, L entries
+  int n0, n1;         // convolution input / output lengths along this axis
+  int rows;           // independent rows of this pass
+  int src_ld, dst_ld;
+};
+
+struct PassBatch {
+  PassDesc d[kMaxPassBatch];
+  int count;
+};
+
+// Per-axis phase polynomials in units of pi, as 64-bit fixed point (2^63 = pi).
+struct AxisCoef {
+  uint64_t in2, in1, in0;     // psi_in(m0)  = in2 m0^2 + in1 m0 + in0
+  uint64_t out2, out1, out0;  // psi_out(m1) = out2 m1^2 + out1 m1 + out0
+  uint64_t h2;                // h[d] = exp(i pi h2 d^2)   (S of Eq. 4)
+  double out_scale;           // real scale of the output chirp
+  int n0, n1, L;
+  float2* cin;                // device, n0
+  float2* cout;               // device, n1
+  float2* H;                  // device, L (register order)
+};
+
+// launchers (one translation unit per FFT length family)
+cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float2* tw, cudaStream_t s);
+cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const float2* tw, cudaStream_t s);
+cudaError_t launch_chirps(const AxisCoef* axes_dev, int n_axes, int max_n, cudaStream_t s);
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+int pass_rows_per_cta(int L);
+int pass_threads(int L);
+size_t pass_smem_bytes(int L);
+bool fft_length_supported(int L);
+
+}  // namespace sf

@@ -1,0 +1,164 @@
+// sf_kernels.cuh -- fused Bluestein row-pass kernel and the plan-time kernels.
+//
+// One launch of k_pass runs Section 2.2 steps 2-4 and 7-9 (and, on the y
+// pass, step 10 with Eq. 5) for every row of up to kMaxPassBatch
+// (view, axis) passes:
+//
+//   load row (implicit zero padding to L)  x  input chirp of Eq. 3   (steps 2-3)
+//   forward length-L FFT network                                     (step 4)
+//   x kernel spectrum FFT(h) of Eq. 4, cached at plan time           (steps 5-7)
+//   adjoint (inverse) FFT network                                    (step 8)
+//   crop to n1 outputs  x  output chirp of Eq. 2 (and 1/L)           (step 9)
+//   y pass only: complex view, |u1|^2 (Eq. 5) and phase              (step 10)
+//
+// A CTA holds G = max(1, 256 / T) groups of T = L / 16 threads; group g
+// handles row blockIdx.x * G + g of pass blockIdx.y.
+#pragma once
+
+#include <climits>
+
+#include "sf_fft.cuh"
+#include "sf_internal.h"
+
+namespace sf {
+
+template <int L>
+struct PassShape {
+  static constexpr int T = L / kE;
+  static constexpr int G = (256 / T) > 0 ? (256 / T) : 1;
+  static constexpr int THREADS = G * T;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)G * L;
+};
+
+// exp(i pi ph / 2^63) from a 64-bit fixed-point phase (full scale 2^64 = 2 pi).
+__device__ __forceinline__ float2 expi_fx(uint64_t ph) {
+  const double a = (double)(int64_t)ph * 0x1p-63;  // in [-1, 1): units of pi
+  double s, c;
+  sincospi(a, &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+__device__ __forceinline__ float phase_of(float2 u) {
+  float p = atan2f(u.y, u.x);
+  return p <= -3.14159265358979f ? 3.14159265358979f : p;  // (-pi, pi]
+}
+
+template <int L, int KIND>
+__global__ void __launch_bounds__(PassShape<L>::THREADS)
+k_pass(const __grid_constant__ PassBatch b, const float2* __restrict__ tw) {
+  using Sh = PassShape<L>;
+  constexpr int T = Sh::T, G = Sh::G, E = kE;
+  extern __shared__ float2 smem[];
+  const PassDesc& d = b.d[blockIdx.y];
+  if ((int)blockIdx.x * G >= d.rows) return;  // whole CTA past this pass's rows
+  const int g = threadIdx.x / T, t = threadIdx.x % T;
+  const int row = blockIdx.x * G + g;
+  const bool valid = row < d.rows;
+  float2* buf = smem + g * L;
+
+  float2 v[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int p = t + T * j;
+    v[j] = make_float2(0.f, 0.f);
+    if (valid && p < d.n0) {
+      const float2 c = __ldg(d.cin + p);
+      if constexpr (KIND == PASS_X_REAL) {
+        const float x = __ldg(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + p);
+        v[j] = cscale(c, x);
+      } else if constexpr (KIND == PASS_X_CPLX) {
+        const float2 x = __ldg(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + p);
+        v[j] = cmul(x, c);
+      } else {
+        const float2 x = static_cast<const float2*>(d.src)[(size_t)p * d.src_ld + row];
+        v[j] = cmul(x, c);
+      }
+    }
+  }
+
+  fft_forward<L, E>(v, t, buf, tw);
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(d.H + e * T + t));
+  fft_inverse<L, E>(v, t, buf, tw);
+
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int p = t + T * j;
+    if (valid && p < d.n1) {
+      const float2 u = cmul(v[j], __ldg(d.cout + p));
+      if constexpr (KIND != PASS_Y) {
+        d.dst[(size_t)row * d.dst_ld + p] = u;
+      } else {
+        const size_t o = (size_t)p * d.dst_ld + row;
+        if (d.dst) d.dst[o] = u;
+        if (d.inten) d.inten[o] = fmaf(u.x, u.x, u.y * u.y);
+        if (d.phase) d.phase[o] = phase_of(u);
+      }
+    }
+  }
+}
+
+// Kernel spectrum of Eq. 4 (steps 5-6), one thread group per axis, run once
+// at plan time: h[p] = exp(i pi S d^2) with d = p for p < n1, d = p - L for
+// p > L - n0, 0 elsewhere; pushed through the same forward network so it
+// lands in register order.
+template <int L>
+__global__ void __launch_bounds__(L / kE) k_hspec(const AxisCoef* __restrict__ axes, const float2* __restrict__ tw) {
+  constexpr int T = L / kE, E = kE;
+  extern __shared__ float2 smem[];
+  const AxisCoef a = axes[blockIdx.x];
+  const int t = threadIdx.x;
+  float2 v[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int p = t + T * j;
+    int dd = INT_MIN;
+    if (p < a.n1) dd = p;
+    else if (p > L - a.n0) dd = p - L;
+    v[j] = dd == INT_MIN ? make_float2(0.f, 0.f) : expi_fx(a.h2 * (uint64_t)((int64_t)dd * dd));
+  }
+  fft_forward<L, E>(v, t, smem, tw);
+#pragma unroll
+  for (int e = 0; e < E; ++e) a.H[e * T + t] = v[e];
+}
+
+template <int L>
+cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const float2* tw, cudaStream_t s) {
+  using Sh = PassShape<L>;
+  const dim3 grid(grid_x, b.count), block(Sh::THREADS);
+  auto go = [&](auto kern) {
+    if (Sh::SMEM > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, block, Sh::SMEM, s>>>(b, tw);
+    return cudaGetLastError();
+  };
+  switch (kind) {
+    case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL>);
+    case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX>);
+    case PASS_Y: return go(k_pass<L, PASS_Y>);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int L>
+cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float2* tw, cudaStream_t s) {
+  constexpr size_t smem = sizeof(float2) * (size_t)L;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_hspec<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_hspec<L><<<n_axes, L / kE, smem, s>>>(axes_dev, tw);
+  return cudaGetLastError();
+}
+
+#define SF_INSTANTIATE_LENGTH(LL)                                                                      \
+  template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float2*, cudaStream_t); \
+  template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float2*, cudaStream_t);
+
+#define SF_DECLARE_LENGTH(LL)                                                                                 \
+  extern template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float2*, cudaStream_t); \
+  extern template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float2*, cudaStream_t);
+
+}  // namespace sf

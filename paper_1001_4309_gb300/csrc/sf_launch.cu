@@ -1,0 +1,97 @@
+// sf_launch.cu -- launch dispatch by FFT length, and the plan-time chirp and
+// twiddle kernels.
+#include "sf_kernels.cuh"
+
+namespace sf {
+
+SF_DECLARE_LENGTH(64)
+SF_DECLARE_LENGTH(128)
+SF_DECLARE_LENGTH(256)
+SF_DECLARE_LENGTH(512)
+SF_DECLARE_LENGTH(1024)
+SF_DECLARE_LENGTH(2048)
+SF_DECLARE_LENGTH(4096)
+SF_DECLARE_LENGTH(8192)
+
+bool fft_length_supported(int L) {
+  switch (L) {
+    case 64: case 128: case 256: case 512: case 1024: case 2048: case 4096: case 8192: return true;
+    default: return false;
+  }
+}
+
+#define SF_LENGTH_SWITCH(L, CALL)                 \
+  switch (L) {                                    \
+    case 64: { constexpr int LL = 64; CALL; }     \
+    case 128: { constexpr int LL = 128; CALL; }   \
+    case 256: { constexpr int LL = 256; CALL; }   \
+    case 512: { constexpr int LL = 512; CALL; }   \
+    case 1024: { constexpr int LL = 1024; CALL; } \
+    case 2048: { constexpr int LL = 2048; CALL; } \
+    case 4096: { constexpr int LL = 4096; CALL; } \
+    case 8192: { constexpr int LL = 8192; CALL; } \
+    default: break;                               \
+  }
+
+cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float2* tw, cudaStream_t s) {
+  SF_LENGTH_SWITCH(L, return launch_pass_t<LL>(kind, b, grid_x, tw, s))
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const float2* tw, cudaStream_t s) {
+  SF_LENGTH_SWITCH(L, return launch_hspec_t<LL>(axes_dev, n_axes, tw, s))
+  return cudaErrorInvalidValue;
+}
+
+int pass_rows_per_cta(int L) {
+  SF_LENGTH_SWITCH(L, return PassShape<LL>::G)
+  return 0;
+}
+int pass_threads(int L) {
+  SF_LENGTH_SWITCH(L, return PassShape<LL>::THREADS)
+  return 0;
+}
+size_t pass_smem_bytes(int L) {
+  SF_LENGTH_SWITCH(L, return PassShape<LL>::SMEM)
+  return 0;
+}
+
+// Input and output chirp vectors of every (view, axis): blockIdx.y = axis,
+// blockIdx.z = 0 for exp(i pi psi_in(m0)), 1 for out_scale exp(i pi psi_out(m1)).
+__global__ void k_chirps(const AxisCoef* __restrict__ axes) {
+  const AxisCoef& a = axes[blockIdx.y];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t mm = (uint64_t)m * (uint64_t)m;
+  if (blockIdx.z == 0) {
+    if (m < a.n0) a.cin[m] = expi_fx(a.in2 * mm + a.in1 * (uint64_t)m + a.in0);
+  } else if (m < a.n1) {
+    const uint64_t ph = a.out2 * mm + a.out1 * (uint64_t)m + a.out0;
+    const double ang = (double)(int64_t)ph * 0x1p-63;
+    double s, c;
+    sincospi(ang, &s, &c);
+    a.cout[m] = make_float2((float)(a.out_scale * c), (float)(a.out_scale * s));
+  }
+}
+
+cudaError_t launch_chirps(const AxisCoef* axes_dev, int n_axes, int max_n, cudaStream_t s) {
+  const dim3 grid((max_n + 255) / 256, n_axes, 2);
+  k_chirps<<<grid, 256, 0, s>>>(axes_dev);
+  return cudaGetLastError();
+}
+
+// tw[i] = exp(-2 pi i i / L), rounded from double precision.
+__global__ void k_twiddles(float2* tw, int L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) {
+    double s, c;
+    sincospi(-2.0 * (double)i / (double)L, &s, &c);
+    tw[i] = make_float2((float)c, (float)s);
+  }
+}
+
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s) {
+  k_twiddles<<<(L + 255) / 256, 256, 0, s>>>(tw, L);
+  return cudaGetLastError();
+}
+
+}  // namespace sf
