@@ -1,0 +1,368 @@
+"""Benchmark: multi-view Shifted-Fresnel reconstruction throughput on GB300.
+
+Workload (paper scale, Section 3): one 1024 x 1024 float32 in-line hologram
+(4.65 um pitch, 632.8 nm) reconstructed into four complex64 1024 x 1024 views
+(z = 3, 5, 7, 10 cm; view pitch 4.65, 2, 1, 0.5 um; seeded offsets within
++-1 mm).  One step = one shifted_fresnel_execute call producing the four
+views.  Metric: views/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched with torch.distributed.run: every rank reconstructs its own
+hologram's views (views are independent; no data-path collective), timing is
+the max over ranks and the value is the total views of all ranks per second.
+"--impl reference" times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import glob
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "views/s (1024² holo → 1024² view, FP32) and % of HBM roofline vs plain path"
+UNIT = "views/s"
+WORKLOAD = ("1024^2 float32 in-line hologram -> 4 complex64 1024^2 views "
+            "(z = 3/5/7/10 cm, p1 = 4.65/2/1/0.5 um, offsets within +-1 mm), FFT length 2048 per axis")
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2, written between timed steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="minimum oracle time for cpu_baseline")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash():
+    """Hash of the CUDA sources; ncu traffic figures are only used while it matches."""
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1001_4309_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel_key)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes and flops (per step)
+# ----------------------------------------------------------------------------
+
+def algorithmic(views, lengths):
+    """Bytes and nominal FFT flops of the two passes for one step.
+
+    x pass: hologram read once (4 nx0 ny0) + workspace write (8 ny0 nx1 per view)
+    y pass: workspace read (8 ny0 nx1 per view) + complex view write (8 ny1 nx1 per view)
+    flops: 2 FFTs of 5 L log2 L per row; x pass ny0 rows, y pass nx1 rows per view.
+    """
+    v0 = views[0]
+    bx = 4 * v0["nx0"] * v0["ny0"] + sum(8 * v["ny0"] * v["nx1"] for v in views)
+    by = sum(8 * v["ny0"] * v["nx1"] + 8 * v["ny1"] * v["nx1"] for v in views)
+    fx = sum(v["ny0"] * 2 * 5 * lx * math.log2(lx) for v, (lx, ly) in zip(views, lengths))
+    fy = sum(v["nx1"] * 2 * 5 * ly * math.log2(ly) for v, (lx, ly) in zip(views, lengths))
+    return {"x": (bx, fx), "y": (by, fy)}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1001_4309_gb300 as P
+    from paper_1001_4309_gb300 import build as B
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    holo_np, views = synth.config_c2()
+    V = len(views)
+    sf = P.ShiftedFresnel(views, device=local)
+    lengths = [sf.sizes(i)[:2] for i in range(V)]
+    holo = torch.from_numpy(holo_np).to(dev)
+    outs = sf.alloc_outputs(field=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
+    step_start = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    step_end = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+
+    for evs in ev + [step_start, step_end]:
+        for e in evs:
+            e.record(stream)  # torch creates event handles lazily; force them before passing them down
+    for _ in range(a.warmup):
+        sf.execute(holo, outs)
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.15)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = P.shifted_fresnel_kernel_launches()
+    for k in range(a.steps):
+        flush.zero_()
+        P.shifted_fresnel_set_profile_events(sf.handle, [e.cuda_event for e in ev[k]])
+        step_start[k].record(stream)
+        sf.execute(holo, outs)
+        step_end[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = P.shifted_fresnel_kernel_launches() - launches0
+    P.shifted_fresnel_set_profile_events(sf.handle, None)
+    clk = clocks.stop()
+
+    step_ms = [step_start[k].elapsed_time(step_end[k]) for k in range(a.steps)]
+    x_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(a.steps)]
+    y_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(a.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / a.steps
+    value = world * V * a.steps / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (the longer pass), from live CUDA events
+    alg = algorithmic(views, lengths)
+    peaks, peak_kind = measured_peaks()
+    xm, ym = statistics.mean(x_ms), statistics.mean(y_ms)
+    dom, dom_ms = ("y", ym) if ym >= xm else ("x", xm)
+    dom_bytes, dom_flops = alg[dom]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks["hbm_gbs"])
+    kernel_key = f"k_pass<2048,{'PASS_Y' if dom == 'y' else 'PASS_X_REAL'}>"
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": ncu_traffic(kernel_key),
+                "kernel": kernel_key, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": round(dom_ms, 5)}
+    step_bytes = alg["x"][0] + alg["y"][0]
+    step_flops = alg["x"][1] + alg["y"][1]
+    passes = {p: {"ms": round(m, 5), "algorithmic_bytes": alg[p][0],
+                  "gbs": round(alg[p][0] / (m * 1e-3) / 1e9, 1),
+                  "nominal_tflops": round(alg[p][1] / (m * 1e-3) / 1e12, 2)}
+              for p, m in (("x", xm), ("y", ym))}
+
+    # end to end: host (pinned) hologram in, host (pinned) views out, through the C ABI
+    h_host = torch.from_numpy(holo_np.copy()).pin_memory()
+    o_host = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64).pin_memory() for v in views]
+    sptr = stream.cuda_stream
+    for _ in range(a.warmup):
+        P.shifted_fresnel_execute(sf.handle, h_host.data_ptr(), [o.data_ptr() for o in o_host], stream=sptr)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        P.shifted_fresnel_execute(sf.handle, h_host.data_ptr(), [o.data_ptr() for o in o_host], stream=sptr)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * V * a.steps / e2e_s, 1), "unit": UNIT,
+           "h2d_bytes_per_step": int(h_host.numel() * 4),
+           "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in o_host)),
+           "path": "shifted_fresnel_execute with pinned host buffers (library-staged copies), stream sync per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(holo_np, views, a.cpu_seconds)
+
+    sf.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded in-line Gabor holograms; the paper's real holograms are not available)",
+            "config": {"workload": WORKLOAD, "views_per_step": V, "fft_lengths": lengths[0],
+                       "outputs": "complex64 field per view", "l2": "flushed between timed steps (256 MiB write)",
+                       "inputs": "device-resident hologram and outputs",
+                       "parallelism": f"replicas x{world} (views independent per rank)"},
+            "roofline": roofline,
+            "step_hbm_frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak, 4),
+            "step_algorithmic_bytes": step_bytes,
+            "step_nominal_tflops": round(step_flops / (ms_per_step * 1e-3) / 1e12, 2),
+            "passes": passes,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(holo_np, views, min_seconds):
+    """The FP64 oracle as it stands, on all host cores: whole views of the same workload."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    n_views = 0
+    while True:
+        oracle.forward(holo_np, views[n_views % len(views)])
+        n_views += 1
+        if time.perf_counter() - t0 >= min_seconds or n_views >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(n_views / dt, 4), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n_views} whole 1024^2 views of the same 4-view workload (FP64 separable direct sum), "
+                      f"{dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 oracle on host cores
+# ----------------------------------------------------------------------------
+
+def run_reference(a):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    oracle.build()
+    holo_np, views = synth.config_c2()
+    cols_per_step = 32
+    nx1 = views[0]["nx1"]
+
+    def step(k):
+        v = views[k % len(views)]
+        c0 = (k * cols_per_step) % nx1
+        oracle.forward(holo_np, v, cols=(c0, c0 + cols_per_step))
+
+    for k in range(a.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        step(k)
+    dt = time.perf_counter() - t0
+    value = a.steps * cols_per_step / nx1 / dt
+    sample = (f"each step: {cols_per_step} of the {nx1} output columns of one view of the 4-view workload "
+              f"(cycling views), FP64 separable direct sum")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

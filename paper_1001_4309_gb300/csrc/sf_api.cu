@@ -29,7 +29,7 @@ constexpr int kMinFFT = 64;
 struct ViewState {
   sf_view v;
   AxisCoef ax[2];          // [0] = x, [1] = y; device pointers into the arena
-  float2* work = nullptr;  // [ny0][nx1] intermediate after the x pass
+  float2* work = nullptr;  // [nx1][ny0] intermediate after the x pass (transposed)
   float2* st_out = nullptr;  // host-I/O staging (lazily allocated)
   float* st_int = nullptr;
   float* st_ph = nullptr;
@@ -42,7 +42,7 @@ struct sf_plan_s {
   int nx0 = 0, ny0 = 0;
   bool in_complex = false;
   std::vector<ViewState> views;
-  std::map<int, float2*> tw;  // twiddle table per FFT length
+  std::map<int, float4*> tw;  // per-stage twiddle tables per FFT length
   void* arena = nullptr;
   void* st_holo = nullptr;
   std::vector<void*> staging;
@@ -221,7 +221,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     for (int a = 0; a < 2; ++a) {
       axis_coefficients(vs.v, a, vs.ax[a]);
       const AxisCoef& c = vs.ax[a];
-      if (!tw_off.count(c.L)) tw_off[c.L] = ar.take(sizeof(float2) * c.L);
+      if (!tw_off.count(c.L)) tw_off[c.L] = ar.take(sizeof(float4) * twiddle_entries(c.L));
       off_cin[2 * i + a] = ar.take(sizeof(float2) * c.n0);
       off_cout[2 * i + a] = ar.take(sizeof(float2) * c.n1);
       off_H[2 * i + a] = ar.take(sizeof(float2) * c.L);
@@ -235,7 +235,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     return SF_ERR_OOM;
   }
   char* base = static_cast<char*>(p->arena);
-  for (auto& kv : tw_off) p->tw[kv.first] = reinterpret_cast<float2*>(base + kv.second);
+  for (auto& kv : tw_off) p->tw[kv.first] = reinterpret_cast<float4*>(base + kv.second);
 
   // axes sorted by FFT length so each length's spectra are built by one launch
   std::vector<AxisCoef> axes;
@@ -257,8 +257,14 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   AxisCoef* axes_dev = reinterpret_cast<AxisCoef*>(base + off_axes);
 
   cudaError_t e = cudaMemcpyAsync(axes_dev, axes.data(), sizeof(AxisCoef) * axes.size(), cudaMemcpyHostToDevice, s);
-  for (auto& kv : p->tw)
-    if (e == cudaSuccess) { e = launch_twiddles(kv.second, kv.first, s); ++g_launches; }
+  std::vector<std::vector<float4>> tw_host;  // kept alive until the stream is synchronised below
+  for (auto& kv : p->tw) {
+    tw_host.emplace_back(twiddle_entries(kv.first));
+    build_twiddles(kv.first, tw_host.back().data());
+    if (e == cudaSuccess && !tw_host.back().empty())
+      e = cudaMemcpyAsync(kv.second, tw_host.back().data(), sizeof(float4) * tw_host.back().size(),
+                          cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) { e = launch_chirps(axes_dev, (int)axes.size(), max_n, s); ++g_launches; }
   for (size_t i = 0; i < axes.size() && e == cudaSuccess;) {
     size_t j = i;
@@ -371,14 +377,14 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
           d.dst = vs.work;
           d.rows = vs.v.ny0;
           d.src_ld = vs.v.nx0;
-          d.dst_ld = vs.v.nx1;
+          d.dst_ld = vs.v.ny0;
         } else {
           d.src = vs.work;
           d.dst = dout[vi];
           d.inten = dint[vi];
           d.phase = dph[vi];
           d.rows = vs.v.nx1;
-          d.src_ld = vs.v.nx1;
+          d.src_ld = vs.v.ny0;
           d.dst_ld = vs.v.nx1;
         }
         max_rows = std::max(max_rows, d.rows);

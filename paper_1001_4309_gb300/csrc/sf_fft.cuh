@@ -188,21 +188,37 @@ struct Stage {
   __device__ __forceinline__ static int nidx(int t, int u) { return (t + T * u) % M; }
 };
 
+// Per-stage twiddle tables.  Stage s (with M > 1) owns M * R / 2 float4
+// entries: entry q * M + n holds (W_{M'}^{n 2q}, W_{M'}^{n (2q+1)}), so a thread
+// fetches the R twiddles of butterfly n with R/2 16-byte loads that are
+// coalesced across consecutive n.  Stages are concatenated in order.
+constexpr int stage_tw_entries(int L, int E, int s) {
+  return (stage_mprev(L, E, s) / stage_radix(L, E, s)) > 1
+             ? (stage_mprev(L, E, s) / stage_radix(L, E, s)) * stage_radix(L, E, s) / 2
+             : 0;
+}
+constexpr int stage_tw_offset(int L, int E, int s) {
+  int o = 0;
+  for (int i = 0; i < s; ++i) o += stage_tw_entries(L, E, i);
+  return o;
+}
+constexpr int tw_table_entries(int L, int E) { return stage_tw_offset(L, E, stage_count(L, E)); }
+
 // Forward stage s on registers (values enter at the stage's read positions
 // and leave at the same positions with k in place of j).
 template <int L, int E, int S>
-__device__ __forceinline__ void stage_fwd(float2* v, int t, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stage_fwd(float2* v, int t, const float4* __restrict__ tw) {
   using St = Stage<L, E, S>;
 #pragma unroll
   for (int u = 0; u < St::NB; ++u) {
     dft<St::R, false>(v + u * St::R);
     if constexpr (St::M > 1) {
-      const int n = St::nidx(t, u);
+      const float4* tp = tw + stage_tw_offset(L, E, S) + St::nidx(t, u);
 #pragma unroll
-      for (int k = 1; k < St::R; ++k) {
-        // W_{M'}^{n k} = tw[n k L / M'] with tw[i] = exp(-2 pi i i / L)
-        const int e = (n * k * (L / St::MP)) & (L - 1);
-        v[u * St::R + k] = cmul(v[u * St::R + k], __ldg(tw + e));
+      for (int q = 0; q < St::R / 2; ++q) {
+        const float4 w = __ldg(tp + q * St::M);
+        if (q > 0) v[u * St::R + 2 * q] = cmul(v[u * St::R + 2 * q], make_float2(w.x, w.y));
+        v[u * St::R + 2 * q + 1] = cmul(v[u * St::R + 2 * q + 1], make_float2(w.z, w.w));
       }
     }
   }
@@ -210,16 +226,17 @@ __device__ __forceinline__ void stage_fwd(float2* v, int t, const float2* __rest
 
 // Adjoint of stage_fwd: conjugate twiddles, then the inverse radix-R DFT.
 template <int L, int E, int S>
-__device__ __forceinline__ void stage_inv(float2* v, int t, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stage_inv(float2* v, int t, const float4* __restrict__ tw) {
   using St = Stage<L, E, S>;
 #pragma unroll
   for (int u = 0; u < St::NB; ++u) {
     if constexpr (St::M > 1) {
-      const int n = St::nidx(t, u);
+      const float4* tp = tw + stage_tw_offset(L, E, S) + St::nidx(t, u);
 #pragma unroll
-      for (int k = 1; k < St::R; ++k) {
-        const int e = (n * k * (L / St::MP)) & (L - 1);
-        v[u * St::R + k] = cmulc(v[u * St::R + k], __ldg(tw + e));
+      for (int q = 0; q < St::R / 2; ++q) {
+        const float4 w = __ldg(tp + q * St::M);
+        if (q > 0) v[u * St::R + 2 * q] = cmulc(v[u * St::R + 2 * q], make_float2(w.x, w.y));
+        v[u * St::R + 2 * q + 1] = cmulc(v[u * St::R + 2 * q + 1], make_float2(w.z, w.w));
       }
     }
     dft<St::R, true>(v + u * St::R);
@@ -252,7 +269,7 @@ __device__ __forceinline__ void stage_load(float2* v, int t, const float2* buf) 
 // Output: the last stage's positions.  buf: this group's L-element row buffer.
 // Barrier: every thread of the CTA calls this the same number of times.
 template <int L, int E, int S = 0>
-__device__ __forceinline__ void fft_forward(float2* v, int t, float2* buf, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft_forward(float2* v, int t, float2* buf, const float4* __restrict__ tw) {
   constexpr int NS = stage_count(L, E);
   stage_fwd<L, E, S>(v, t, tw);
   if constexpr (S + 1 < NS) {
@@ -266,7 +283,7 @@ __device__ __forceinline__ void fft_forward(float2* v, int t, float2* buf, const
 
 // Adjoint network: from the last stage's positions back to v[j] = x[t + T j].
 template <int L, int E, int S = stage_count(L, E) - 1>
-__device__ __forceinline__ void fft_inverse(float2* v, int t, float2* buf, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft_inverse(float2* v, int t, float2* buf, const float4* __restrict__ tw) {
   stage_inv<L, E, S>(v, t, tw);
   if constexpr (S > 0) {
     __syncthreads();

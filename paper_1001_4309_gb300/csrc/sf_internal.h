@@ -12,9 +12,10 @@ constexpr int kE = 16;             // complex values per thread in the FFT netwo
 enum PassKind : int { PASS_X_REAL = 0, PASS_X_CPLX = 1, PASS_Y = 2 };
 
 // One separable half of one view (Section 2.2, steps 2-9 along one axis).
-//   X pass: src = hologram rows [rows = ny0][src_ld = nx0], dst = workspace [ny0][dst_ld = nx1]
-//   Y pass: src = workspace, column `row` read with stride src_ld = nx1;
-//           dst = view [ny1][nx1] written down column `row` (stride dst_ld = nx1)
+// Row r is read from src[r * src_ld + p] (p < n0); output p of row r goes to
+// dst[p * dst_ld + r] (p < n1).
+//   X pass: src = hologram [rows = ny0][src_ld = nx0], dst = workspace [nx1][dst_ld = ny0]
+//   Y pass: src = workspace [rows = nx1][src_ld = ny0], dst = view [ny1][dst_ld = nx1]
 struct PassDesc {
   const void* src;
   float2* dst;        // complex output (Y: may be null)
@@ -46,10 +47,11 @@ struct AxisCoef {
 };
 
 // launchers (one translation unit per FFT length family)
-cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float2* tw, cudaStream_t s);
-cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const float2* tw, cudaStream_t s);
+cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s);
+cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const float4* tw, cudaStream_t s);
 cudaError_t launch_chirps(const AxisCoef* axes_dev, int n_axes, int max_n, cudaStream_t s);
-cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+size_t twiddle_entries(int L);
+void build_twiddles(int L, float4* host_table);
 int pass_rows_per_cta(int L);
 int pass_threads(int L);
 size_t pass_smem_bytes(int L);

@@ -11,6 +11,9 @@
 //   crop to n1 outputs  x  output chirp of Eq. 2 (and 1/L)           (step 9)
 //   y pass only: complex view, |u1|^2 (Eq. 5) and phase              (step 10)
 //
+// The x pass reads hologram rows and writes the intermediate transposed,
+// [nx1][ny0]; the y pass then reads those rows (hologram columns) and writes
+// the view [ny1][nx1] transposed back.  Both passes load contiguous rows.
 // A CTA holds G = max(1, 256 / T) groups of T = L / 16 threads; group g
 // handles row blockIdx.x * G + g of pass blockIdx.y.
 #pragma once
@@ -27,6 +30,7 @@ struct PassShape {
   static constexpr int T = L / kE;
   static constexpr int G = (256 / T) > 0 ? (256 / T) : 1;
   static constexpr int THREADS = G * T;
+  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;  // caps registers at 128 per thread
   static constexpr size_t SMEM = sizeof(float2) * (size_t)G * L;
 };
 
@@ -43,16 +47,21 @@ __device__ __forceinline__ float phase_of(float2 u) {
   return p <= -3.14159265358979f ? 3.14159265358979f : p;  // (-pi, pi]
 }
 
+// Row pass.  Group g of the CTA transforms source row r = blockIdx.x * G + g,
+// read contiguously (src[r * src_ld + p], p < n0), and the n1 outputs are
+// written transposed (dst[p * dst_ld + r]) through a shared-memory tile so
+// the G rows of the CTA leave as G-element contiguous runs.
 template <int L, int KIND>
-__global__ void __launch_bounds__(PassShape<L>::THREADS)
-k_pass(const __grid_constant__ PassBatch b, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
+k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
   using Sh = PassShape<L>;
   constexpr int T = Sh::T, G = Sh::G, E = kE;
   extern __shared__ float2 smem[];
   const PassDesc& d = b.d[blockIdx.y];
-  if ((int)blockIdx.x * G >= d.rows) return;  // whole CTA past this pass's rows
+  const int row0 = blockIdx.x * G;
+  if (row0 >= d.rows) return;  // whole CTA past this pass's rows
   const int g = threadIdx.x / T, t = threadIdx.x % T;
-  const int row = blockIdx.x * G + g;
+  const int row = row0 + g;
   const bool valid = row < d.rows;
   float2* buf = smem + g * L;
 
@@ -66,11 +75,8 @@ k_pass(const __grid_constant__ PassBatch b, const float2* __restrict__ tw) {
       if constexpr (KIND == PASS_X_REAL) {
         const float x = __ldg(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + p);
         v[j] = cscale(c, x);
-      } else if constexpr (KIND == PASS_X_CPLX) {
-        const float2 x = __ldg(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + p);
-        v[j] = cmul(x, c);
       } else {
-        const float2 x = static_cast<const float2*>(d.src)[(size_t)p * d.src_ld + row];
+        const float2 x = __ldg(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + p);
         v[j] = cmul(x, c);
       }
     }
@@ -81,15 +87,24 @@ k_pass(const __grid_constant__ PassBatch b, const float2* __restrict__ tw) {
   for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(d.H + e * T + t));
   fft_inverse<L, E>(v, t, buf, tw);
 
+  // output chirp, then the transposed store through the tile [n1][G]
+  const int n1 = d.n1;
+  __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int p = t + T * j;
-    if (valid && p < d.n1) {
-      const float2 u = cmul(v[j], __ldg(d.cout + p));
+    if (p < n1) smem[p * G + g] = cmul(v[j], __ldg(d.cout + p));
+  }
+  __syncthreads();
+  const int rows_here = min(G, d.rows - row0);
+  for (int i = threadIdx.x; i < n1 * G; i += Sh::THREADS) {
+    const int p = i / G, gg = i - p * G;
+    if (gg < rows_here) {
+      const float2 u = smem[i];
+      const size_t o = (size_t)p * d.dst_ld + row0 + gg;
       if constexpr (KIND != PASS_Y) {
-        d.dst[(size_t)row * d.dst_ld + p] = u;
+        d.dst[o] = u;
       } else {
-        const size_t o = (size_t)p * d.dst_ld + row;
         if (d.dst) d.dst[o] = u;
         if (d.inten) d.inten[o] = fmaf(u.x, u.x, u.y * u.y);
         if (d.phase) d.phase[o] = phase_of(u);
@@ -103,7 +118,7 @@ k_pass(const __grid_constant__ PassBatch b, const float2* __restrict__ tw) {
 // p > L - n0, 0 elsewhere; pushed through the same forward network so it
 // lands in register order.
 template <int L>
-__global__ void __launch_bounds__(L / kE) k_hspec(const AxisCoef* __restrict__ axes, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(L / kE) k_hspec(const AxisCoef* __restrict__ axes, const float4* __restrict__ tw) {
   constexpr int T = L / kE, E = kE;
   extern __shared__ float2 smem[];
   const AxisCoef a = axes[blockIdx.x];
@@ -123,7 +138,7 @@ __global__ void __launch_bounds__(L / kE) k_hspec(const AxisCoef* __restrict__ a
 }
 
 template <int L>
-cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const float2* tw, cudaStream_t s) {
+cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s) {
   using Sh = PassShape<L>;
   const dim3 grid(grid_x, b.count), block(Sh::THREADS);
   auto go = [&](auto kern) {
@@ -143,7 +158,7 @@ cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const f
 }
 
 template <int L>
-cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float2* tw, cudaStream_t s) {
+cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float4* tw, cudaStream_t s) {
   constexpr size_t smem = sizeof(float2) * (size_t)L;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_hspec<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -154,11 +169,11 @@ cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float2* t
 }
 
 #define SF_INSTANTIATE_LENGTH(LL)                                                                      \
-  template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float2*, cudaStream_t); \
-  template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float2*, cudaStream_t);
+  template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float4*, cudaStream_t); \
+  template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float4*, cudaStream_t);
 
 #define SF_DECLARE_LENGTH(LL)                                                                                 \
-  extern template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float2*, cudaStream_t); \
-  extern template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float2*, cudaStream_t);
+  extern template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float4*, cudaStream_t); \
+  extern template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float4*, cudaStream_t);
 
 }  // namespace sf

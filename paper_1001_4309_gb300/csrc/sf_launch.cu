@@ -1,5 +1,7 @@
 // sf_launch.cu -- launch dispatch by FFT length, and the plan-time chirp and
 // twiddle kernels.
+#include <cmath>
+
 #include "sf_kernels.cuh"
 
 namespace sf {
@@ -33,12 +35,12 @@ bool fft_length_supported(int L) {
     default: break;                               \
   }
 
-cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float2* tw, cudaStream_t s) {
+cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s) {
   SF_LENGTH_SWITCH(L, return launch_pass_t<LL>(kind, b, grid_x, tw, s))
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const float2* tw, cudaStream_t s) {
+cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const float4* tw, cudaStream_t s) {
   SF_LENGTH_SWITCH(L, return launch_hspec_t<LL>(axes_dev, n_axes, tw, s))
   return cudaErrorInvalidValue;
 }
@@ -79,19 +81,29 @@ cudaError_t launch_chirps(const AxisCoef* axes_dev, int n_axes, int max_n, cudaS
   return cudaGetLastError();
 }
 
-// tw[i] = exp(-2 pi i i / L), rounded from double precision.
-__global__ void k_twiddles(float2* tw, int L) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < L) {
-    double s, c;
-    sincospi(-2.0 * (double)i / (double)L, &s, &c);
-    tw[i] = make_float2((float)c, (float)s);
-  }
-}
+size_t twiddle_entries(int L) { return (size_t)tw_table_entries(L, kE); }
 
-cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s) {
-  k_twiddles<<<(L + 255) / 256, 256, 0, s>>>(tw, L);
-  return cudaGetLastError();
+// Per-stage twiddle tables (layout described at stage_tw_entries), built in
+// double precision on the host and rounded to float.
+void build_twiddles(int L, float4* tab) {
+  const double two_pi = 6.283185307179586476925286766559;
+  auto w = [&](long e, float& re, float& im) {
+    const double a = two_pi * (double)(e % L) / (double)L;
+    re = (float)std::cos(a);
+    im = (float)-std::sin(a);
+  };
+  for (int st = 0; st < stage_count(L, kE); ++st) {
+    const int MP = stage_mprev(L, kE, st), R = stage_radix(L, kE, st), M = MP / R;
+    if (M <= 1) continue;
+    float4* base = tab + stage_tw_offset(L, kE, st);
+    for (int q = 0; q < R / 2; ++q)
+      for (int n = 0; n < M; ++n) {
+        float4 f;
+        w((long)n * (2 * q) * (L / MP), f.x, f.y);
+        w((long)n * (2 * q + 1) * (L / MP), f.z, f.w);
+        base[q * M + n] = f;
+      }
+  }
 }
 
 }  // namespace sf
