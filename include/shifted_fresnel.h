@@ -147,6 +147,49 @@ int shifted_fresnel_plan_query(sf_plan plan, int view, int32_t* lx, int32_t* ly,
 int shifted_fresnel_set_profile_events(sf_plan plan, void* const* events, int n_events);
 
 /*
+ * shifted_fresnel_execute_static -- reconstruct one view without allocating.
+ *
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot allocate device memory while they run -- for example a plugin
+ * whose host application owns every device allocation, or an acquisition
+ * loop whose memory is fixed before the first frame -- and therefore cannot
+ * create a plan (shifted_fresnel_plan calls cudaMalloc).
+ *
+ * It computes the same view as a one-view plan's shifted_fresnel_execute,
+ * on the calling thread's current device, using one fixed device array of
+ * SF_STATIC_SCRATCH_BYTES that the library declares at file scope (every GPU
+ * that loads the library holds it until the process exits).  Nothing here
+ * calls cudaMalloc, cudaFree or an allocating library routine.
+ *
+ *   view       one view (copied); the hologram size and flags are its own.
+ *   holo       device pointer, hologram [ny0][nx0] float32 (complex64 with
+ *              SF_IN_COMPLEX).
+ *   view_out   device pointer to a complex64 [ny1][nx1] view, or NULL.
+ *   intensity  device pointer to a float32 [ny1][nx1] |u1|^2 image, or NULL.
+ *   phase      device pointer to a float32 [ny1][nx1] phase image, or NULL.
+ *   stream     stream to run on.
+ * At least one output must be non-NULL.  Limits: nx0 + nx1 - 1 and
+ * ny0 + ny1 - 1 at most SF_STATIC_MAX_FFT_LENGTH after rounding up to the
+ * FFT length, and nx1 * ny0 at most SF_STATIC_MAX_WORKSPACE_ELEMS; larger
+ * views return SF_ERR_UNSUPPORTED_SIZE.  Host buffers cannot be staged
+ * without allocating and return SF_ERR_INVALID_ARG.
+ *
+ * The array is shared by all calls on a device and keeps the last call's
+ * contents; each call rewrites every part it reads, so nothing has to be
+ * cleared, but calls that overlap on the GPU (other streams, other host
+ * threads on the same device) race and corrupt each other's results.  The
+ * first call on each device looks up the array's device address, which may
+ * load the module: make that first call before any stream capture.
+ * Errors: SF_ERR_INVALID_ARG, SF_ERR_UNSUPPORTED_SIZE, SF_ERR_DEVICE_MISMATCH,
+ * SF_ERR_CUDA.
+ */
+#define SF_STATIC_MAX_FFT_LENGTH 2048
+#define SF_STATIC_MAX_WORKSPACE_ELEMS (1u << 20) /* 8 MiB of complex64 intermediate */
+#define SF_STATIC_SCRATCH_BYTES ((size_t)(8u << 20) + (size_t)(256u << 10))
+int shifted_fresnel_execute_static(const sf_view* view, const void* holo, void* view_out,
+                                   float* intensity, float* phase, void* stream);
+
+/*
  * shifted_fresnel_kernel_launches -- number of CUDA kernels this library has
  * launched in this process so far (all plans, all devices).
  */

@@ -12,6 +12,7 @@ from .binding import (  # noqa: F401
     make_view,
     shifted_fresnel_plan,
     shifted_fresnel_execute,
+    shifted_fresnel_execute_static,
     shifted_fresnel_destroy,
     shifted_fresnel_strerror,
     shifted_fresnel_plan_query,

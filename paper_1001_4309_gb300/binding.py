@@ -77,6 +77,8 @@ def load():
     lib.shifted_fresnel_plan_query.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t)]
     lib.shifted_fresnel_kernel_launches.restype = ctypes.c_uint64
+    lib.shifted_fresnel_execute_static.argtypes = [ctypes.POINTER(sf_view), vp, vp, vp, vp, vp]
+    lib.shifted_fresnel_execute_static.restype = ctypes.c_int
     lib.shifted_fresnel_set_profile_events.argtypes = [vp, pp, ctypes.c_int]
     lib.shifted_fresnel_set_profile_events.restype = ctypes.c_int
     for f in ("shifted_fresnel_plan", "shifted_fresnel_execute", "shifted_fresnel_destroy",
@@ -128,6 +130,22 @@ def shifted_fresnel_execute(plan, holo_ptr, view_out=None, intensity=None, phase
                                         ctypes.c_void_p(stream) if stream else None)
     if check and rc != SF_OK:
         raise SFError(rc, "shifted_fresnel_execute")
+    return rc
+
+
+def shifted_fresnel_execute_static(view, holo_ptr, view_out=None, intensity=None, phase=None, stream=0,
+                                   check=True):
+    """One view without a plan and without allocating (device pointers as ints, or None).
+
+    For callers that cannot allocate device memory while running; the
+    library's fixed scratch array is shared by all calls on a device.
+    """
+    v = make_view(view)
+    p = lambda x: ctypes.c_void_p(x) if x else None  # noqa: E731
+    rc = load().shifted_fresnel_execute_static(ctypes.byref(v), p(holo_ptr), p(view_out), p(intensity), p(phase),
+                                               ctypes.c_void_p(stream) if stream else None)
+    if check and rc != SF_OK:
+        raise SFError(rc, "shifted_fresnel_execute_static")
     return rc
 
 

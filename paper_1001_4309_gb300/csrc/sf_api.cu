@@ -49,7 +49,7 @@ struct sf_plan_s {
   cudaEvent_t prof[3] = {nullptr, nullptr, nullptr};
 };
 
-namespace {
+namespace sf {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
 
@@ -110,6 +110,12 @@ void axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
   a.out0 = to_fx(c0);
   a.h2 = to_fx(S);
 }
+
+void count_launches(uint64_t n) { g_launches += n; }
+
+}  // namespace sf
+
+namespace {
 
 struct Arena {
   size_t off = 0;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "shifted_fresnel.h"
+
 namespace sf {
 
 constexpr int kMaxPassBatch = 16;  // (view, axis) passes per launch
@@ -45,6 +47,11 @@ struct AxisCoef {
   float2* cout;               // device, n1
   float2* H;                  // device, L (register order)
 };
+
+// host helpers shared by the entry points (defined in sf_api.cu)
+int validate_view(const sf_view& v);
+void axis_coefficients(const sf_view& v, int axis, AxisCoef& a);
+void count_launches(uint64_t n);
 
 // launchers (one translation unit per FFT length family)
 cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s);
