@@ -17,9 +17,9 @@
 // in reverse order, conjugated twiddles applied before an inverse radix-R DFT)
 // returns L times the circular convolution in natural order.
 //
-// Between stages the values move through a shared-memory row buffer with an
-// XOR swizzle on the low four position bits, which keeps 8-byte accesses of
-// 16 consecutive lanes on distinct bank pairs for every stage pattern used.
+// Between stages the values move through a shared-memory row buffer padded
+// by one slot every 16 positions, which keeps the 8-byte accesses of each
+// half warp on distinct bank pairs for every stage pattern at L >= 256.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,8 +28,27 @@
 namespace sf {
 
 // ---------------------------------------------------------------- complex ops
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract are one packed f32x2 instruction each (sm_100+);
+// products by +-i are folded into scalar adds (add_w4 / sub_w4) instead of
+// being formed as lane-swapped operands.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 ta, tb, tr;\n\tmov.b64 ta, {%2, %3};\n\tmov.b64 tb, {%4, %5};\n\t"
+      "sub.rn.f32x2 tr, ta, tb;\n\tmov.b64 {%0, %1}, tr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+// a + W_4 b and a - W_4 b with W_4 = -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 add_w4(float2 a, float2 b) {
+  return INV ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 sub_w4(float2 a, float2 b) {
+  return INV ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -85,12 +104,12 @@ __device__ __forceinline__ void dft2(float2& a, float2& b) {
 
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  float2 s0 = cadd(a0, a2), d0 = csub(a0, a2);
-  float2 s1 = cadd(a1, a3), d1 = mul_w4<INV>(csub(a1, a3));
+  const float2 s0 = cadd(a0, a2), d0 = csub(a0, a2);
+  const float2 s1 = cadd(a1, a3), e1 = csub(a1, a3);
   a0 = cadd(s0, s1);
   a2 = csub(s0, s1);
-  a1 = cadd(d0, d1);
-  a3 = csub(d0, d1);
+  a1 = add_w4<INV>(d0, e1);
+  a3 = sub_w4<INV>(d0, e1);
 }
 
 template <bool INV>
@@ -101,11 +120,10 @@ __device__ __forceinline__ void dft8(float2* x) {
   dft4<INV>(e0, e1, e2, e3);
   dft4<INV>(o0, o1, o2, o3);
   o1 = mul_w16<INV, 2>(o1);
-  o2 = mul_w16<INV, 4>(o2);
   o3 = mul_w16<INV, 6>(o3);
   x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
   x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
-  x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+  x[2] = add_w4<INV>(e2, o2); x[6] = sub_w4<INV>(e2, o2);  // o2 carries W_8^2 = W_4
   x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
 }
 
@@ -124,15 +142,24 @@ __device__ __forceinline__ void dft16(float2* x) {
   b[4 * 1 + 2] = mul_w16<INV, 2>(b[4 * 1 + 2]);
   b[4 * 1 + 3] = mul_w16<INV, 3>(b[4 * 1 + 3]);
   b[4 * 2 + 1] = mul_w16<INV, 2>(b[4 * 2 + 1]);
-  b[4 * 2 + 2] = mul_w16<INV, 4>(b[4 * 2 + 2]);
   b[4 * 2 + 3] = mul_w16<INV, 6>(b[4 * 2 + 3]);
   b[4 * 3 + 1] = mul_w16<INV, 3>(b[4 * 3 + 1]);
   b[4 * 3 + 2] = mul_w16<INV, 6>(b[4 * 3 + 2]);
   b[4 * 3 + 3] = mul_w16<INV, 9>(b[4 * 3 + 3]);
+  // b[4 * 2 + 2] carries W_16^4 = W_4, folded into the k1 = 2 butterfly below
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
     float2 a0 = b[k1], a1 = b[4 + k1], a2 = b[8 + k1], a3 = b[12 + k1];
-    dft4<INV>(a0, a1, a2, a3);  // over j2 -> k2
+    if (k1 == 2) {
+      const float2 s0 = add_w4<INV>(a0, a2), d0 = sub_w4<INV>(a0, a2);
+      const float2 s1 = cadd(a1, a3), e1 = csub(a1, a3);
+      a0 = cadd(s0, s1);
+      a2 = csub(s0, s1);
+      a1 = add_w4<INV>(d0, e1);
+      a3 = sub_w4<INV>(d0, e1);
+    } else {
+      dft4<INV>(a0, a1, a2, a3);  // over j2 -> k2
+    }
     x[k1 + 0] = a0; x[k1 + 4] = a1; x[k1 + 8] = a2; x[k1 + 12] = a3;
   }
 }
@@ -169,8 +196,12 @@ constexpr int stage_radix(int L, int E, int s) {
   return stage_mprev(L, E, s) > E ? E : stage_mprev(L, E, s);
 }
 
-// Shared-memory swizzle of a row position (8-byte elements).
-__device__ __forceinline__ int swz(int p) { return p ^ ((p >> 4) & 15); }
+// Shared-memory address of a row position (8-byte elements): one pad slot
+// every 16 positions.  Stage positions are sums of disjoint power-of-two bit
+// fields, over which phys is additive, so every access is a per-thread base
+// plus a compile-time offset.
+__host__ __device__ constexpr int phys(int p) { return p + (p >> 4); }
+__host__ __device__ constexpr int buf_elems(int L) { return phys(L - 1) + 1; }
 
 // Position of element j of butterfly u (u < E / R) of thread t in stage s.
 template <int L, int E, int S>
@@ -248,9 +279,9 @@ __device__ __forceinline__ void stage_store(const float2* v, int t, float2* buf)
   using St = Stage<L, E, S>;
 #pragma unroll
   for (int u = 0; u < St::NB; ++u) {
-    const int b0 = St::base(t, u);
+    const int b0 = phys(St::base(t, u));
 #pragma unroll
-    for (int k = 0; k < St::R; ++k) buf[swz(b0 + k * St::M)] = v[u * St::R + k];
+    for (int k = 0; k < St::R; ++k) buf[b0 + phys(k * St::M)] = v[u * St::R + k];
   }
 }
 
@@ -259,38 +290,51 @@ __device__ __forceinline__ void stage_load(float2* v, int t, const float2* buf) 
   using St = Stage<L, E, S>;
 #pragma unroll
   for (int u = 0; u < St::NB; ++u) {
-    const int b0 = St::base(t, u);
+    const int b0 = phys(St::base(t, u));
 #pragma unroll
-    for (int k = 0; k < St::R; ++k) v[u * St::R + k] = buf[swz(b0 + k * St::M)];
+    for (int k = 0; k < St::R; ++k) v[u * St::R + k] = buf[b0 + phys(k * St::M)];
+  }
+}
+
+// Barrier over the T threads that share one row buffer: a named barrier per
+// thread group when the group is whole warps (so the groups of a CTA do not
+// wait for each other), the CTA barrier otherwise.  Every thread of the
+// group calls it the same number of times.
+template <int T>
+__device__ __forceinline__ void group_sync(int g) {
+  if constexpr (T >= 32 && T % 32 == 0) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(T) : "memory");
+  } else {
+    __syncthreads();
   }
 }
 
 // Full forward network.  Input: v[j] = x[t + T j] (stage 0 layout).
-// Output: the last stage's positions.  buf: this group's L-element row buffer.
-// Barrier: every thread of the CTA calls this the same number of times.
+// Output: the last stage's positions.  buf: this group's row buffer
+// (buf_elems(L) elements); g: the group's index in the CTA.
 template <int L, int E, int S = 0>
-__device__ __forceinline__ void fft_forward(float2* v, int t, float2* buf, const float4* __restrict__ tw) {
+__device__ __forceinline__ void fft_forward(float2* v, int t, int g, float2* buf, const float4* __restrict__ tw) {
   constexpr int NS = stage_count(L, E);
   stage_fwd<L, E, S>(v, t, tw);
   if constexpr (S + 1 < NS) {
-    __syncthreads();  // previous readers of buf are done
+    group_sync<L / E>(g);  // previous readers of buf are done
     stage_store<L, E, S>(v, t, buf);
-    __syncthreads();
+    group_sync<L / E>(g);
     stage_load<L, E, S + 1>(v, t, buf);
-    fft_forward<L, E, S + 1>(v, t, buf, tw);
+    fft_forward<L, E, S + 1>(v, t, g, buf, tw);
   }
 }
 
 // Adjoint network: from the last stage's positions back to v[j] = x[t + T j].
 template <int L, int E, int S = stage_count(L, E) - 1>
-__device__ __forceinline__ void fft_inverse(float2* v, int t, float2* buf, const float4* __restrict__ tw) {
+__device__ __forceinline__ void fft_inverse(float2* v, int t, int g, float2* buf, const float4* __restrict__ tw) {
   stage_inv<L, E, S>(v, t, tw);
   if constexpr (S > 0) {
-    __syncthreads();
+    group_sync<L / E>(g);
     stage_store<L, E, S>(v, t, buf);
-    __syncthreads();
+    group_sync<L / E>(g);
     stage_load<L, E, S - 1>(v, t, buf);
-    fft_inverse<L, E, S - 1>(v, t, buf, tw);
+    fft_inverse<L, E, S - 1>(v, t, g, buf, tw);
   }
 }
 

@@ -31,7 +31,7 @@ struct PassShape {
   static constexpr int G = (256 / T) > 0 ? (256 / T) : 1;
   static constexpr int THREADS = G * T;
   static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;  // caps registers at 128 per thread
-  static constexpr size_t SMEM = sizeof(float2) * (size_t)G * L;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)G * buf_elems(L);
 };
 
 // exp(i pi ph / 2^63) from a 64-bit fixed-point phase (full scale 2^64 = 2 pi).
@@ -63,7 +63,7 @@ k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   const int row = row0 + g;
   const bool valid = row < d.rows;
-  float2* buf = smem + g * L;
+  float2* buf = smem + g * buf_elems(L);
 
   float2 v[E];
 #pragma unroll
@@ -82,10 +82,10 @@ k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
     }
   }
 
-  fft_forward<L, E>(v, t, buf, tw);
+  fft_forward<L, E>(v, t, g, buf, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(d.H + e * T + t));
-  fft_inverse<L, E>(v, t, buf, tw);
+  fft_inverse<L, E>(v, t, g, buf, tw);
 
   // output chirp, then the transposed store through the tile [n1][G]
   const int n1 = d.n1;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(L / kE) k_hspec(const AxisCoef* __restrict__ a
     else if (p > L - a.n0) dd = p - L;
     v[j] = dd == INT_MIN ? make_float2(0.f, 0.f) : expi_fx(a.h2 * (uint64_t)((int64_t)dd * dd));
   }
-  fft_forward<L, E>(v, t, smem, tw);
+  fft_forward<L, E>(v, t, 0, smem, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) a.H[e * T + t] = v[e];
 }
@@ -159,7 +159,7 @@ cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const f
 
 template <int L>
 cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float4* tw, cudaStream_t s) {
-  constexpr size_t smem = sizeof(float2) * (size_t)L;
+  constexpr size_t smem = sizeof(float2) * (size_t)buf_elems(L);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_hspec<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

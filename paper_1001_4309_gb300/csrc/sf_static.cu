@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(L / kE) k_static_hspec(AxisCoef a, const float
     else if (p > L - a.n0) dd = p - L;
     v[j] = dd == INT_MIN ? make_float2(0.f, 0.f) : expi_fx(a.h2 * (uint64_t)((int64_t)dd * dd));
   }
-  fft_forward<L, E>(v, t, smem, tw);
+  fft_forward<L, E>(v, t, 0, smem, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) a.H[e * T + t] = v[e];
 }
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(L / kE) k_static_hspec(AxisCoef a, const float
 cudaError_t launch_static_hspec(const AxisCoef& a, const float4* tw, cudaStream_t s) {
   switch (a.L) {
 #define SF_STATIC_HSPEC_CASE(LL) \
-  case LL: k_static_hspec<LL><<<1, LL / kE, sizeof(float2) * LL, s>>>(a, tw); return cudaGetLastError();
+  case LL: k_static_hspec<LL><<<1, LL / kE, sizeof(float2) * buf_elems(LL), s>>>(a, tw); return cudaGetLastError();
     SF_STATIC_HSPEC_CASE(64)
     SF_STATIC_HSPEC_CASE(128)
     SF_STATIC_HSPEC_CASE(256)
