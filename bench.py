@@ -273,6 +273,8 @@ def run_ours(a):
            "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in o_host)),
            "path": "shifted_fresnel_execute with pinned host buffers (library-staged copies), stream sync per step"}
 
+    plain = plain_path(holo, views, outs, flush, stream, a, step_bytes, float(peaks["hbm_gbs"]), value / world)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(holo_np, views, a.cpu_seconds)
@@ -293,11 +295,43 @@ def run_ours(a):
             "step_algorithmic_bytes": step_bytes,
             "step_nominal_tflops": round(step_flops / (ms_per_step * 1e-3) / 1e12, 2),
             "passes": passes,
+            "plain_path": plain,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def plain_path(holo, views, outs, flush, stream, a, step_bytes, hbm_peak, ours_per_gpu):
+    """The paper's steps 2-10 with cuFFT on the 2N x 2N grid, same workload and timing rules."""
+    import torch
+    from paper_1001_4309_gb300 import build as B
+    from paper_1001_4309_gb300.plain import PlainPath
+    B.build_plain()
+    pp = PlainPath(views, device=holo.device.index)
+    fields = outs["field"]
+    for _ in range(a.warmup):
+        pp.execute(holo, fields)
+        flush.zero_()
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.execute(holo, fields)
+        e1.record(stream)
+        t.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in t) / a.steps
+    pp.close()
+    v = len(views) / (ms * 1e-3)
+    return {"value": round(v, 1), "unit": UNIT, "ms_per_step": round(ms, 5),
+            "step_hbm_frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+            "speedup_of_fused_path": round(ours_per_gpu / v, 2),
+            "what": "paper steps 2-10 per view: pad + chirp kernels, cuFFT 2D C2C forward of the "
+                    "2048^2 grid and of h, spectrum multiply, inverse 2D FFT, crop + C1; same 4-view step"}
 
 
 def cpu_baseline(holo_np, views, min_seconds):

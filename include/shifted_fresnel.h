@@ -118,6 +118,39 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
 int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out,
                             float* const* intensity, float* const* phase, void* stream);
 
+/*
+ * shifted_fresnel_adjoint -- back-propagate view gradients to the hologram
+ * plane, and optionally differentiate with respect to each view's z.
+ *
+ * The forward map of view v is the linear operator A_v of Eqs. 1-4
+ * (Section 2.1).  With g_v the gradient of a real loss with respect to the
+ * view field in the convention g = 2 dL/d(conj u1) (PyTorch's), this
+ * computes
+ *   grad_holo = sum_v A_v^H g_v                   (complex64 [ny0][nx0])
+ *   grad_z[v] = Re sum conj(g_v) d(u1_v)/dz        (double, per view)
+ * A^H of each axis is itself a Bluestein pass (conjugate chirps, kernel
+ * conj(h), lengths swapped); the z-derivative uses two further adjoint
+ * transforms, of x1 g and y1 g, and a recomputed view field.  The paper has
+ * no adjoint; this is the conjugate transpose of its operator.
+ *
+ *   holo       the hologram / object field given to execute (float32 or
+ *              complex64 per SF_IN_COMPLEX); required when grad_z != NULL,
+ *              otherwise ignored (may be NULL).
+ *   grad_view  n_views pointers to complex64 [ny1][nx1] gradients; NULL
+ *              entries contribute nothing (and get grad_z = 0).
+ *   grad_holo  complex64 [ny0][nx0] output (overwritten), or NULL.
+ *   grad_z     n_views doubles, or NULL.  At least one of grad_holo and
+ *              grad_z must be non-NULL.
+ *   stream     stream to run on.
+ * Any buffer may be device or host memory (host buffers are staged).  The
+ * first call allocates the plan's adjoint scratch (about
+ * 8 * (3 nx0 ny1 + 4 nx0 ny0 + 4 nx1 ny1) bytes); calls on one plan must
+ * not overlap with each other or with execute on another stream.
+ * Errors: SF_ERR_INVALID_ARG, SF_ERR_DEVICE_MISMATCH, SF_ERR_OOM, SF_ERR_CUDA.
+ */
+int shifted_fresnel_adjoint(sf_plan plan, const void* holo, const void* const* grad_view, void* grad_holo,
+                            double* grad_z, void* stream);
+
 /* shifted_fresnel_destroy -- synchronise the plan's device and free everything it owns. */
 int shifted_fresnel_destroy(sf_plan plan);
 

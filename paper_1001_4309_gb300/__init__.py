@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     shifted_fresnel_execute,
     shifted_fresnel_execute_static,
     shifted_fresnel_destroy,
+    shifted_fresnel_adjoint,
     shifted_fresnel_strerror,
     shifted_fresnel_plan_query,
     shifted_fresnel_kernel_launches,

@@ -1,0 +1,97 @@
+"""Differentiable Shifted-Fresnel views and gradient-descent phase retrieval.
+
+``ShiftedFresnelFunction`` wraps a plan as a ``torch.autograd.Function``:
+the forward pass is ``shifted_fresnel_execute`` and the backward pass is
+``shifted_fresnel_adjoint``, which returns the gradient with respect to the
+complex object field (sum over views of A_v^H g_v) and, when asked, with
+respect to each view's z.  The z values are part of the plan (the chirps and
+kernel spectra depend on them); the ``z`` tensor passed in is the plan's z,
+used only as the handle that receives dL/dz.
+
+``phase_retrieval`` fits a complex object to measured view intensities
+(twin-image-free in-line holography from several depths) by minimising
+sum_v || |A_v u|^2 - I_v ||^2 with Adam.
+"""
+
+from __future__ import annotations
+
+import torch
+
+from .binding import ShiftedFresnel, shifted_fresnel_adjoint, SF_IN_COMPLEX
+
+
+class ShiftedFresnelFunction(torch.autograd.Function):
+    """views = ShiftedFresnelFunction.apply(u0, z, sf) -> tuple of complex64 view fields."""
+
+    @staticmethod
+    def forward(ctx, u0, z, sf):
+        if not (sf.views[0].get("flags", 0) & SF_IN_COMPLEX):
+            raise ValueError("the plan must take a complex object (SF_IN_COMPLEX)")
+        zs = [v["z"] for v in sf.views]
+        if z is not None and (z.numel() != len(zs) or
+                              any(abs(float(a) - b) > 1e-12 * abs(b) for a, b in zip(z.detach().cpu(), zs))):
+            raise ValueError("z must hold the plan's per-view distances")
+        u0c = u0.contiguous()
+        outs = sf.reconstruct(u0c, field=True)
+        ctx.sf = sf
+        ctx.save_for_backward(u0c)
+        return tuple(outs["field"])
+
+    @staticmethod
+    def backward(ctx, *grads):
+        (u0,) = ctx.saved_tensors
+        sf = ctx.sf
+        need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_u or need_z):
+            return None, None, None
+        gs = [g.contiguous() if g is not None else None for g in grads]
+        grad_u = torch.empty_like(u0) if need_u else None
+        grad_z = torch.zeros(len(sf.views), dtype=torch.float64, device=u0.device) if need_z else None
+        shifted_fresnel_adjoint(sf.handle, u0.data_ptr() if need_z else None,
+                                [g.data_ptr() if g is not None else None for g in gs],
+                                grad_u.data_ptr() if need_u else None,
+                                grad_z.data_ptr() if need_z else None,
+                                stream=torch.cuda.current_stream(u0.device).cuda_stream)
+        return grad_u, grad_z, None
+
+
+def views(u0, sf, z=None):
+    """Differentiable views of a complex object field through plan ``sf``."""
+    return ShiftedFresnelFunction.apply(u0, z, sf)
+
+
+def intensity_loss(u0, sf, intensities, z=None):
+    """sum_v || |A_v u0|^2 - I_v ||^2 (the loss of the multi-depth phase retrieval)."""
+    outs = views(u0, sf, z)
+    return sum(((o.real ** 2 + o.imag ** 2 - I) ** 2).sum() for o, I in zip(outs, intensities))
+
+
+def phase_retrieval(sf, intensities, n_iter=200, u_init=None, lr=0.05, recompute=False, callback=None):
+    """Fit a complex object to measured view intensities by gradient descent (Adam).
+
+    ``recompute=True`` keeps no view fields between forward and backward
+    (they are recomputed in backward through torch.utils.checkpoint), for
+    memory-bound view sets.  Returns (u, losses).
+    """
+    v0 = sf.views[0]
+    if u_init is None:
+        u_init = torch.ones((v0["ny0"], v0["nx0"]), dtype=torch.complex64, device=sf.device)
+    u = u_init.detach().clone().requires_grad_(True)
+    opt = torch.optim.Adam([u], lr=lr)
+    losses = []
+    for it in range(n_iter):
+        opt.zero_grad(set_to_none=True)
+        if recompute:
+            from torch.utils.checkpoint import checkpoint
+            loss = checkpoint(lambda x: intensity_loss(x, sf, intensities), u, use_reentrant=False)
+        else:
+            loss = intensity_loss(u, sf, intensities)
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+        if callback is not None:
+            callback(it, u, loss)
+    return u.detach(), [float(x) for x in torch.stack(losses).cpu()]
+
+
+__all__ = ["ShiftedFresnelFunction", "views", "intensity_loss", "phase_retrieval", "ShiftedFresnel"]

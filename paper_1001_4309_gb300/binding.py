@@ -79,6 +79,8 @@ def load():
     lib.shifted_fresnel_kernel_launches.restype = ctypes.c_uint64
     lib.shifted_fresnel_execute_static.argtypes = [ctypes.POINTER(sf_view), vp, vp, vp, vp, vp]
     lib.shifted_fresnel_execute_static.restype = ctypes.c_int
+    lib.shifted_fresnel_adjoint.argtypes = [vp, vp, pp, vp, vp, vp]
+    lib.shifted_fresnel_adjoint.restype = ctypes.c_int
     lib.shifted_fresnel_set_profile_events.argtypes = [vp, pp, ctypes.c_int]
     lib.shifted_fresnel_set_profile_events.restype = ctypes.c_int
     for f in ("shifted_fresnel_plan", "shifted_fresnel_execute", "shifted_fresnel_destroy",
@@ -146,6 +148,16 @@ def shifted_fresnel_execute_static(view, holo_ptr, view_out=None, intensity=None
                                                ctypes.c_void_p(stream) if stream else None)
     if check and rc != SF_OK:
         raise SFError(rc, "shifted_fresnel_execute_static")
+    return rc
+
+
+def shifted_fresnel_adjoint(plan, holo_ptr, grad_view, grad_holo=None, grad_z=None, stream=0, check=True):
+    """grad_holo = sum_v A_v^H g_v and grad_z[v] = Re sum conj(g_v) du1_v/dz (pointers as ints or None)."""
+    p = lambda x: ctypes.c_void_p(x) if x else None  # noqa: E731
+    rc = load().shifted_fresnel_adjoint(plan, p(holo_ptr), _ptr_array(list(grad_view)), p(grad_holo), p(grad_z),
+                                        ctypes.c_void_p(stream) if stream else None)
+    if check and rc != SF_OK:
+        raise SFError(rc, "shifted_fresnel_adjoint")
     return rc
 
 
@@ -222,6 +234,19 @@ class ShiftedFresnel:
     def reconstruct(self, holo, field=True, intensity=False, phase=False):
         outs = self.alloc_outputs(field, intensity, phase)
         return self.execute(holo, outs)
+
+    def adjoint(self, grad_views, holo=None, grad_holo=None, grad_z=None, stream=None):
+        """grad_holo (complex64 [ny0][nx0]) and grad_z (float64 [n_views]) from per-view gradients."""
+        t = self.torch
+        v0 = self.views[0]
+        if grad_holo is None:
+            grad_holo = t.empty((v0["ny0"], v0["nx0"]), dtype=t.complex64, device=self.device)
+        s = stream if stream is not None else t.cuda.current_stream(self.device).cuda_stream
+        shifted_fresnel_adjoint(self.handle, holo.data_ptr() if holo is not None else None,
+                                [g.data_ptr() if g is not None else None for g in grad_views],
+                                grad_holo.data_ptr() if grad_holo is not False else None,
+                                grad_z.data_ptr() if grad_z is not None else None, stream=s)
+        return grad_holo, grad_z
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,8 +1,13 @@
-"""Build the sm_103a CUDA library ``libshifted_fresnel.so`` in-tree.
+"""Build the sm_103a CUDA libraries in-tree.
 
-Each ``csrc/*.cu`` translation unit is compiled in parallel with nvcc for
-``arch=compute_103a,code=sm_103a`` and linked into
-``paper_1001_4309_gb300/_build/libshifted_fresnel.so`` (static CUDA runtime).
+* ``libshifted_fresnel.so`` -- the product library: each ``csrc/*.cu``
+  translation unit is compiled in parallel with nvcc for
+  ``arch=compute_103a,code=sm_103a`` and linked with the static CUDA runtime.
+* ``libsf_plain.so`` -- the paper's per-view procedure with cuFFT
+  (``csrc_plain/``), a timed comparison only; the product library does not
+  use it.
+
+Both land in ``paper_1001_4309_gb300/_build/``.
 """
 
 from __future__ import annotations
@@ -33,6 +38,32 @@ def nvcc():
 
 def library_path():
     return os.path.join(BUILD, LIB_NAME)
+
+
+PLAIN_SRC = os.path.join(PKG, "csrc_plain", "sf_plain.cu")
+PLAIN_LIB = "libsf_plain.so"
+
+
+def plain_library_path():
+    return os.path.join(BUILD, PLAIN_LIB)
+
+
+def build_plain(force=False):
+    """Compile the cuFFT comparison library if needed; returns its path."""
+    lib = plain_library_path()
+    deps = [PLAIN_SRC, os.path.join(INCLUDE, "shifted_fresnel.h")]
+    if not force and os.path.exists(lib) and all(os.path.getmtime(d) <= os.path.getmtime(lib) for d in deps):
+        return lib
+    os.makedirs(BUILD, exist_ok=True)
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+    tmp = lib + ".tmp"
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-shared", PLAIN_SRC, "-o", tmp, "-lcufft", "-L" + cuda_lib,
+           "-Xlinker", "-rpath=" + cuda_lib]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PLAIN_SRC}:\n{r.stderr}")
+    os.replace(tmp, lib)
+    return lib
 
 
 def _sources():
@@ -85,3 +116,4 @@ if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
                 extra_flags=("-Xptxas", "-v") if "-v" in sys.argv else ()))
+    print(build_plain(force="--force" in sys.argv))

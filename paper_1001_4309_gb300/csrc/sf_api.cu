@@ -29,6 +29,7 @@ constexpr int kMinFFT = 64;
 struct ViewState {
   sf_view v;
   AxisCoef ax[2];          // [0] = x, [1] = y; device pointers into the arena
+  AxisCoef adj[2];         // adjoint passes: [0] along x (nx1 -> nx0), [1] along y (ny1 -> ny0)
   float2* work = nullptr;  // [nx1][ny0] intermediate after the x pass (transposed)
   float2* st_out = nullptr;  // host-I/O staging (lazily allocated)
   float* st_int = nullptr;
@@ -47,6 +48,15 @@ struct sf_plan_s {
   void* st_holo = nullptr;
   std::vector<void*> staging;
   cudaEvent_t prof[3] = {nullptr, nullptr, nullptr};
+  // adjoint scratch, allocated by the first shifted_fresnel_adjoint call
+  float2* adj_work = nullptr;   // 3 x max(nx0 * ny1): x-pass intermediates of g, x1 g, y1 g
+  float2* adj_G = nullptr;      // 3 x nx0 * ny0: A^H g, A^H (x1 g), A^H (y1 g)
+  float2* adj_u1 = nullptr;     // max(nx1 * ny1): recomputed view field
+  float2* adj_xy = nullptr;     // 2 x max(nx1 * ny1): x1 g and y1 g
+  float2* adj_gst = nullptr;    // max(nx1 * ny1): staging of a host gradient
+  float2* adj_out = nullptr;    // nx0 * ny0: staging of a host grad_holo
+  double2* adj_part = nullptr;  // kZGradBlocks x 5 partial sums
+  double* adj_z = nullptr;      // n_views dL/dz values
 };
 
 namespace sf {
@@ -111,6 +121,27 @@ void axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
   a.h2 = to_fx(S);
 }
 
+// Adjoint of one axis, A^H = D_in^H T^H D_out^H: a Bluestein pass from n1 to
+// n0 samples whose input chirp is the conjugate of the forward output chirp
+// (including the constant of Eq. 2), whose kernel is conj(h) (h is even, so
+// T^H is the Toeplitz operator of conj(h) with the lengths swapped) and whose
+// output chirp is the conjugate of the forward input chirp, with the same
+// real scale (1/L, and 1/(lambda z) on y).
+void adjoint_axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
+  AxisCoef f;
+  axis_coefficients(v, axis, f);
+  a = f;
+  a.n0 = f.n1;
+  a.n1 = f.n0;
+  a.in2 = 0 - f.out2;
+  a.in1 = 0 - f.out1;
+  a.in0 = 0 - f.out0;
+  a.out2 = 0 - f.in2;
+  a.out1 = 0 - f.in1;
+  a.out0 = 0 - f.in0;
+  a.h2 = 0 - f.h2;
+}
+
 void count_launches(uint64_t n) { g_launches += n; }
 
 }  // namespace sf
@@ -170,6 +201,54 @@ int stage_alloc(sf_plan p, void** out, size_t bytes) {
   return SF_OK;
 }
 
+
+// Adjoint scratch, one cudaMalloc on the first shifted_fresnel_adjoint call.
+int alloc_adjoint_scratch(sf_plan p) {
+  if (p->adj_work) return SF_OK;
+  size_t w = 1, v1 = 1;
+  const size_t h0 = (size_t)p->nx0 * p->ny0;
+  for (const ViewState& vs : p->views) {
+    w = std::max(w, (size_t)vs.v.nx0 * vs.v.ny1);
+    v1 = std::max(v1, (size_t)vs.v.nx1 * vs.v.ny1);
+  }
+  Arena ar;
+  const size_t o_work = ar.take(sizeof(float2) * 3 * w), o_G = ar.take(sizeof(float2) * 3 * h0);
+  const size_t o_u1 = ar.take(sizeof(float2) * v1), o_xy = ar.take(sizeof(float2) * 2 * v1);
+  const size_t o_gst = ar.take(sizeof(float2) * v1), o_out = ar.take(sizeof(float2) * h0);
+  const size_t o_part = ar.take(sizeof(double2) * 5 * kZGradBlocks), o_z = ar.take(sizeof(double) * p->views.size());
+  void* base = nullptr;
+  if (cudaMalloc(&base, ar.off) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_OOM;
+  }
+  p->staging.push_back(base);
+  char* b = static_cast<char*>(base);
+  p->adj_work = reinterpret_cast<float2*>(b + o_work);
+  p->adj_G = reinterpret_cast<float2*>(b + o_G);
+  p->adj_u1 = reinterpret_cast<float2*>(b + o_u1);
+  p->adj_xy = reinterpret_cast<float2*>(b + o_xy);
+  p->adj_gst = reinterpret_cast<float2*>(b + o_gst);
+  p->adj_out = reinterpret_cast<float2*>(b + o_out);
+  p->adj_part = reinterpret_cast<double2*>(b + o_part);
+  p->adj_z = reinterpret_cast<double*>(b + o_z);
+  return SF_OK;
+}
+
+// Launch one pass over up to kMaxPassBatch descriptors of one FFT length.
+cudaError_t run_pass(sf_plan p, int L, PassKind kind, const PassDesc* descs, int n, cudaStream_t s) {
+  PassBatch b;
+  std::memset(&b, 0, sizeof(b));
+  int max_rows = 0;
+  for (int i = 0; i < n; ++i) {
+    b.d[i] = descs[i];
+    max_rows = std::max(max_rows, descs[i].rows);
+  }
+  b.count = n;
+  const int G = pass_rows_per_cta(L);
+  ++g_launches;
+  return launch_pass(L, kind, b, (max_rows + G - 1) / G, p->tw[L], s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -220,7 +299,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   // coefficients and arena layout
   Arena ar;
   std::map<int, size_t> tw_off;
-  std::vector<size_t> off_cin(2 * n_views), off_cout(2 * n_views), off_H(2 * n_views), off_work(n_views);
+  std::vector<size_t> off_cin(4 * n_views), off_cout(4 * n_views), off_H(4 * n_views), off_work(n_views);
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.v = views[i];
@@ -231,10 +310,15 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       off_cin[2 * i + a] = ar.take(sizeof(float2) * c.n0);
       off_cout[2 * i + a] = ar.take(sizeof(float2) * c.n1);
       off_H[2 * i + a] = ar.take(sizeof(float2) * c.L);
+      adjoint_axis_coefficients(vs.v, a, vs.adj[a]);
+      const AxisCoef& ca = vs.adj[a];
+      off_cin[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.n0);
+      off_cout[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.n1);
+      off_H[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.L);
     }
     off_work[i] = ar.take(sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1);
   }
-  const size_t off_axes = ar.take(sizeof(AxisCoef) * 2 * n_views);
+  const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
   if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
     cudaGetLastError();
     free_plan(p);
@@ -245,7 +329,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
 
   // axes sorted by FFT length so each length's spectra are built by one launch
   std::vector<AxisCoef> axes;
-  axes.reserve(2 * n_views);
+  axes.reserve(4 * n_views);
   int max_n = 1;
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
@@ -257,6 +341,11 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       c.H = reinterpret_cast<float2*>(base + off_H[2 * i + a]);
       axes.push_back(c);
       max_n = std::max(max_n, std::max(c.n0, c.n1));
+      AxisCoef& ca = vs.adj[a];
+      ca.cin = reinterpret_cast<float2*>(base + off_cin[2 * n_views + 2 * i + a]);
+      ca.cout = reinterpret_cast<float2*>(base + off_cout[2 * n_views + 2 * i + a]);
+      ca.H = reinterpret_cast<float2*>(base + off_H[2 * n_views + 2 * i + a]);
+      axes.push_back(ca);
     }
   }
   std::stable_sort(axes.begin(), axes.end(), [](const AxisCoef& x, const AxisCoef& y) { return x.L < y.L; });
@@ -404,6 +493,147 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   if (e == cudaSuccess && plan->prof[2]) e = cudaEventRecord(plan->prof[2], s);
   for (const Copy& c : d2h)
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+int shifted_fresnel_adjoint(sf_plan plan, const void* holo, const void* const* grad_view, void* grad_holo,
+                            double* grad_z, void* stream) {
+  if (!plan || !grad_view || (!grad_holo && !grad_z)) return SF_ERR_INVALID_ARG;
+  if (grad_z && !holo) return SF_ERR_INVALID_ARG;
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return SF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = alloc_adjoint_scratch(plan);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  const int nv = (int)plan->views.size();
+  const size_t h0 = (size_t)plan->nx0 * plan->ny0;
+
+  // hologram (only for dL/dz): device pointer used in place, host memory staged
+  const void* u0 = holo;
+  if (grad_z) {
+    const size_t hb = (plan->in_complex ? sizeof(float2) : sizeof(float)) * h0;
+    switch (classify(holo, plan->device)) {
+      case PTR_OTHER_DEVICE: return SF_ERR_DEVICE_MISMATCH;
+      case PTR_HOST:
+        if ((rc = stage_alloc(plan, &plan->st_holo, hb))) return rc;
+        if (cudaMemcpyAsync(plan->st_holo, holo, hb, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+          cudaGetLastError();
+          return SF_ERR_CUDA;
+        }
+        u0 = plan->st_holo;
+        break;
+      default: break;
+    }
+  }
+  // grad_holo: device pointer written in place, host memory staged
+  float2* gout = nullptr;
+  bool gout_host = false;
+  if (grad_holo) {
+    switch (classify(grad_holo, plan->device)) {
+      case PTR_OTHER_DEVICE: return SF_ERR_DEVICE_MISMATCH;
+      case PTR_HOST: gout = plan->adj_out; gout_host = true; break;
+      default: gout = static_cast<float2*>(grad_holo); break;
+    }
+  }
+  if (grad_z && cudaMemsetAsync(plan->adj_z, 0, sizeof(double) * nv, s) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+
+  size_t wmax = 1;
+  for (const ViewState& vs : plan->views) wmax = std::max(wmax, (size_t)vs.v.nx0 * vs.v.ny1);
+  bool first = true;
+  for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+    if (!grad_view[vi]) continue;
+    ViewState& vs = plan->views[vi];
+    const sf_view& v = vs.v;
+    const size_t n1px = (size_t)v.nx1 * v.ny1;
+    const float2* g = static_cast<const float2*>(grad_view[vi]);
+    switch (classify(g, plan->device)) {
+      case PTR_OTHER_DEVICE: return SF_ERR_DEVICE_MISMATCH;
+      case PTR_HOST:
+        e = cudaMemcpyAsync(plan->adj_gst, g, sizeof(float2) * n1px, cudaMemcpyHostToDevice, s);
+        g = plan->adj_gst;
+        break;
+      default: break;
+    }
+    const bool zg = grad_z != nullptr;
+    float2* xg = plan->adj_xy;
+    float2* yg = plan->adj_xy + n1px;
+    if (zg && e == cudaSuccess) {
+      // recompute this view's field u1 = A u0 (no stored forward state is needed)
+      PassDesc d;
+      std::memset(&d, 0, sizeof(d));
+      d.cin = vs.ax[0].cin; d.cout = vs.ax[0].cout; d.H = vs.ax[0].H;
+      d.n0 = vs.ax[0].n0; d.n1 = vs.ax[0].n1;
+      d.src = u0; d.dst = vs.work; d.rows = v.ny0; d.src_ld = v.nx0; d.dst_ld = v.ny0;
+      e = run_pass(plan, vs.ax[0].L, plan->in_complex ? PASS_X_CPLX : PASS_X_REAL, &d, 1, s);
+      if (e == cudaSuccess) {
+        std::memset(&d, 0, sizeof(d));
+        d.cin = vs.ax[1].cin; d.cout = vs.ax[1].cout; d.H = vs.ax[1].H;
+        d.n0 = vs.ax[1].n0; d.n1 = vs.ax[1].n1;
+        d.src = vs.work; d.dst = plan->adj_u1; d.rows = v.nx1; d.src_ld = v.ny0; d.dst_ld = v.nx1;
+        e = run_pass(plan, vs.ax[1].L, PASS_Y, &d, 1, s);
+      }
+      if (e == cudaSuccess) {
+        e = launch_weight_xy(g, xg, yg, v.nx1, v.ny1, v.px1, v.py1, v.ox1, v.oy1, s);
+        ++g_launches;
+      }
+    }
+    // adjoint along x: rows of g (length nx1) -> nx0 outputs, intermediate [nx0][ny1]
+    const float2* ins[3] = {g, xg, yg};
+    const int nin = zg ? 3 : 1;
+    PassDesc dx[3], dy[3];
+    for (int k = 0; k < nin; ++k) {
+      std::memset(&dx[k], 0, sizeof(PassDesc));
+      dx[k].cin = vs.adj[0].cin; dx[k].cout = vs.adj[0].cout; dx[k].H = vs.adj[0].H;
+      dx[k].n0 = vs.adj[0].n0; dx[k].n1 = vs.adj[0].n1;
+      dx[k].src = ins[k]; dx[k].dst = plan->adj_work + k * wmax;
+      dx[k].rows = v.ny1; dx[k].src_ld = v.nx1; dx[k].dst_ld = v.ny1;
+      std::memset(&dy[k], 0, sizeof(PassDesc));
+      dy[k].cin = vs.adj[1].cin; dy[k].cout = vs.adj[1].cout; dy[k].H = vs.adj[1].H;
+      dy[k].n0 = vs.adj[1].n0; dy[k].n1 = vs.adj[1].n1;
+      dy[k].src = plan->adj_work + k * wmax; dy[k].rows = v.nx0; dy[k].src_ld = v.ny1; dy[k].dst_ld = v.nx0;
+      if (zg) {
+        dy[k].dst = plan->adj_G + k * h0;
+      } else {
+        dy[k].dst = gout;
+        dy[k].accumulate = first ? 0 : 1;
+      }
+    }
+    if (e == cudaSuccess) e = run_pass(plan, vs.adj[0].L, PASS_X_CPLX, dx, nin, s);
+    if (e == cudaSuccess) e = run_pass(plan, vs.adj[1].L, PASS_Y, dy, nin, s);
+    if (zg && e == cudaSuccess) {
+      ZGradArgs za;
+      za.g = g; za.u1 = plan->adj_u1;
+      za.G0 = plan->adj_G; za.G1 = plan->adj_G + h0; za.G2 = plan->adj_G + 2 * h0;
+      za.u0 = u0; za.u0_complex = plan->in_complex ? 1 : 0;
+      za.nx0 = v.nx0; za.ny0 = v.ny0; za.nx1 = v.nx1; za.ny1 = v.ny1;
+      za.px0 = v.px0; za.py0 = v.py0; za.px1 = v.px1; za.py1 = v.py1;
+      za.ox0 = v.ox0; za.oy0 = v.oy0; za.ox1 = v.ox1; za.oy1 = v.oy1;
+      const double pi = 3.14159265358979323846;
+      const bool pre = !(v.flags & SF_NO_PREFACTOR);
+      const double c_re = pre ? -1.0 / v.z : 0.0, c_im = pre ? 2.0 * pi / v.wavelength : 0.0;
+      const double q_im = -pi / (v.wavelength * v.z * v.z);
+      e = launch_zgrad(za, plan->adj_part, kZGradBlocks, plan->adj_z + vi, c_re, c_im, 0.0, q_im, s);
+      g_launches += 2;
+      if (e == cudaSuccess && gout) {
+        e = launch_axpy(gout, plan->adj_G, h0, first ? 0 : 1, s);
+        ++g_launches;
+      }
+    }
+    first = false;
+  }
+  if (e == cudaSuccess && gout && first) e = cudaMemsetAsync(gout, 0, sizeof(float2) * h0, s);
+  if (e == cudaSuccess && gout_host)
+    e = cudaMemcpyAsync(grad_holo, gout, sizeof(float2) * h0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && grad_z)
+    e = cudaMemcpyAsync(grad_z, plan->adj_z, sizeof(double) * nv, cudaMemcpyDefault, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SF_ERR_CUDA;

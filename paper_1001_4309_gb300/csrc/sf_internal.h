@@ -29,6 +29,7 @@ struct PassDesc {
   int n0, n1;         // convolution input / output lengths along this axis
   int rows;           // independent rows of this pass
   int src_ld, dst_ld;
+  int accumulate;     // Y only: add into dst instead of overwriting it
 };
 
 struct PassBatch {
@@ -51,6 +52,26 @@ struct AxisCoef {
 // host helpers shared by the entry points (defined in sf_api.cu)
 int validate_view(const sf_view& v);
 void axis_coefficients(const sf_view& v, int axis, AxisCoef& a);
+void adjoint_axis_coefficients(const sf_view& v, int axis, AxisCoef& a);
+
+// Inner products for d(loss)/dz of one view (see shifted_fresnel_adjoint).
+struct ZGradArgs {
+  const float2* g;    // [ny1][nx1] gradient w.r.t. the view
+  const float2* u1;   // [ny1][nx1] view field
+  const float2* G0;   // [ny0][nx0] A^H g
+  const float2* G1;   // [ny0][nx0] A^H (x1 g)
+  const float2* G2;   // [ny0][nx0] A^H (y1 g)
+  const void* u0;     // [ny0][nx0] hologram, float32 or complex64
+  int u0_complex;
+  int nx0, ny0, nx1, ny1;
+  double px0, py0, px1, py1, ox0, oy0, ox1, oy1;
+};
+cudaError_t launch_weight_xy(const float2* g, float2* xg, float2* yg, int nx1, int ny1, double px1, double py1,
+                             double ox1, double oy1, cudaStream_t s);
+cudaError_t launch_zgrad(const ZGradArgs& a, double2* partials, int n_partials, double* out, double c_re,
+                         double c_im, double q_re, double q_im, cudaStream_t s);
+cudaError_t launch_axpy(float2* y, const float2* x, size_t n, int accumulate, cudaStream_t s);
+constexpr int kZGradBlocks = 304;
 void count_launches(uint64_t n);
 
 // launchers (one translation unit per FFT length family)

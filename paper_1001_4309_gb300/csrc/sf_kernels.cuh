@@ -105,7 +105,7 @@ k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
       if constexpr (KIND != PASS_Y) {
         d.dst[o] = u;
       } else {
-        if (d.dst) d.dst[o] = u;
+        if (d.dst) d.dst[o] = d.accumulate ? cadd(d.dst[o], u) : u;
         if (d.inten) d.inten[o] = fmaf(u.x, u.x, u.y * u.y);
         if (d.phase) d.phase[o] = phase_of(u);
       }

@@ -209,3 +209,24 @@ def test_kernel_launch_counter_counts_two_passes(P):
         assert P.shifted_fresnel_kernel_launches() - before == 2
     finally:
         sf.close()
+
+
+def test_plain_cufft_comparison_path_matches_oracle(P):
+    """The benchmark's comparison path (the paper's steps 2-10 with cuFFT) is itself correct."""
+    import torch
+    from paper_1001_4309_gb300 import build as b
+    from paper_1001_4309_gb300.plain import PlainPath
+    b.build_plain()
+    holo, views = synth.config_c1()
+    views = views + [view(WAVELENGTH, 0.07, (PITCH, 3.1e-6), (1.0e-6, 2.2e-6), o1=(-3e-4, 2e-4),
+                          n0=(256, 256), n1=(200, 120))]
+    pp = PlainPath(views)
+    try:
+        h = torch.from_numpy(holo).cuda()
+        outs = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64, device="cuda") for v in views]
+        pp.execute(h, outs)
+        torch.cuda.synchronize()
+        for o, v in zip(outs, views):
+            assert rel_l2(o.cpu().numpy(), oracle.forward(holo, v)) <= TOL
+    finally:
+        pp.close()
