@@ -119,6 +119,48 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
                             float* const* intensity, float* const* phase, void* stream);
 
 /*
+ * shifted_fresnel_execute_batch -- reconstruct every view of the plan for
+ * each of n_holos holograms (the paper's per-frame loop of Section 2.2,
+ * steps 1-11, over a stream of frames) in ONE persistent kernel launch,
+ * issued as a CUDA graph (descriptor upload, counter reset, kernel).
+ *
+ *   holos      n_holos device pointers, each a hologram as for execute.
+ *   view_out   n_holos * n_views device pointers (index h * n_views + v) to
+ *              complex64 [ny1][nx1] views, or NULL; entries may be NULL.
+ *   intensity  same layout, float32 |u1|^2 images, or NULL.
+ *   phase      same layout, float32 phase images, or NULL.
+ *   stream     stream to launch the graph on.
+ * Every (hologram, view) needs at least one non-NULL output.  All buffers
+ * must be device memory of the plan's device (SF_ERR_INVALID_ARG otherwise).
+ * Views may have different sizes (ragged); every FFT length must be at most
+ * 4096 (SF_ERR_UNSUPPORTED_SIZE otherwise).
+ *
+ * Inside the launch, CTAs take (hologram, pass, view, row tile) items in
+ * order from a counter; a y-pass item waits for the x-pass tiles of its
+ * hologram and view, an x-pass item for hologram h waits for the y pass of
+ * hologram h - 2 (two intermediate slots per view).  The waits are bounded;
+ * if one expires the launch ends early and shifted_fresnel_batch_status
+ * reports SF_ERR_TIMEOUT.  The first call (and a call with a new n_holos)
+ * allocates per-view second intermediate slots, descriptor tables (pinned
+ * and device) and builds the graph; calls return after launching and may
+ * block the host only until the call two back has finished.  Calls on one
+ * plan must not overlap with other calls on another stream.
+ * Testing aids read when the graph is built: SF_BATCH_SPIN_LIMIT (sleeps
+ * before a wait gives up, default 4194304) and SF_BATCH_POISON_GROUP (an
+ * item group whose dependency is made unsatisfiable).
+ * Errors: SF_ERR_INVALID_ARG, SF_ERR_UNSUPPORTED_SIZE, SF_ERR_OOM, SF_ERR_CUDA.
+ */
+int shifted_fresnel_execute_batch(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
+                                  float* const* intensity, float* const* phase, void* stream);
+
+/*
+ * shifted_fresnel_batch_status -- synchronise `stream` and report whether a
+ * bounded wait of an earlier batch launch expired (SF_ERR_TIMEOUT, after
+ * which the flag is cleared) or not (SF_OK).
+ */
+int shifted_fresnel_batch_status(sf_plan plan, void* stream);
+
+/*
  * shifted_fresnel_adjoint -- back-propagate view gradients to the hologram
  * plane, and optionally differentiate with respect to each view's z.
  *

@@ -15,6 +15,8 @@ from .binding import (  # noqa: F401
     shifted_fresnel_execute_static,
     shifted_fresnel_destroy,
     shifted_fresnel_adjoint,
+    shifted_fresnel_execute_batch,
+    shifted_fresnel_batch_status,
     shifted_fresnel_strerror,
     shifted_fresnel_plan_query,
     shifted_fresnel_kernel_launches,

@@ -79,6 +79,10 @@ def load():
     lib.shifted_fresnel_kernel_launches.restype = ctypes.c_uint64
     lib.shifted_fresnel_execute_static.argtypes = [ctypes.POINTER(sf_view), vp, vp, vp, vp, vp]
     lib.shifted_fresnel_execute_static.restype = ctypes.c_int
+    lib.shifted_fresnel_execute_batch.argtypes = [vp, pp, ctypes.c_int, pp, pp, pp, vp]
+    lib.shifted_fresnel_execute_batch.restype = ctypes.c_int
+    lib.shifted_fresnel_batch_status.argtypes = [vp, vp]
+    lib.shifted_fresnel_batch_status.restype = ctypes.c_int
     lib.shifted_fresnel_adjoint.argtypes = [vp, vp, pp, vp, vp, vp]
     lib.shifted_fresnel_adjoint.restype = ctypes.c_int
     lib.shifted_fresnel_set_profile_events.argtypes = [vp, pp, ctypes.c_int]
@@ -149,6 +153,21 @@ def shifted_fresnel_execute_static(view, holo_ptr, view_out=None, intensity=None
     if check and rc != SF_OK:
         raise SFError(rc, "shifted_fresnel_execute_static")
     return rc
+
+
+def shifted_fresnel_execute_batch(plan, holo_ptrs, view_out=None, intensity=None, phase=None, stream=0,
+                                  check=True):
+    """All views for each hologram in one persistent graph launch; outputs indexed h * n_views + v."""
+    rc = load().shifted_fresnel_execute_batch(plan, _ptr_array(list(holo_ptrs)), len(holo_ptrs),
+                                              _ptr_array(view_out), _ptr_array(intensity), _ptr_array(phase),
+                                              ctypes.c_void_p(stream) if stream else None)
+    if check and rc != SF_OK:
+        raise SFError(rc, "shifted_fresnel_execute_batch")
+    return rc
+
+
+def shifted_fresnel_batch_status(plan, stream=0):
+    return load().shifted_fresnel_batch_status(plan, ctypes.c_void_p(stream) if stream else None)
 
 
 def shifted_fresnel_adjoint(plan, holo_ptr, grad_view, grad_holo=None, grad_z=None, stream=0, check=True):
@@ -234,6 +253,20 @@ class ShiftedFresnel:
     def reconstruct(self, holo, field=True, intensity=False, phase=False):
         outs = self.alloc_outputs(field, intensity, phase)
         return self.execute(holo, outs)
+
+    def execute_batch(self, holos, outs, stream=None):
+        """outs: dict of lists indexed [h][v] (from alloc_batch_outputs)."""
+        ptr = lambda x: x.data_ptr() if x is not None else None  # noqa: E731
+        flat = lambda key: ([ptr(o) for row in outs[key] for o in row]  # noqa: E731
+                            if outs.get(key) and any(o is not None for row in outs[key] for o in row) else None)
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
+        shifted_fresnel_execute_batch(self.handle, [h.data_ptr() for h in holos], flat("field"),
+                                      flat("intensity"), flat("phase"), stream=s)
+        return outs
+
+    def alloc_batch_outputs(self, n_holos, field=True, intensity=False, phase=False):
+        per = [self.alloc_outputs(field, intensity, phase) for _ in range(n_holos)]
+        return {k: [o[k] for o in per] for k in ("field", "intensity", "phase")}
 
     def adjoint(self, grad_views, holo=None, grad_holo=None, grad_z=None, stream=None):
         """grad_holo (complex64 [ny0][nx0]) and grad_z (float64 [n_views]) from per-view gradients."""

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <new>
 #include <vector>
@@ -36,6 +37,26 @@ struct ViewState {
   float* st_ph = nullptr;
 };
 
+// Resources of shifted_fresnel_execute_batch, built by its first call.
+struct BatchState {
+  bool init = false;
+  int n_holos = 0;                       // hologram count the graphs are built for
+  std::vector<BatchGroup> groups;
+  int items_per_holo = 0, grid = 0;
+  std::vector<float2*> slot1;            // second intermediate slot per view
+  BatchGroup* d_groups = nullptr;
+  int* d_error = nullptr;
+  void* d_fixed = nullptr;               // slot1 workspaces + groups + error word
+  void* d_sized = nullptr;               // descriptors + counters for n_holos
+  PassDesc* d_descs = nullptr;
+  int* d_done = nullptr;                 // n_holos * n_groups completion counters, then the item counter
+  PassDesc* h_descs[2] = {nullptr, nullptr};  // pinned, alternated between calls
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int flip = 0;
+};
+
 }  // namespace
 
 struct sf_plan_s {
@@ -57,6 +78,7 @@ struct sf_plan_s {
   float2* adj_out = nullptr;    // nx0 * ny0: staging of a host grad_holo
   double2* adj_part = nullptr;  // kZGradBlocks x 5 partial sums
   double* adj_z = nullptr;      // n_views dL/dz values
+  BatchState batch;
 };
 
 namespace sf {
@@ -183,8 +205,26 @@ struct DeviceGuard {
   }
 };
 
+void free_batch_sized(BatchState& b) {
+  for (int k = 0; k < 2; ++k) {
+    if (b.exec[k]) cudaGraphExecDestroy(b.exec[k]);
+    if (b.graph[k]) cudaGraphDestroy(b.graph[k]);
+    if (b.h_descs[k]) cudaFreeHost(b.h_descs[k]);
+    b.exec[k] = nullptr;
+    b.graph[k] = nullptr;
+    b.h_descs[k] = nullptr;
+  }
+  if (b.d_sized) cudaFree(b.d_sized);
+  b.d_sized = nullptr;
+  b.n_holos = 0;
+}
+
 void free_plan(sf_plan p) {
   if (!p) return;
+  free_batch_sized(p->batch);
+  for (int k = 0; k < 2; ++k)
+    if (p->batch.ev[k]) cudaEventDestroy(p->batch.ev[k]);
+  if (p->batch.d_fixed) cudaFree(p->batch.d_fixed);
   for (void* s : p->staging) cudaFree(s);
   if (p->arena) cudaFree(p->arena);
   delete p;
@@ -247,6 +287,132 @@ cudaError_t run_pass(sf_plan p, int L, PassKind kind, const PassDesc* descs, int
   const int G = pass_rows_per_cta(L);
   ++g_launches;
   return launch_pass(L, kind, b, (max_rows + G - 1) / G, p->tw[L], s);
+}
+
+long long env_ll(const char* name, long long dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoll(v) : dflt;
+}
+
+// Build (or rebuild for a new hologram count) the batch graph:
+// memcpy(descriptors <- pinned table), memset(counters), persistent kernel.
+int batch_prepare(sf_plan p, int n_holos) {
+  BatchState& b = p->batch;
+  const int nv = (int)p->views.size();
+  if (!b.init) {
+    b.groups.clear();
+    int first = 0;
+    for (int ph = 0; ph < 2; ++ph)
+      for (int v = 0; v < nv; ++v) {
+        const ViewState& vs = p->views[v];
+        const int L = vs.ax[ph].L;
+        if (!batch_length_supported(L)) return SF_ERR_UNSUPPORTED_SIZE;
+        const int rows = ph == 0 ? vs.v.ny0 : vs.v.nx1, G = batch_tile_rows(L);
+        b.groups.push_back({first, (rows + G - 1) / G, L, ph});
+        first += (rows + G - 1) / G;
+      }
+    b.items_per_holo = first;
+    Arena ar;
+    std::vector<size_t> off(nv);
+    for (int v = 0; v < nv; ++v) off[v] = ar.take(sizeof(float2) * (size_t)p->views[v].v.ny0 * p->views[v].v.nx1);
+    const size_t o_groups = ar.take(sizeof(BatchGroup) * b.groups.size()), o_err = ar.take(sizeof(int));
+    if (cudaMalloc(&b.d_fixed, ar.off) != cudaSuccess) {
+      cudaGetLastError();
+      return SF_ERR_OOM;
+    }
+    char* base = static_cast<char*>(b.d_fixed);
+    b.slot1.resize(nv);
+    for (int v = 0; v < nv; ++v) b.slot1[v] = reinterpret_cast<float2*>(base + off[v]);
+    b.d_groups = reinterpret_cast<BatchGroup*>(base + o_groups);
+    b.d_error = reinterpret_cast<int*>(base + o_err);
+    if (cudaMemcpy(b.d_groups, b.groups.data(), sizeof(BatchGroup) * b.groups.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemset(b.d_error, 0, sizeof(int)) != cudaSuccess)
+      return SF_ERR_CUDA;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    for (PassKind k : {PASS_X_REAL, PASS_X_CPLX})
+      cudaFuncSetAttribute(batch_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(p->in_complex ? PASS_X_CPLX : PASS_X_REAL),
+                                                      kBatchThreads, batch_smem_bytes()) != cudaSuccess ||
+        per_sm < 1)
+      return SF_ERR_CUDA;
+    b.grid = sms * per_sm;
+    for (int k = 0; k < 2; ++k)
+      if (cudaEventCreateWithFlags(&b.ev[k], cudaEventDisableTiming) != cudaSuccess) return SF_ERR_CUDA;
+    b.init = true;
+  }
+  if (b.n_holos == n_holos) return SF_OK;
+  free_batch_sized(b);
+  const int ng = (int)b.groups.size();
+  const size_t n_desc = (size_t)n_holos * ng, n_cnt = n_desc + 1;
+  Arena ar;
+  const size_t o_desc = ar.take(sizeof(PassDesc) * n_desc), o_done = ar.take(sizeof(int) * n_cnt);
+  if (cudaMalloc(&b.d_sized, ar.off) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_OOM;
+  }
+  b.d_descs = reinterpret_cast<PassDesc*>(static_cast<char*>(b.d_sized) + o_desc);
+  b.d_done = reinterpret_cast<int*>(static_cast<char*>(b.d_sized) + o_done);
+  BatchArgs args;
+  std::memset(&args, 0, sizeof(args));
+  args.descs = b.d_descs;
+  args.groups = b.d_groups;
+  args.done = b.d_done;
+  args.next = b.d_done + n_desc;
+  args.error = b.d_error;
+  for (auto& kv : p->tw) {
+    int lg = 0;
+    while ((1 << lg) < kv.first) ++lg;
+    if (lg < 13) args.tw[lg] = kv.second;
+  }
+  args.n_holos = n_holos;
+  args.n_groups = ng;
+  args.n_views = nv;
+  args.items_per_holo = b.items_per_holo;
+  args.total_items = n_holos * b.items_per_holo;
+  args.poison_group = (int)env_ll("SF_BATCH_POISON_GROUP", -1);
+  args.spin_limit = env_ll("SF_BATCH_SPIN_LIMIT", 1ll << 22);
+  for (int k = 0; k < 2; ++k) {
+    if (cudaHostAlloc(&b.h_descs[k], sizeof(PassDesc) * n_desc, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch_sized(b);
+      return SF_ERR_OOM;
+    }
+    std::memset(b.h_descs[k], 0, sizeof(PassDesc) * n_desc);
+    cudaGraphNode_t cp, ms, kn;
+    cudaError_t e = cudaGraphCreate(&b.graph[k], 0);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&cp, b.graph[k], nullptr, 0, b.d_descs, b.h_descs[k], sizeof(PassDesc) * n_desc,
+                                   cudaMemcpyHostToDevice);
+    cudaMemsetParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.dst = b.d_done;
+    mp.value = 0;
+    mp.elementSize = sizeof(int);
+    mp.width = n_cnt;
+    mp.height = 1;
+    mp.pitch = sizeof(int) * n_cnt;
+    if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&ms, b.graph[k], nullptr, 0, &mp);
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    void* kargs[] = {&args};
+    kp.func = const_cast<void*>(batch_kernel(p->in_complex ? PASS_X_CPLX : PASS_X_REAL));
+    kp.gridDim = dim3(b.grid);
+    kp.blockDim = dim3(kBatchThreads);
+    kp.sharedMemBytes = (unsigned)batch_smem_bytes();
+    kp.kernelParams = kargs;
+    cudaGraphNode_t deps[2] = {cp, ms};
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&kn, b.graph[k], deps, 2, &kp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b.exec[k], b.graph[k], 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_batch_sized(b);
+      return SF_ERR_CUDA;
+    }
+  }
+  b.n_holos = n_holos;
+  return SF_OK;
 }
 
 }  // namespace
@@ -637,6 +803,87 @@ int shifted_fresnel_adjoint(sf_plan plan, const void* holo, const void* const* g
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+int shifted_fresnel_execute_batch(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
+                                  float* const* intensity, float* const* phase, void* stream) {
+  if (!plan || !holos || n_holos < 1) return SF_ERR_INVALID_ARG;
+  const int nv = (int)plan->views.size();
+  for (int h = 0; h < n_holos; ++h) {
+    if (!holos[h]) return SF_ERR_INVALID_ARG;
+    for (int v = 0; v < nv; ++v) {
+      const size_t i = (size_t)h * nv + v;
+      if (!((view_out && view_out[i]) || (intensity && intensity[i]) || (phase && phase[i]))) return SF_ERR_INVALID_ARG;
+    }
+  }
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return SF_ERR_CUDA;
+  // device memory of this plan's device only (the batch is one graph launch; nothing is staged)
+  for (int h = 0; h < n_holos; ++h) {
+    if (classify(holos[h], plan->device) != PTR_DEVICE) return SF_ERR_INVALID_ARG;
+    for (int v = 0; v < nv; ++v) {
+      const size_t i = (size_t)h * nv + v;
+      for (const void* q : {view_out ? (const void*)view_out[i] : nullptr,
+                            intensity ? (const void*)intensity[i] : nullptr, phase ? (const void*)phase[i] : nullptr})
+        if (q && classify(q, plan->device) != PTR_DEVICE) return SF_ERR_INVALID_ARG;
+    }
+  }
+  int rc = batch_prepare(plan, n_holos);
+  if (rc) return rc;
+  BatchState& b = plan->batch;
+  const int k = b.flip;
+  if (cudaEventSynchronize(b.ev[k]) != cudaSuccess) {  // the call two back has finished reading this table
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  const int ng = (int)b.groups.size();
+  for (int h = 0; h < n_holos; ++h)
+    for (int g = 0; g < ng; ++g) {
+      const int v = g % nv, ph = g / nv;
+      ViewState& vs = plan->views[v];
+      float2* slot = (h & 1) ? b.slot1[v] : vs.work;
+      const AxisCoef& c = vs.ax[ph];
+      PassDesc& d = b.h_descs[k][(size_t)h * ng + g];
+      std::memset(&d, 0, sizeof(d));
+      d.cin = c.cin; d.cout = c.cout; d.H = c.H; d.n0 = c.n0; d.n1 = c.n1;
+      if (ph == 0) {
+        d.src = holos[h]; d.dst = slot; d.rows = vs.v.ny0; d.src_ld = vs.v.nx0; d.dst_ld = vs.v.ny0;
+      } else {
+        const size_t i = (size_t)h * nv + v;
+        d.src = slot;
+        d.dst = view_out ? static_cast<float2*>(view_out[i]) : nullptr;
+        d.inten = intensity ? intensity[i] : nullptr;
+        d.phase = phase ? phase[i] : nullptr;
+        d.rows = vs.v.nx1; d.src_ld = vs.v.ny0; d.dst_ld = vs.v.nx1;
+      }
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaGraphLaunch(b.exec[k], s);
+  if (e == cudaSuccess) e = cudaEventRecord(b.ev[k], s);
+  ++g_launches;
+  b.flip ^= 1;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+int shifted_fresnel_batch_status(sf_plan plan, void* stream) {
+  if (!plan) return SF_ERR_INVALID_ARG;
+  if (!plan->batch.init) return SF_OK;
+  DeviceGuard guard(plan->device);
+  int err = 0;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+      cudaMemcpy(&err, plan->batch.d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  if (err) {
+    cudaMemset(plan->batch.d_error, 0, sizeof(int));
+    return SF_ERR_TIMEOUT;
   }
   return SF_OK;
 }

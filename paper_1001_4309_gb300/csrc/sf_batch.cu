@@ -1,0 +1,142 @@
+// sf_batch.cu -- persistent kernel for a batch of ragged views over a stream
+// of holograms (the paper's real-time loop, Section 2.2, repeated over frames,
+// with every view and frame in one launch).
+//
+// Work items are (hologram h, group g, tile): group g < V is the x pass of
+// view g, group V + v the y pass of view v; within a hologram all x items
+// precede all y items, and holograms follow one another.  A CTA takes the
+// next item from a global counter, so items start in index order.
+// Dependencies, each a wait on a per-(hologram, group) completion counter:
+//   - a y item of (h, v) waits until every x tile of (h, v) is done;
+//   - an x item of (h, v), h >= 2, waits until every y tile of (h - 2, v) is
+//     done, because the x pass of h writes the intermediate slot h % 2 that
+//     the y pass of h - 2 read.
+// Every awaited item has a smaller index, was therefore taken earlier by a
+// running CTA, and itself only waits on smaller indices: the lowest
+// unfinished item never waits, so the launch always progresses, whatever
+// the number of resident CTAs.  Waits are still bounded (spin_limit sleeps);
+// on expiry a CTA sets the error word and leaves, which unblocks nobody but
+// ends every other wait by its own limit, so the launch always returns.
+#include "sf_kernels.cuh"
+
+namespace sf {
+namespace {
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int KIND_X>
+__device__ __forceinline__ void run_item(const PassDesc& d, int phase, int L, int tile, float2* smem,
+                                         const float4* const* tw) {
+#define SF_BATCH_CASE(LL, LG)                                                                   \
+  case LL:                                                                                      \
+    if (phase == 0) row_tile<LL, KIND_X, false>(d, tile * PassShape<LL>::G, smem, tw[LG]);      \
+    else row_tile<LL, PASS_Y, true>(d, tile * PassShape<LL>::G, smem, tw[LG]);                  \
+    break;
+  switch (L) {
+    SF_BATCH_CASE(64, 6)
+    SF_BATCH_CASE(128, 7)
+    SF_BATCH_CASE(256, 8)
+    SF_BATCH_CASE(512, 9)
+    SF_BATCH_CASE(1024, 10)
+    SF_BATCH_CASE(2048, 11)
+    SF_BATCH_CASE(4096, 12)
+    default: break;
+  }
+#undef SF_BATCH_CASE
+}
+
+template <int KIND_X>
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const __grid_constant__ BatchArgs a) {
+  extern __shared__ float2 smem[];
+  __shared__ int s_item, s_group, s_stop;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int item = atomicAdd(a.next, 1);
+      int stop = item >= a.total_items || ld_acquire(a.error) != 0;
+      int g = 0;
+      if (!stop) {
+        const int h = item / a.items_per_holo, r = item - h * a.items_per_holo;
+        int lo = 0, hi = a.n_groups - 1;  // last group with first_item <= r
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.groups[mid].first_item <= r) lo = mid; else hi = mid - 1;
+        }
+        g = lo;
+        // dependency of this item, if any
+        const int* cnt = nullptr;
+        int target = 0;
+        if (g >= a.n_views) {
+          cnt = a.done + (size_t)h * a.n_groups + (g - a.n_views);
+          target = a.groups[g - a.n_views].tiles;
+        } else if (h >= 2) {
+          cnt = a.done + (size_t)(h - 2) * a.n_groups + (g + a.n_views);
+          target = a.groups[g + a.n_views].tiles;
+        }
+        if (g == a.poison_group) target = 0x7fffffff;  // host-injected never-satisfied dependency (tests)
+        if (cnt) {
+          long long spins = 0;
+          while (ld_acquire(cnt) < target) {
+            if (++spins > a.spin_limit || ld_acquire(a.error) != 0) {
+              atomicExch(a.error, 1);
+              stop = 1;
+              break;
+            }
+            __nanosleep(256);
+          }
+        }
+      }
+      s_item = item;
+      s_group = g;
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const int item = s_item, g = s_group;
+    const int h = item / a.items_per_holo;
+    const BatchGroup gi = a.groups[g];
+    const PassDesc& d = a.descs[(size_t)h * a.n_groups + g];
+    run_item<KIND_X>(d, gi.phase, gi.L, item - h * a.items_per_holo - gi.first_item, smem, a.tw);
+    __threadfence();  // this thread's stores are visible device-wide before the tile is counted
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(a.done + (size_t)h * a.n_groups + g, 1);
+  }
+}
+
+}  // namespace
+
+bool batch_length_supported(int L) { return L >= 64 && L <= 4096 && (L & (L - 1)) == 0; }
+
+int batch_tile_rows(int L) {
+  switch (L) {
+    case 64: return PassShape<64>::G;
+    case 128: return PassShape<128>::G;
+    case 256: return PassShape<256>::G;
+    case 512: return PassShape<512>::G;
+    case 1024: return PassShape<1024>::G;
+    case 2048: return PassShape<2048>::G;
+    case 4096: return PassShape<4096>::G;
+    default: return 0;
+  }
+}
+
+size_t batch_smem_bytes() {
+  size_t m = 0;
+  m = std::max(m, PassShape<64>::SMEM);
+  m = std::max(m, PassShape<128>::SMEM);
+  m = std::max(m, PassShape<256>::SMEM);
+  m = std::max(m, PassShape<512>::SMEM);
+  m = std::max(m, PassShape<1024>::SMEM);
+  m = std::max(m, PassShape<2048>::SMEM);
+  m = std::max(m, PassShape<4096>::SMEM);
+  return m;
+}
+
+const void* batch_kernel(PassKind kind_x) {
+  return kind_x == PASS_X_CPLX ? (const void*)k_batch<PASS_X_CPLX> : (const void*)k_batch<PASS_X_REAL>;
+}
+
+}  // namespace sf

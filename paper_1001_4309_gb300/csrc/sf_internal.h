@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "shifted_fresnel.h"
 
 namespace sf {
@@ -48,6 +50,30 @@ struct AxisCoef {
   float2* cout;               // device, n1
   float2* H;                  // device, L (register order)
 };
+
+// Persistent batch kernel (sf_batch.cu)
+constexpr int kBatchThreads = 256;
+struct BatchGroup {
+  int first_item;  // index of the group's first tile within one hologram's items
+  int tiles;       // tiles of the group
+  int L;           // FFT length
+  int phase;       // 0: x pass, 1: y pass
+};
+struct BatchArgs {
+  const PassDesc* descs;     // [n_holos][n_groups]
+  const BatchGroup* groups;  // [n_groups] (x groups of views 0..V-1, then y groups)
+  int* done;                 // [n_holos][n_groups] completed tiles
+  int* next;                 // item counter
+  int* error;                // set to 1 when a bounded wait expires
+  const float4* tw[13];      // per-stage twiddle tables indexed by log2(L)
+  int n_holos, n_groups, n_views, items_per_holo, total_items;
+  int poison_group;          // -1; a group index makes its dependency unsatisfiable (tests)
+  long long spin_limit;      // sleeps before a wait gives up
+};
+bool batch_length_supported(int L);
+int batch_tile_rows(int L);
+size_t batch_smem_bytes();
+const void* batch_kernel(PassKind kind_x);
 
 // host helpers shared by the entry points (defined in sf_api.cu)
 int validate_view(const sf_view& v);

@@ -47,19 +47,15 @@ __device__ __forceinline__ float phase_of(float2 u) {
   return p <= -3.14159265358979f ? 3.14159265358979f : p;  // (-pi, pi]
 }
 
-// Row pass.  Group g of the CTA transforms source row r = blockIdx.x * G + g,
+// One tile of a pass: group g of the CTA transforms source row r = row0 + g,
 // read contiguously (src[r * src_ld + p], p < n0), and the n1 outputs are
 // written transposed (dst[p * dst_ld + r]) through a shared-memory tile so
-// the G rows of the CTA leave as G-element contiguous runs.
-template <int L, int KIND>
-__global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
-k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
+// the G rows of the tile leave as G-element contiguous runs.  COHERENT reads
+// the source through L2 only, for data written earlier in the same launch.
+template <int L, int KIND, bool COHERENT>
+__device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw) {
   using Sh = PassShape<L>;
   constexpr int T = Sh::T, G = Sh::G, E = kE;
-  extern __shared__ float2 smem[];
-  const PassDesc& d = b.d[blockIdx.y];
-  const int row0 = blockIdx.x * G;
-  if (row0 >= d.rows) return;  // whole CTA past this pass's rows
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   const int row = row0 + g;
   const bool valid = row < d.rows;
@@ -76,7 +72,8 @@ k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
         const float x = __ldg(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + p);
         v[j] = cscale(c, x);
       } else {
-        const float2 x = __ldg(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + p);
+        const float2* sp = static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + p;
+        const float2 x = COHERENT ? __ldcg(sp) : __ldg(sp);
         v[j] = cmul(x, c);
       }
     }
@@ -111,6 +108,17 @@ k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
       }
     }
   }
+}
+
+// Row pass: tile blockIdx.x of pass blockIdx.y.
+template <int L, int KIND>
+__global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
+k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
+  extern __shared__ float2 smem[];
+  const PassDesc& d = b.d[blockIdx.y];
+  const int row0 = blockIdx.x * PassShape<L>::G;
+  if (row0 >= d.rows) return;  // whole CTA past this pass's rows
+  row_tile<L, KIND, false>(d, row0, smem, tw);
 }
 
 // Kernel spectrum of Eq. 4 (steps 5-6), one thread group per axis, run once

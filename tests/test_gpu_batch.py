@@ -1,0 +1,180 @@
+"""Persistent batched execution of ragged views over a stream of holograms.
+
+shifted_fresnel_execute_batch runs every (hologram, view) of a call in one
+graph launch of the persistent kernel; its outputs must equal, bit for bit,
+shifted_fresnel_execute on each hologram (same arithmetic), across FFT
+lengths 64..4096 in one launch, more holograms than intermediate slots,
+changing hologram counts and repeated calls.  A host-poisoned work queue
+must end the launch through its bounded waits and be reported as
+SF_ERR_TIMEOUT.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import view, random_field, WAVELENGTH, PITCH
+from helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1001_4309_gb300 import build as b
+    b.build()
+    import paper_1001_4309_gb300 as P
+    return P
+
+
+N0 = (300, 280)
+
+
+def ragged_views():
+    rng = np.random.default_rng(11)
+    sizes = [(300, 280), (64, 512), (1000, 30), (7, 3), (2000, 16), (33, 65), (200, 200)]
+    out = []
+    for k, n1 in enumerate(sizes):
+        out.append(view(WAVELENGTH, float(rng.uniform(0.02, 0.12)), PITCH,
+                        float(np.exp(rng.uniform(np.log(0.25e-6), np.log(9.3e-6)))),
+                        o1=tuple(rng.uniform(-2e-3, 2e-3, size=2)), n0=N0, n1=n1))
+    return out
+
+
+def holograms(n, shape=N0, seed=0):
+    import torch
+    return [torch.from_numpy(random_field(shape[1], shape[0], seed=seed + h).real.astype(np.float32)).cuda()
+            for h in range(n)]
+
+
+def per_hologram(sf, holos):
+    import torch
+    res = []
+    for h in holos:
+        o = sf.reconstruct(h, field=True, intensity=True)
+        res.append(([f.clone() for f in o["field"]], [i.clone() for i in o["intensity"]]))
+    torch.cuda.synchronize()
+    return res
+
+
+def check_equal(outs, ref):
+    for h, (f_ref, i_ref) in enumerate(ref):
+        for v in range(len(f_ref)):
+            assert np.array_equal(outs["field"][h][v].cpu().numpy(), f_ref[v].cpu().numpy()), (h, v)
+            assert np.array_equal(outs["intensity"][h][v].cpu().numpy(), i_ref[v].cpu().numpy()), (h, v)
+
+
+def test_batch_equals_per_hologram_execute(P):
+    import torch
+    vs = ragged_views()
+    sf = P.ShiftedFresnel(vs)
+    try:
+        lengths = {sf.sizes(i)[0] for i in range(len(vs))} | {sf.sizes(i)[1] for i in range(len(vs))}
+        assert min(lengths) <= 512 and 4096 in lengths
+        holos = holograms(5)
+        ref = per_hologram(sf, holos)
+        outs = sf.alloc_batch_outputs(5, field=True, intensity=True)
+        sf.execute_batch(holos, outs)
+        assert P.shifted_fresnel_batch_status(sf.handle, torch.cuda.current_stream().cuda_stream) == P.SF_OK
+        check_equal(outs, ref)
+        # a different hologram count rebuilds the graph; the original count again reuses a new one
+        outs2 = sf.alloc_batch_outputs(2, field=True, intensity=True)
+        sf.execute_batch(holos[3:], outs2)
+        torch.cuda.synchronize()
+        check_equal(outs2, ref[3:])
+        for _ in range(3):  # repeated calls alternate the pinned descriptor tables
+            sf.execute_batch(holos, outs)
+        torch.cuda.synchronize()
+        check_equal(outs, ref)
+        # and the batch agrees with the oracle on a sampled view
+        h_np = holos[4].cpu().numpy()
+        v = vs[0]
+        cols = (140, 148)
+        got = outs["field"][4][0].cpu().numpy()[:, cols[0]:cols[1]]
+        assert rel_l2(got, oracle.forward(h_np, v, cols=cols)) <= 1e-5
+    finally:
+        sf.close()
+
+
+def test_batch_paper_sized_ragged_views(P):
+    """2048^2 holograms with views of 256^2 .. 2048^2 (FFT lengths 4096)."""
+    import torch
+    _, all_views = synth.config_c3(n_holos=1, n_views=64, with_holograms=False)
+    picked = {}
+    for v in all_views[0]:
+        picked.setdefault(v["nx1"], v)
+    vs = [picked[k] for k in sorted(picked)]
+    holos = [torch.from_numpy(synth.gabor_hologram(2048, seed=2000 + h, kind="target_blobs", photons=2000)).cuda()
+             for h in range(3)]
+    sf = P.ShiftedFresnel(vs)
+    try:
+        ref = per_hologram(sf, holos)
+        outs = sf.alloc_batch_outputs(3, field=True, intensity=True)
+        sf.execute_batch(holos, outs)
+        torch.cuda.synchronize()
+        check_equal(outs, ref)
+    finally:
+        sf.close()
+
+
+def test_batch_rejects_bad_arguments(P):
+    import torch
+    vs = ragged_views()[:2]
+    sf = P.ShiftedFresnel(vs)
+    try:
+        h = holograms(1)
+        f = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64, device="cuda") for v in vs]
+        rc = P.shifted_fresnel_execute_batch(sf.handle, [h[0].data_ptr()], [f[0].data_ptr(), None], check=False)
+        assert rc == P.SF_ERR_INVALID_ARG  # a (hologram, view) without outputs
+        host = torch.empty_like(f[0], device="cpu")
+        rc = P.shifted_fresnel_execute_batch(sf.handle, [h[0].data_ptr()], [host.data_ptr(), f[1].data_ptr()],
+                                             check=False)
+        assert rc == P.SF_ERR_INVALID_ARG  # host memory is not staged by the batch path
+        assert P.shifted_fresnel_execute_batch(sf.handle, [], None, check=False) == P.SF_ERR_INVALID_ARG
+    finally:
+        sf.close()
+    big = view(WAVELENGTH, 0.05, PITCH, PITCH, n0=(4000, 4), n1=(200, 4))  # FFT length 8192
+    sfb = P.ShiftedFresnel([big])
+    try:
+        hb = torch.zeros((4, 4000), dtype=torch.float32, device="cuda")
+        fb = torch.empty((4, 200), dtype=torch.complex64, device="cuda")
+        rc = P.shifted_fresnel_execute_batch(sfb.handle, [hb.data_ptr()], [fb.data_ptr()], check=False)
+        assert rc == P.SF_ERR_UNSUPPORTED_SIZE
+    finally:
+        sfb.close()
+
+
+def test_poisoned_queue_times_out_and_is_reported(P):
+    """A dependency the host makes unsatisfiable ends the launch through the bounded waits."""
+    import torch
+    vs = ragged_views()[:3]
+    os.environ["SF_BATCH_POISON_GROUP"] = str(len(vs))  # the first y-pass group never sees its x tiles
+    os.environ["SF_BATCH_SPIN_LIMIT"] = "2000"
+    try:
+        sf = P.ShiftedFresnel(vs)
+        outs = sf.alloc_batch_outputs(2, field=True)
+        sf.execute_batch(holograms(2), outs)
+        s = torch.cuda.current_stream().cuda_stream
+        assert P.shifted_fresnel_batch_status(sf.handle, s) == P.SF_ERR_TIMEOUT
+        assert P.shifted_fresnel_batch_status(sf.handle, s) == P.SF_OK  # cleared
+        sf.close()
+    finally:
+        del os.environ["SF_BATCH_POISON_GROUP"]
+        del os.environ["SF_BATCH_SPIN_LIMIT"]
+    # the context is still usable
+    sf = P.ShiftedFresnel(vs)
+    try:
+        holos = holograms(2)
+        ref = per_hologram(sf, holos)
+        outs = sf.alloc_batch_outputs(2, field=True, intensity=True)
+        sf.execute_batch(holos, outs)
+        torch.cuda.synchronize()
+        check_equal(outs, ref)
+    finally:
+        sf.close()
