@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="minimum oracle time for cpu_baseline")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
@@ -274,6 +275,7 @@ def run_ours(a):
            "path": "shifted_fresnel_execute with pinned host buffers (library-staged copies), stream sync per step"}
 
     plain = plain_path(holo, views, outs, flush, stream, a, step_bytes, float(peaks["hbm_gbs"]), value / world)
+    batched = None if a.no_batch else batched_runs(holo_np, views, dev, stream, flush, float(peaks["hbm_gbs"]))
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -296,11 +298,79 @@ def run_ours(a):
             "step_nominal_tflops": round(step_flops / (ms_per_step * 1e-3) / 1e12, 2),
             "passes": passes,
             "plain_path": plain,
+            "batched": batched,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def batch_bytes(views, n_holos):
+    """Algorithmic bytes of n_holos holograms through a view set (hologram read once per hologram)."""
+    v0 = views[0]
+    per_holo = 4 * v0["nx0"] * v0["ny0"] + sum(16 * v["ny0"] * v["nx1"] + 8 * v["ny1"] * v["nx1"] for v in views)
+    return n_holos * per_holo
+
+
+def time_batch(sf, holos, outs, stream, flush, reps):
+    import torch
+    import paper_1001_4309_gb300 as P
+    for _ in range(2):
+        sf.execute_batch(holos, outs)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sf.execute_batch(holos, outs)
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    if P.shifted_fresnel_batch_status(sf.handle, stream.cuda_stream) != 0:
+        raise RuntimeError("batched launch reported a timeout")
+    return sum(x.elapsed_time(y) for x, y in ms) / reps
+
+
+def batched_runs(holo_np, views, dev, stream, flush, hbm_peak):
+    """Whole batches in one persistent graph launch (shifted_fresnel_execute_batch)."""
+    import torch
+    import synth
+    import paper_1001_4309_gb300 as P
+    res = {}
+    # 16-hologram stream of the paper-scale 4-view set
+    H = 16
+    sf = P.ShiftedFresnel(views, device=dev.index)
+    holos = [torch.from_numpy(holo_np).to(dev) for _ in range(H)]
+    outs = sf.alloc_batch_outputs(H, field=True)
+    ms = time_batch(sf, holos, outs, stream, flush, 20)
+    b = batch_bytes(views, H)
+    res["stream_1024_4views"] = {
+        "workload": "16 holograms x the 1024^2 four-view set per launch", "value": round(H * len(views) / (ms * 1e-3), 1),
+        "unit": UNIT, "ms_per_launch": round(ms, 4), "hbm_frac": round(b / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    del outs, holos
+    sf.close()
+    # ragged: 2048^2 holograms, 64 views with N1 in {256, 512, 1024, 2048}
+    _, vsets = synth.config_c3(n_holos=1, n_views=64, with_holograms=False)
+    vs = vsets[0]
+    H = 16
+    base = [torch.from_numpy(synth.gabor_hologram(2048, seed=2000 + h, kind="target_blobs", photons=2000)).to(dev)
+            for h in range(2)]
+    holos = [base[h % 2] for h in range(H)]
+    sf = P.ShiftedFresnel(vs, device=dev.index)
+    outs = sf.alloc_batch_outputs(H, field=True)
+    ms = time_batch(sf, holos, outs, stream, flush, 3)
+    b = batch_bytes(vs, H)
+    res["ragged_2048_64views"] = {
+        "workload": "16 holograms 2048^2 x 64 views (N1 in {256,512,1024,2048}, z in [2,12] cm, log-uniform "
+                    "pitch 0.25-9.3 um, offsets +-2 mm) per launch; FFT length 4096; two distinct holograms cycled",
+        "value": round(H * len(vs) / (ms * 1e-3), 1), "unit": UNIT, "ms_per_launch": round(ms, 3),
+        "hbm_frac": round(b / (ms * 1e-3) / 1e9 / hbm_peak, 4), "algorithmic_bytes": b}
+    del outs, holos
+    sf.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def plain_path(holo, views, outs, flush, stream, a, step_bytes, hbm_peak, ours_per_gpu):

@@ -307,9 +307,10 @@ int batch_prepare(sf_plan p, int n_holos) {
         const ViewState& vs = p->views[v];
         const int L = vs.ax[ph].L;
         if (!batch_length_supported(L)) return SF_ERR_UNSUPPORTED_SIZE;
-        const int rows = ph == 0 ? vs.v.ny0 : vs.v.nx1, G = batch_tile_rows(L);
-        b.groups.push_back({first, (rows + G - 1) / G, L, ph});
-        first += (rows + G - 1) / G;
+        const int rows = ph == 0 ? vs.v.ny0 : vs.v.nx1, G = batch_tile_rows(L), chunk = batch_item_tiles(L);
+        const int tiles = (rows + G - 1) / G, items = (tiles + chunk - 1) / chunk;
+        b.groups.push_back({first, items, tiles, chunk, L, ph});
+        first += items;
       }
     b.items_per_holo = first;
     Arena ar;

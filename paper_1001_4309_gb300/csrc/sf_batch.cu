@@ -71,10 +71,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const __grid_constan
         int target = 0;
         if (g >= a.n_views) {
           cnt = a.done + (size_t)h * a.n_groups + (g - a.n_views);
-          target = a.groups[g - a.n_views].tiles;
+          target = a.groups[g - a.n_views].items;
         } else if (h >= 2) {
           cnt = a.done + (size_t)(h - 2) * a.n_groups + (g + a.n_views);
-          target = a.groups[g + a.n_views].tiles;
+          target = a.groups[g + a.n_views].items;
         }
         if (g == a.poison_group) target = 0x7fffffff;  // host-injected never-satisfied dependency (tests)
         if (cnt) {
@@ -99,10 +99,18 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const __grid_constan
     const int h = item / a.items_per_holo;
     const BatchGroup gi = a.groups[g];
     const PassDesc& d = a.descs[(size_t)h * a.n_groups + g];
-    run_item<KIND_X>(d, gi.phase, gi.L, item - h * a.items_per_holo - gi.first_item, smem, a.tw);
-    __threadfence();  // this thread's stores are visible device-wide before the tile is counted
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(a.done + (size_t)h * a.n_groups + g, 1);
+    const int t0 = (item - h * a.items_per_holo - gi.first_item) * gi.chunk;
+    const int t1 = min(t0 + gi.chunk, gi.tiles);
+    for (int tile = t0; tile < t1; ++tile) {
+      run_item<KIND_X>(d, gi.phase, gi.L, tile, smem, a.tw);
+      __syncthreads();  // the next tile reuses the shared tile buffer
+    }
+    // The barrier orders every thread's stores before thread 0's device-scope
+    // fence and count (the pattern of a grid-wide barrier).
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(a.done + (size_t)h * a.n_groups + g, 1);
+    }
   }
 }
 
@@ -121,6 +129,13 @@ int batch_tile_rows(int L) {
     case 4096: return PassShape<4096>::G;
     default: return 0;
   }
+}
+
+// Tiles per work item: items carry at least 8 rows so the dequeue, dependency
+// check and completion count are amortised over several tiles.
+int batch_item_tiles(int L) {
+  const int g = batch_tile_rows(L);
+  return g >= 8 ? 1 : 8 / g;
 }
 
 size_t batch_smem_bytes() {

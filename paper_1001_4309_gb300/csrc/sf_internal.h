@@ -54,15 +54,17 @@ struct AxisCoef {
 // Persistent batch kernel (sf_batch.cu)
 constexpr int kBatchThreads = 256;
 struct BatchGroup {
-  int first_item;  // index of the group's first tile within one hologram's items
-  int tiles;       // tiles of the group
+  int first_item;  // index of the group's first item within one hologram's items
+  int items;       // items of the group (each `chunk` tiles, the last one possibly fewer)
+  int tiles;       // row tiles of the group
+  int chunk;       // tiles per item
   int L;           // FFT length
   int phase;       // 0: x pass, 1: y pass
 };
 struct BatchArgs {
   const PassDesc* descs;     // [n_holos][n_groups]
   const BatchGroup* groups;  // [n_groups] (x groups of views 0..V-1, then y groups)
-  int* done;                 // [n_holos][n_groups] completed tiles
+  int* done;                 // [n_holos][n_groups] completed items
   int* next;                 // item counter
   int* error;                // set to 1 when a bounded wait expires
   const float4* tw[13];      // per-stage twiddle tables indexed by log2(L)
@@ -72,6 +74,7 @@ struct BatchArgs {
 };
 bool batch_length_supported(int L);
 int batch_tile_rows(int L);
+int batch_item_tiles(int L);
 size_t batch_smem_bytes();
 const void* batch_kernel(PassKind kind_x);
 
