@@ -14,7 +14,8 @@
 // Every awaited item has a smaller index, was therefore taken earlier by a
 // running CTA, and itself only waits on smaller indices: the lowest
 // unfinished item never waits, so the launch always progresses, whatever
-// the number of resident CTAs.  Waits are still bounded (spin_limit sleeps);
+// the number of resident CTAs.  (A CTA takes its next item while working on
+// the current one; the next one is larger, so the argument still holds.)  Waits are still bounded (spin_limit sleeps);
 // on expiry a CTA sets the error word and leaves, which unblocks nobody but
 // ends every other wait by its own limit, so the launch always returns.
 #include "sf_kernels.cuh"
@@ -53,9 +54,15 @@ template <int KIND_X>
 __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const __grid_constant__ BatchArgs a) {
   extern __shared__ float2 smem[];
   __shared__ int s_item, s_group, s_stop;
+  if (threadIdx.x == 0) s_item = atomicAdd(a.next, 1);
   for (;;) {
+    __syncthreads();
+    int nxt = 0;
     if (threadIdx.x == 0) {
-      int item = atomicAdd(a.next, 1);
+      const int item = s_item;
+      // Take the following item now; its value is only needed at the end of
+      // this one, so the round trip overlaps the work (items stay in order).
+      nxt = atomicAdd(a.next, 1);
       int stop = item >= a.total_items || ld_acquire(a.error) != 0;
       int g = 0;
       if (!stop) {
@@ -89,7 +96,6 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const __grid_constan
           }
         }
       }
-      s_item = item;
       s_group = g;
       s_stop = stop;
     }
@@ -110,6 +116,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const __grid_constan
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(a.done + (size_t)h * a.n_groups + g, 1);
+      s_item = nxt;
     }
   }
 }
