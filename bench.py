@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-launch measurements")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the tensor-core precision measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="minimum oracle time for cpu_baseline")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
@@ -276,6 +277,8 @@ def run_ours(a):
 
     plain = plain_path(holo, views, outs, flush, stream, a, step_bytes, float(peaks["hbm_gbs"]), value / world)
     batched = None if a.no_batch else batched_runs(holo_np, views, dev, stream, flush, float(peaks["hbm_gbs"]))
+    mixed = None if a.no_mixed else mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes,
+                                                    float(peaks["hbm_gbs"]), value / world)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -299,6 +302,7 @@ def run_ours(a):
             "passes": passes,
             "plain_path": plain,
             "batched": batched,
+            "mixed_precision": mixed,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
@@ -370,6 +374,48 @@ def batched_runs(holo_np, views, dev, stream, flush, hbm_peak):
     del outs, holos
     sf.close()
     torch.cuda.empty_cache()
+    return res
+
+
+def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm_peak, fp32_value):
+    """The same 4-view step with the DFT stages on tensor cores; error vs the oracle on sampled columns."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1001_4309_gb300 as P
+    oracle.build()
+    cols = (500, 508)
+    refs = [oracle.forward(holo_np, v, cols=cols) for v in views]
+    res = {"fp32_value": round(fp32_value, 1)}
+    for name, prec in (("fp16tc", P.binding.SF_PREC_FP16TC), ("bf16tc", P.binding.SF_PREC_BF16TC)):
+        h = P.shifted_fresnel_plan(views, precision=prec, device=dev.index, stream=stream.cuda_stream)
+        outs = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64, device=dev) for v in views]
+        ptrs = [o.data_ptr() for o in outs]
+        for _ in range(a.warmup):
+            P.shifted_fresnel_execute(h, holo.data_ptr(), ptrs, stream=stream.cuda_stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(a.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.shifted_fresnel_execute(h, holo.data_ptr(), ptrs, stream=stream.cuda_stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(x.elapsed_time(y) for x, y in ev) / a.steps
+        errs = []
+        for o, r in zip(outs, refs):
+            g = o.cpu().numpy()[:, cols[0]:cols[1]].astype(np.complex128)
+            errs.append(float(np.linalg.norm(g - r) / np.linalg.norm(r)))
+        P.shifted_fresnel_destroy(h)
+        v = len(views) / (ms * 1e-3)
+        res[name] = {"value": round(v, 1), "unit": UNIT, "ms_per_step": round(ms, 5),
+                     "speedup_vs_fp32": round(v / fp32_value, 3),
+                     "step_hbm_frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                     "rel_l2_vs_oracle_max": float(f"{max(errs):.3e}"),
+                     "rel_l2_sample": f"columns {cols[0]}-{cols[1] - 1} of each view"}
     return res
 
 

@@ -53,7 +53,12 @@ extern "C" {
 #define SF_IN_COMPLEX 8u    /* the hologram is complex64 instead of float32 (same for every view of a plan) */
 
 /* ---- precision selector ---- */
-#define SF_PREC_FP32 0 /* FP32 FFT stages on CUDA cores; phases exact (64-bit fixed point) */
+#define SF_PREC_FP32 0   /* FP32 FFT stages on CUDA cores; phases exact (64-bit fixed point) */
+#define SF_PREC_FP16TC 1 /* radix-16/8 DFT stages as FP16 tensor-core products, FP32 accumulation */
+#define SF_PREC_BF16TC 2 /* same with BF16 operands */
+/* The tensor-core precisions apply to axes whose FFT length is 2048 or 4096;
+ * other axes, the adjoint and the batch path run in FP32.  Chirps, twiddles,
+ * spectrum and accumulation stay FP32 (phases exact) in every precision. */
 
 /* Longest linear convolution per axis: nx0 + nx1 - 1 <= SF_MAX_CONV_LENGTH. */
 #define SF_MAX_CONV_LENGTH 8192
@@ -83,7 +88,7 @@ typedef struct sf_plan_s* sf_plan;
  *   out        receives the plan handle (set to NULL on failure).
  *   views      host array of n_views view descriptions (copied; not retained).
  *   n_views    1 .. 4096.
- *   precision  SF_PREC_FP32.
+ *   precision  SF_PREC_FP32, SF_PREC_FP16TC or SF_PREC_BF16TC.
  *   device     CUDA device ordinal the plan is bound to (made current).
  *   stream     stream for the set-up kernels; the call synchronises it
  *              before returning.

@@ -9,6 +9,8 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <climits>
+#include <cstdint>
 #include <cstdlib>
 #include <map>
 #include <new>
@@ -31,6 +33,7 @@ struct ViewState {
   sf_view v;
   AxisCoef ax[2];          // [0] = x, [1] = y; device pointers into the arena
   AxisCoef adj[2];         // adjoint passes: [0] along x (nx1 -> nx0), [1] along y (ny1 -> ny0)
+  float2* hpos[2] = {nullptr, nullptr};  // kernel spectra in position order (tensor-core axes)
   float2* work = nullptr;  // [nx1][ny0] intermediate after the x pass (transposed)
   float2* st_out = nullptr;  // host-I/O staging (lazily allocated)
   float* st_int = nullptr;
@@ -65,6 +68,8 @@ struct sf_plan_s {
   bool in_complex = false;
   std::vector<ViewState> views;
   std::map<int, float4*> tw;  // per-stage twiddle tables per FFT length
+  int precision = SF_PREC_FP32;
+  uint32_t* tc_frags = nullptr;  // per-lane DFT fragments of the tensor-core pass
   void* arena = nullptr;
   void* st_holo = nullptr;
   std::vector<void*> staging;
@@ -440,7 +445,8 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   if (!out) return SF_ERR_INVALID_ARG;
   *out = nullptr;
   if (!views || n_views < 1 || n_views > kMaxViews) return SF_ERR_INVALID_ARG;
-  if (precision != SF_PREC_FP32) return SF_ERR_INVALID_ARG;
+  if (precision != SF_PREC_FP32 && precision != SF_PREC_FP16TC && precision != SF_PREC_BF16TC)
+    return SF_ERR_INVALID_ARG;
   for (int i = 0; i < n_views; ++i) {
     int rc = validate_view(views[i]);
     if (rc) return rc;
@@ -461,12 +467,14 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   p->nx0 = views[0].nx0;
   p->ny0 = views[0].ny0;
   p->in_complex = (views[0].flags & SF_IN_COMPLEX) != 0;
+  p->precision = precision;
   p->views.resize(n_views);
 
   // coefficients and arena layout
   Arena ar;
   std::map<int, size_t> tw_off;
   std::vector<size_t> off_cin(4 * n_views), off_cout(4 * n_views), off_H(4 * n_views), off_work(n_views);
+  std::vector<size_t> off_hpos(2 * n_views, SIZE_MAX);
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.v = views[i];
@@ -484,7 +492,11 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       off_H[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.L);
     }
     off_work[i] = ar.take(sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1);
+    for (int a = 0; a < 2; ++a)
+      off_hpos[2 * i + a] = (precision != SF_PREC_FP32 && tc_length_supported(vs.ax[a].L))
+                                ? ar.take(sizeof(float2) * vs.ax[a].L) : SIZE_MAX;
   }
+  const size_t off_frags = precision != SF_PREC_FP32 ? ar.take(sizeof(uint32_t) * tc_frag_words()) : SIZE_MAX;
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
   if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
     cudaGetLastError();
@@ -501,6 +513,8 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.work = reinterpret_cast<float2*>(base + off_work[i]);
+    for (int a = 0; a < 2; ++a)
+      if (off_hpos[2 * i + a] != SIZE_MAX) vs.hpos[a] = reinterpret_cast<float2*>(base + off_hpos[2 * i + a]);
     for (int a = 0; a < 2; ++a) {
       AxisCoef& c = vs.ax[a];
       c.cin = reinterpret_cast<float2*>(base + off_cin[2 * i + a]);
@@ -534,6 +548,17 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     e = launch_hspec(axes[i].L, axes_dev + i, (int)(j - i), p->tw[axes[i].L], s);
     ++g_launches;
     i = j;
+  }
+  if (off_frags != SIZE_MAX && e == cudaSuccess) {
+    p->tc_frags = reinterpret_cast<uint32_t*>(base + off_frags);
+    e = launch_tc_frags(p->tc_frags, precision, s);
+    ++g_launches;
+    for (ViewState& vs : p->views)
+      for (int a = 0; a < 2 && e == cudaSuccess; ++a)
+        if (vs.hpos[a]) {
+          e = launch_hpos(vs.ax[a].L, vs.ax[a].H, vs.hpos[a], s);
+          ++g_launches;
+        }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -624,8 +649,10 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
       PassBatch b;
       std::memset(&b, 0, sizeof(b));
       int max_rows = 0;
+      int batch_view[kMaxPassBatch];
       while (i < nv && b.count < kMaxPassBatch && plan->views[order[i]].ax[axis].L == L) {
         const int vi = order[i++];
+        batch_view[b.count] = vi;
         ViewState& vs = plan->views[vi];
         const AxisCoef& c = vs.ax[axis];
         PassDesc& d = b.d[b.count++];
@@ -651,9 +678,15 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
         }
         max_rows = std::max(max_rows, d.rows);
       }
-      const int G = pass_rows_per_cta(L);
       const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
-      e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
+      if (plan->tc_frags && tc_length_supported(L)) {
+        for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[batch_view[k]].hpos[axis];
+        const int G = tc_rows_per_cta();
+        e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tw[L], plan->tc_frags, s);
+      } else {
+        const int G = pass_rows_per_cta(L);
+        e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
+      }
       ++g_launches;
     }
   }

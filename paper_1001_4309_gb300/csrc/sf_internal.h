@@ -78,6 +78,15 @@ int batch_item_tiles(int L);
 size_t batch_smem_bytes();
 const void* batch_kernel(PassKind kind_x);
 
+// Mixed-precision row pass (sf_tc.cu)
+bool tc_length_supported(int L);
+int tc_rows_per_cta();
+size_t tc_frag_words();
+cudaError_t launch_tc_frags(uint32_t* out, int prec, cudaStream_t s);
+cudaError_t launch_hpos(int L, const float2* Hreg, float2* Hpos, cudaStream_t s);
+cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, int grid_x, const float4* tw,
+                           const uint32_t* frags, cudaStream_t s);
+
 // host helpers shared by the entry points (defined in sf_api.cu)
 int validate_view(const sf_view& v);
 void axis_coefficients(const sf_view& v, int axis, AxisCoef& a);
