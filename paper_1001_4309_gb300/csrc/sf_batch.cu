@@ -33,6 +33,7 @@ template <int KIND_X>
 __device__ __forceinline__ void run_item(const PassDesc& d, int phase, int L, int tile, float2* smem,
                                          const float4* const* tw) {
 #define SF_BATCH_CASE(LL, LG)                                                                   \
+  static_assert(PassShape<LL>::THREADS == kBatchThreads, "batch tiles assume the pass CTA size"); \
   case LL:                                                                                      \
     if (phase == 0) row_tile<LL, KIND_X, false>(d, tile * PassShape<LL>::G, smem, tw[LG]);      \
     else row_tile<LL, PASS_Y, true>(d, tile * PassShape<LL>::G, smem, tw[LG]);                  \

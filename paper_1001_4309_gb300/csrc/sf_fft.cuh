@@ -302,6 +302,7 @@ __device__ __forceinline__ void stage_load(float2* v, int t, const float2* buf) 
 // group calls it the same number of times.
 template <int T>
 __device__ __forceinline__ void group_sync(int g) {
+  // callers keep 1 + g <= 15 (checked where the group count is fixed)
   if constexpr (T >= 32 && T % 32 == 0) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(T) : "memory");
   } else {

@@ -23,15 +23,26 @@
 #include "sf_fft.cuh"
 #include "sf_internal.h"
 
+#ifndef SF_PASS_CTA_THREADS
+#define SF_PASS_CTA_THREADS 256
+#endif
+#ifndef SF_PASS_MIN_WARPS
+#define SF_PASS_MIN_WARPS 16
+#endif
+
 namespace sf {
 
 template <int L>
 struct PassShape {
   static constexpr int T = L / kE;
-  static constexpr int G = (256 / T) > 0 ? (256 / T) : 1;
+  static constexpr int G = (SF_PASS_CTA_THREADS / T) > 0 ? (SF_PASS_CTA_THREADS / T) : 1;
   static constexpr int THREADS = G * T;
-  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;  // caps registers at 128 per thread
+  // CTAs per SM the register budget is set for (2 x 256 threads: 128 registers)
+  static constexpr int MIN_BLOCKS = SF_PASS_MIN_WARPS / (THREADS / 32) > 0 ? SF_PASS_MIN_WARPS / (THREADS / 32) : 1;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)G * buf_elems(L);
+  // group g synchronises on named barrier 1 + g when its T threads are whole
+  // warps; hardware barrier ids are 0..15
+  static_assert(T < 32 || T % 32 != 0 || G <= 15, "row groups need named barrier ids 1..15");
 };
 
 // exp(i pi ph / 2^63) from a 64-bit fixed-point phase (full scale 2^64 = 2 pi).

@@ -82,21 +82,21 @@ __device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const uint16
 // W_{M'}^{n k} of stage S (conjugated when CONJ), from the FP32 network's table.
 template <int L, int S, bool CONJ>
 __device__ __forceinline__ float2 twiddle(const float4* __restrict__ tw, int n, int k) {
-  using St = Stage<L, kE, S>;
-  const float4 w = __ldg(tw + stage_tw_offset(L, kE, S) + (k >> 1) * St::M + n);
+  using St = Stage<L, kTcE, S>;
+  const float4 w = __ldg(tw + stage_tw_offset(L, kTcE, S) + (k >> 1) * St::M + n);
   const float2 v = (k & 1) ? make_float2(w.z, w.w) : make_float2(w.x, w.y);
   return CONJ ? make_float2(v.x, -v.y) : v;
 }
 
 template <int L, int S>
 __device__ __forceinline__ int pos_of(int b, int k) {
-  using St = Stage<L, kE, S>;
+  using St = Stage<L, kTcE, S>;
   return (b / St::M) * St::MP + (b % St::M) + k * St::M;
 }
 
 template <int L, int S>
 __device__ __forceinline__ void bk_of(int p, int& b, int& k) {
-  using St = Stage<L, kE, S>;
+  using St = Stage<L, kTcE, S>;
   const int K = p / St::MP, rem = p - K * St::MP;
   const int n = rem % St::M;
   k = rem / St::M;
@@ -106,7 +106,7 @@ __device__ __forceinline__ void bk_of(int p, int& b, int& k) {
 // Store one complex value at position p of row `row` in stage S's input layout.
 template <int L, int S, int PREC>
 __device__ __forceinline__ void put(uint16_t* buf, int row, int p, float2 v) {
-  constexpr int R = Stage<L, kE, S>::R;
+  constexpr int R = Stage<L, kTcE, S>::R;
   int b, k;
   bk_of<L, S>(p, b, k);
   uint16_t* q = buf + row * TcShape<L>::BUF + b * bstride<R>();
@@ -120,7 +120,7 @@ __host__ __device__ constexpr int frag_words(int R) { return 2 * (R / 8) * (R / 
 // One stage's GEMM over all rows of the CTA; epi(row, butterfly, element, value).
 template <int L, int S, int PREC, bool INV, typename Epi>
 __device__ __forceinline__ void stage_gemm(const uint16_t* in, const uint32_t* __restrict__ frags, Epi&& epi) {
-  using St = Stage<L, kE, S>;
+  using St = Stage<L, kTcE, S>;
   constexpr int R = St::R;
   static_assert(R == 16 || R == 8, "tensor-core stages need radix 8 or 16");
   constexpr int NT = L / R / 8;   // n-tiles (8 butterflies) per row
@@ -175,8 +175,8 @@ template <int L, int S, int PREC>
 __device__ __forceinline__ uint16_t* forward(uint16_t* cur, uint16_t* oth, const uint32_t* frags,
                                              const float4* __restrict__ tw, const float2* __restrict__ Hpos,
                                              float hs) {
-  using St = Stage<L, kE, S>;
-  constexpr int NS = stage_count(L, kE);
+  using St = Stage<L, kTcE, S>;
+  constexpr int NS = stage_count(L, kTcE);
   constexpr float f = inv_sqrt_radix<St::R>();
   if constexpr (S + 1 < NS) {
     stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 v) {
@@ -202,10 +202,10 @@ __device__ __forceinline__ uint16_t* forward(uint16_t* cur, uint16_t* oth, const
 template <int L, int S, int PREC, typename Out>
 __device__ __forceinline__ void inverse(uint16_t* cur, uint16_t* oth, const uint32_t* frags,
                                         const float4* __restrict__ tw, Out&& out) {
-  using St = Stage<L, kE, S>;
+  using St = Stage<L, kTcE, S>;
   constexpr float f = inv_sqrt_radix<St::R>();
   if constexpr (S > 0) {
-    using Sp = Stage<L, kE, S - 1>;
+    using Sp = Stage<L, kTcE, S - 1>;
     stage_gemm<L, S, PREC, true>(cur, frags, [&](int row, int b, int k, float2 v) {
       const int p = pos_of<L, S>(b, k);
       int bp, kp;
@@ -282,7 +282,7 @@ k_pass_tc(const __grid_constant__ PassBatch pb, const float4* __restrict__ tw, c
   uint16_t* spec = forward<L, 0, PREC>(buf0, buf1, frags, tw, reinterpret_cast<const float2*>(d.H), hs);
   uint16_t* other = spec == buf0 ? buf1 : buf0;
   const float undo = (float)L * sqrtf((float)L);  // the three 1/sqrt(L) scales
-  inverse<L, stage_count(L, kE) - 1, PREC>(spec, other, frags, tw, [&](int r, int p, float2 v) {
+  inverse<L, stage_count(L, kTcE) - 1, PREC>(spec, other, frags, tw, [&](int r, int p, float2 v) {
     const int row = row0 + r;
     if (row >= d.rows || p >= d.n1) return;
     const float s = undo * __uint_as_float(rowmax[r]);
@@ -373,7 +373,9 @@ cudaError_t launch_tc_t(PassKind kind, const PassBatch& b, int grid_x, const flo
 
 }  // namespace tc
 
-bool tc_length_supported(int L) { return L == 2048 || L == 4096; }
+// The spectrum is converted from the FP32 network's register order, so both
+// networks must share their radix plan.
+bool tc_length_supported(int L) { return kE == kTcE && (L == 2048 || L == 4096); }
 int tc_rows_per_cta() { return tc::kRows; }
 size_t tc_frag_words() { return (size_t)tc::frag_words(16) + tc::frag_words(8); }
 
