@@ -115,9 +115,12 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
  *
  * Each of holo and the output buffers may be device memory or host memory
  * (pinned or pageable).  Host buffers are staged through plan-owned device
- * buffers that the first call with a host buffer allocates; their copies are
- * ordered on the stream, so the caller synchronises the stream before
- * reading host outputs.  Every view needs at least one non-NULL output.
+ * buffers that the first call with a host buffer allocates.  With host
+ * outputs the y passes run one view at a time and each view's copies to the
+ * host start on a plan-owned copy stream as soon as that view is done,
+ * overlapping the rest of the computation; the caller's stream waits for the
+ * last copy, so the caller synchronises its stream before reading host
+ * outputs.  Every view needs at least one non-NULL output.
  * Errors: SF_ERR_INVALID_ARG, SF_ERR_DEVICE_MISMATCH, SF_ERR_OOM, SF_ERR_CUDA.
  */
 int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out,

@@ -84,6 +84,10 @@ struct sf_plan_s {
   double2* adj_part = nullptr;  // kZGradBlocks x 5 partial sums
   double* adj_z = nullptr;      // n_views dL/dz values
   BatchState batch;
+  // host-output overlap: a copy stream and one event per view, created on first use
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> view_done;
+  cudaEvent_t copies_done = nullptr;
 };
 
 namespace sf {
@@ -226,6 +230,9 @@ void free_batch_sized(BatchState& b) {
 
 void free_plan(sf_plan p) {
   if (!p) return;
+  for (cudaEvent_t e : p->view_done) cudaEventDestroy(e);
+  if (p->copies_done) cudaEventDestroy(p->copies_done);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   free_batch_sized(p->batch);
   for (int k = 0; k < 2; ++k)
     if (p->batch.ev[k]) cudaEventDestroy(p->batch.ev[k]);
@@ -233,6 +240,32 @@ void free_plan(sf_plan p) {
   for (void* s : p->staging) cudaFree(s);
   if (p->arena) cudaFree(p->arena);
   delete p;
+}
+
+// Copy stream and events for overlapping device-to-host copies with compute.
+int ensure_copy_resources(sf_plan p) {
+  if (p->copy_stream) return SF_OK;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  std::vector<cudaEvent_t> ev(p->views.size(), nullptr);
+  cudaEvent_t done = nullptr;
+  bool ok = cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess;
+  for (size_t i = 0; ok && i < ev.size(); ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    if (done) cudaEventDestroy(done);
+    cudaStreamDestroy(cs);
+    return SF_ERR_CUDA;
+  }
+  p->copy_stream = cs;
+  p->view_done = ev;
+  p->copies_done = done;
+  return SF_OK;
 }
 
 int stage_alloc(sf_plan p, void** out, size_t bytes) {
@@ -609,7 +642,7 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   }
 
   // outputs: resolve staging for host buffers
-  struct Copy { void* dst; const void* src; size_t bytes; };
+  struct Copy { void* dst; const void* src; size_t bytes; int view; };
   std::vector<Copy> d2h;
   std::vector<float2*> dout(nv, nullptr);
   std::vector<float*> dint(nv, nullptr), dph(nv, nullptr);
@@ -623,7 +656,7 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
         case PTR_HOST: {
           int rc = stage_alloc(plan, stage, bytes);
           if (rc) return rc;
-          d2h.push_back({user, *stage, bytes});
+          d2h.push_back({user, *stage, bytes, i});
           *dev = *stage;
           return SF_OK;
         }
@@ -636,7 +669,14 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
     if (rc) return rc;
   }
 
-  // x passes then y passes, each grouped by FFT length
+  // x passes then y passes, each grouped by FFT length.  With host outputs the
+  // y passes run one view per launch and each view's copies start on the copy
+  // stream as soon as its pass is done, overlapping the remaining compute.
+  const bool overlap = !d2h.empty();
+  if (overlap) {
+    int rc = ensure_copy_resources(plan);
+    if (rc) return rc;
+  }
   if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);
   for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
     if (axis == 1 && plan->prof[1]) e = cudaEventRecord(plan->prof[1], s);
@@ -650,7 +690,8 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
       std::memset(&b, 0, sizeof(b));
       int max_rows = 0;
       int batch_view[kMaxPassBatch];
-      while (i < nv && b.count < kMaxPassBatch && plan->views[order[i]].ax[axis].L == L) {
+      const int max_count = (overlap && axis == 1) ? 1 : kMaxPassBatch;
+      while (i < nv && b.count < max_count && plan->views[order[i]].ax[axis].L == L) {
         const int vi = order[i++];
         batch_view[b.count] = vi;
         ViewState& vs = plan->views[vi];
@@ -688,11 +729,22 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
         e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
       }
       ++g_launches;
+      if (overlap && axis == 1 && e == cudaSuccess) {
+        const int vi = batch_view[0];
+        e = cudaEventRecord(plan->view_done[vi], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->copy_stream, plan->view_done[vi], 0);
+        for (const Copy& c : d2h)
+          if (e == cudaSuccess && c.view == vi)
+            e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
+      }
     }
   }
   if (e == cudaSuccess && plan->prof[2]) e = cudaEventRecord(plan->prof[2], s);
-  for (const Copy& c : d2h)
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, s);
+  if (overlap && e == cudaSuccess) {
+    // the caller's stream resumes after the last copy
+    e = cudaEventRecord(plan->copies_done, plan->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->copies_done, 0);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SF_ERR_CUDA;
