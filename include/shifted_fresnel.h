@@ -121,6 +121,12 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
  * overlapping the rest of the computation; the caller's stream waits for the
  * last copy, so the caller synchronises its stream before reading host
  * outputs.  Every view needs at least one non-NULL output.
+ * Implementation: each pass runs a one-tile-per-CTA kernel, or, where the
+ * plan chose it (SF_PASS_IMPL=tma or the autotuner, see
+ * shifted_fresnel_fft_length) and the rows' address, stride and length are
+ * multiples of 16 bytes (FFT length 256 .. 4096), a persistent kernel that
+ * prefetches the next rows with bulk copies while transforming the current
+ * ones.
  * Errors: SF_ERR_INVALID_ARG, SF_ERR_DEVICE_MISMATCH, SF_ERR_OOM, SF_ERR_CUDA.
  */
 int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out,
@@ -163,8 +169,10 @@ int shifted_fresnel_execute_batch(sf_plan plan, const void* const* holos, int n_
 
 /*
  * shifted_fresnel_batch_status -- synchronise `stream` and report whether a
- * bounded wait of an earlier batch launch expired (SF_ERR_TIMEOUT, after
- * which the flag is cleared) or not (SF_OK).
+ * bounded device-side wait of an earlier launch on this plan expired
+ * (SF_ERR_TIMEOUT, after which the flag is cleared) or not (SF_OK).  It
+ * covers the persistent batch kernel and the persistent row pass that
+ * execute uses for 16-byte aligned rows (whose copy waits are bounded too).
  */
 int shifted_fresnel_batch_status(sf_plan plan, void* stream);
 
@@ -277,6 +285,31 @@ int shifted_fresnel_execute_static(const sf_view* view, const void* holo, void* 
  * launched in this process so far (all plans, all devices).
  */
 uint64_t shifted_fresnel_kernel_launches(void);
+
+/*
+ * shifted_fresnel_fft_length -- the FFT length a plan uses, without tuning,
+ * for an axis whose linear convolution has `need` = n0 + n1 - 1 samples
+ * (Section 2.2, step 2: zero padding so the circular convolution equals the
+ * linear one; the paper pads 1024 to 2048 = 2N).  Supported lengths are the
+ * powers of two 64 .. 8192 and 1536, 2304, 3072, 4608, 6144 (3 x 2^k and
+ * 9 x 2^8, whose FFT network starts with a radix-24 stage); allow_mixed = 0
+ * restricts the choice to powers of two.  Pure host function, no device
+ * needed.  Returns the length, SF_ERR_INVALID_ARG for need < 1, or
+ * SF_ERR_UNSUPPORTED_SIZE above SF_MAX_CONV_LENGTH.
+ *
+ * Plan-time choices (environment, read by shifted_fresnel_plan):
+ *   SF_FFT_LENGTHS=pow2   powers of two only.
+ *   SF_PASS_IMPL=tma      persistent row-pass kernel for every eligible pass.
+ *   SF_AUTOTUNE=1         measure instead: per axis the cheaper of the two
+ *                         candidate lengths (next power of two, next length
+ *                         with a factor 3), per (length, pass kind) the
+ *                         cheaper row-pass kernel, by the time per row of a
+ *                         synthetic pass timed once per device and process.
+ *   SF_AUTOTUNE_CACHE=path  file the measurements are read from and appended
+ *                         to (one "device L kind kernel ns_per_row" line each).
+ * All choices compute the same convolution; results differ by rounding only.
+ */
+int32_t shifted_fresnel_fft_length(int32_t need, int32_t allow_mixed);
 
 #ifdef __cplusplus
 }

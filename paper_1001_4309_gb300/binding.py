@@ -89,6 +89,8 @@ def load():
     lib.shifted_fresnel_adjoint.restype = ctypes.c_int
     lib.shifted_fresnel_set_profile_events.argtypes = [vp, pp, ctypes.c_int]
     lib.shifted_fresnel_set_profile_events.restype = ctypes.c_int
+    lib.shifted_fresnel_fft_length.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.shifted_fresnel_fft_length.restype = ctypes.c_int32
     for f in ("shifted_fresnel_plan", "shifted_fresnel_execute", "shifted_fresnel_destroy",
               "shifted_fresnel_plan_query"):
         getattr(lib, f).restype = ctypes.c_int
@@ -210,6 +212,11 @@ def shifted_fresnel_set_profile_events(plan, events):
 
 def shifted_fresnel_kernel_launches():
     return int(load().shifted_fresnel_kernel_launches())
+
+
+def shifted_fresnel_fft_length(need, allow_mixed=True):
+    """FFT length an untuned plan uses for an axis with n0 + n1 - 1 = need (negative status on error)."""
+    return int(load().shifted_fresnel_fft_length(int(need), 1 if allow_mixed else 0))
 
 
 class ShiftedFresnel:

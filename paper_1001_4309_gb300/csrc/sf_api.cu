@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <map>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -70,6 +71,9 @@ struct sf_plan_s {
   std::map<int, float4*> tw;  // per-stage twiddle tables per FFT length
   int precision = SF_PREC_FP32;
   uint32_t* tc_frags = nullptr;  // per-lane DFT fragments of the tensor-core pass
+  int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
+  int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA
+  int sms = 0;
   void* arena = nullptr;
   void* st_holo = nullptr;
   std::vector<void*> staging;
@@ -103,10 +107,12 @@ uint64_t to_fx(double c) {
   return (uint64_t)s;
 }
 
-int next_fft_length(int need) {
-  int L = kMinFFT;
-  while (L < need) L <<= 1;
-  return L;
+int next_fft_length(int need, bool allow_mixed) {
+  for (int i = 0; i < kNumFftLengths; ++i) {
+    const int L = kFftLengths[i];
+    if (L >= std::max(need, kMinFFT) && (allow_mixed || (L & (L - 1)) == 0)) return L;
+  }
+  return 0;
 }
 
 int validate_view(const sf_view& v) {
@@ -126,7 +132,7 @@ int validate_view(const sf_view& v) {
 //   beta (x1 - x0)^2 = S (m1 - m0)^2 + psi_in(m0) + psi_out(m1)
 //   psi_in(m0)  = (beta p0^2 - S) m0^2 - 2 beta p0 D m0
 //   psi_out(m1) = (beta p1^2 - S) m1^2 + 2 beta p1 D m1 + beta D^2
-void axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
+void axis_coefficients(const sf_view& v, int axis, AxisCoef& a, int L) {
   const double lam = v.wavelength, z = v.z, beta = 1.0 / (lam * z);
   const int n0 = axis == 0 ? v.nx0 : v.ny0, n1 = axis == 0 ? v.nx1 : v.ny1;
   const double p0 = axis == 0 ? v.px0 : v.py0, p1 = axis == 0 ? v.px1 : v.py1;
@@ -135,7 +141,7 @@ void axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
   const double D = a1 - a0, S = p0 * p1 * beta;
   a.n0 = n0;
   a.n1 = n1;
-  a.L = next_fft_length(n0 + n1 - 1);
+  a.L = L > 0 ? L : next_fft_length(n0 + n1 - 1, true);
   a.in2 = to_fx(beta * p0 * p0 - S);
   a.in1 = to_fx(-2.0 * beta * p0 * D);
   a.in0 = 0;
@@ -158,9 +164,9 @@ void axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
 // T^H is the Toeplitz operator of conj(h) with the lengths swapped) and whose
 // output chirp is the conjugate of the forward input chirp, with the same
 // real scale (1/L, and 1/(lambda z) on y).
-void adjoint_axis_coefficients(const sf_view& v, int axis, AxisCoef& a) {
+void adjoint_axis_coefficients(const sf_view& v, int axis, AxisCoef& a, int L) {
   AxisCoef f;
-  axis_coefficients(v, axis, f);
+  axis_coefficients(v, axis, f, L);
   a = f;
   a.n0 = f.n1;
   a.n1 = f.n0;
@@ -354,7 +360,7 @@ int batch_prepare(sf_plan p, int n_holos) {
     Arena ar;
     std::vector<size_t> off(nv);
     for (int v = 0; v < nv; ++v) off[v] = ar.take(sizeof(float2) * (size_t)p->views[v].v.ny0 * p->views[v].v.nx1);
-    const size_t o_groups = ar.take(sizeof(BatchGroup) * b.groups.size()), o_err = ar.take(sizeof(int));
+    const size_t o_groups = ar.take(sizeof(BatchGroup) * b.groups.size());
     if (cudaMalloc(&b.d_fixed, ar.off) != cudaSuccess) {
       cudaGetLastError();
       return SF_ERR_OOM;
@@ -363,10 +369,9 @@ int batch_prepare(sf_plan p, int n_holos) {
     b.slot1.resize(nv);
     for (int v = 0; v < nv; ++v) b.slot1[v] = reinterpret_cast<float2*>(base + off[v]);
     b.d_groups = reinterpret_cast<BatchGroup*>(base + o_groups);
-    b.d_error = reinterpret_cast<int*>(base + o_err);
+    b.d_error = p->dev_err;
     if (cudaMemcpy(b.d_groups, b.groups.data(), sizeof(BatchGroup) * b.groups.size(), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemset(b.d_error, 0, sizeof(int)) != cudaSuccess)
+        cudaSuccess)
       return SF_ERR_CUDA;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -401,9 +406,8 @@ int batch_prepare(sf_plan p, int n_holos) {
   args.next = b.d_done + n_desc;
   args.error = b.d_error;
   for (auto& kv : p->tw) {
-    int lg = 0;
-    while ((1 << lg) < kv.first) ++lg;
-    if (lg < 13) args.tw[lg] = kv.second;
+    const int slot = fft_length_slot(kv.first);
+    if (slot >= 0) args.tw[slot] = kv.second;
   }
   args.n_holos = n_holos;
   args.n_groups = ng;
@@ -454,9 +458,90 @@ int batch_prepare(sf_plan p, int n_holos) {
   return SF_OK;
 }
 
+// The persistent TMA pass: chosen for (L, kind) at plan time, and it needs
+// 16-byte aligned rows, row strides and row lengths.
+bool persistent_eligible(sf_plan p, int L, PassKind kind, const PassBatch& b) {
+  const int slot = fft_length_slot(L);
+  if (slot < 0 || p->impl[slot][kind] != 1 || !tma_length_supported(L)) return false;
+  const size_t elem = kind == PASS_X_REAL ? 4 : 8;
+  for (int k = 0; k < b.count; ++k) {
+    const PassDesc& d = b.d[k];
+    if (reinterpret_cast<uintptr_t>(d.src) % 16 || (d.src_ld * elem) % 16 || (d.n0 * elem) % 16) return false;
+  }
+  return true;
+}
+
+// FFT length per (view, axis) and row-pass kernel per (length, kind).
+//   default: the smallest supported length (SF_FFT_LENGTHS=pow2 keeps powers
+//            of two only); the one-tile-per-CTA kernel (SF_PASS_IMPL=tma
+//            selects the persistent kernel where it applies);
+//   SF_AUTOTUNE=1: per axis the cheaper of the two candidate lengths, per
+//            (length, kind) the cheaper kernel, by measured time per row.
+// Tensor-core plans keep the power of two where the tensor-core pass takes it.
+struct PlanChoices {
+  std::vector<int> L;  // [2 * view + axis]
+  int impl[kNumFftLengths][3] = {};
+};
+
+PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int precision, cudaStream_t s) {
+  PlanChoices c;
+  c.L.resize(2 * n_views);
+  const char* lens = std::getenv("SF_FFT_LENGTHS");
+  const bool allow_mixed = !(lens && std::string(lens) == "pow2");
+  const char* impl_env = std::getenv("SF_PASS_IMPL");
+  const int impl_default = (impl_env && std::string(impl_env) == "tma") ? 1 : 0;
+  const bool tune = autotune_mode() == 1;
+  auto kind_of = [&](int axis) {
+    return axis == 1 ? PASS_Y : (p->in_complex ? PASS_X_CPLX : PASS_X_REAL);
+  };
+  // best measured cost of (L, kind) over the kernels, remembering the kernel
+  auto best = [&](int L, PassKind kind, int* impl) {
+    double b = -1;
+    for (int k = 0; k < 2; ++k) {
+      const double ns = row_cost_ns(p->device, L, kind, k, p->sms, s);
+      if (ns > 0 && (b < 0 || ns < b)) {
+        b = ns;
+        if (impl) *impl = k;
+      }
+    }
+    return b;
+  };
+  for (int i = 0; i < n_views; ++i)
+    for (int a = 0; a < 2; ++a) {
+      const int need = a == 0 ? views[i].nx0 + views[i].nx1 - 1 : views[i].ny0 + views[i].ny1 - 1;
+      const int P = next_fft_length(need, false), Q = allow_mixed ? next_fft_length(need, true) : P;
+      int L = Q;
+      if (precision != SF_PREC_FP32 && tc_length_supported(P)) {
+        L = P;
+      } else if (tune && Q != P) {
+        const double cp = best(P, kind_of(a), nullptr), cq = best(Q, kind_of(a), nullptr);
+        if (cp > 0 && cq > 0 && cp < cq) L = P;
+      }
+      c.L[2 * i + a] = L;
+    }
+  for (int slot = 0; slot < kNumFftLengths; ++slot)
+    for (int k = 0; k < 3; ++k) {
+      const int L = kFftLengths[slot];
+      c.impl[slot][k] = tma_length_supported(L) ? impl_default : 0;
+      if (!tune || !tma_length_supported(L)) continue;
+      bool used = false;
+      for (int i = 0; i < n_views && !used; ++i)
+        for (int a = 0; a < 2; ++a)
+          if (c.L[2 * i + a] == L && (kind_of(a) == k || (a == 0 && k == PASS_X_CPLX))) used = true;  // adjoint x: complex
+      if (used) best(L, (PassKind)k, &c.impl[slot][k]);
+    }
+  return c;
+}
+
 }  // namespace
 
 extern "C" {
+
+int32_t shifted_fresnel_fft_length(int32_t need, int32_t allow_mixed) {
+  if (need < 1) return SF_ERR_INVALID_ARG;
+  if (need > SF_MAX_CONV_LENGTH) return SF_ERR_UNSUPPORTED_SIZE;
+  return next_fft_length(need, allow_mixed != 0);
+}
 
 const char* shifted_fresnel_strerror(int status) {
   switch (status) {
@@ -503,6 +588,12 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   p->precision = precision;
   p->views.resize(n_views);
 
+  p->sms = 0;
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
+  const PlanChoices ch = plan_choices(p, views, n_views, precision, s);
+  for (int i = 0; i < kNumFftLengths; ++i)
+    for (int k = 0; k < 3; ++k) p->impl[i][k] = ch.impl[i][k];
+
   // coefficients and arena layout
   Arena ar;
   std::map<int, size_t> tw_off;
@@ -512,13 +603,13 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     ViewState& vs = p->views[i];
     vs.v = views[i];
     for (int a = 0; a < 2; ++a) {
-      axis_coefficients(vs.v, a, vs.ax[a]);
+      axis_coefficients(vs.v, a, vs.ax[a], ch.L[2 * i + a]);
       const AxisCoef& c = vs.ax[a];
       if (!tw_off.count(c.L)) tw_off[c.L] = ar.take(sizeof(float4) * twiddle_entries(c.L));
       off_cin[2 * i + a] = ar.take(sizeof(float2) * c.n0);
       off_cout[2 * i + a] = ar.take(sizeof(float2) * c.n1);
       off_H[2 * i + a] = ar.take(sizeof(float2) * c.L);
-      adjoint_axis_coefficients(vs.v, a, vs.adj[a]);
+      adjoint_axis_coefficients(vs.v, a, vs.adj[a], ch.L[2 * i + a]);
       const AxisCoef& ca = vs.adj[a];
       off_cin[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.n0);
       off_cout[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.n1);
@@ -530,6 +621,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
                                 ? ar.take(sizeof(float2) * vs.ax[a].L) : SIZE_MAX;
   }
   const size_t off_frags = precision != SF_PREC_FP32 ? ar.take(sizeof(uint32_t) * tc_frag_words()) : SIZE_MAX;
+  const size_t off_err = ar.take(sizeof(int));
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
   if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
     cudaGetLastError();
@@ -582,6 +674,8 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     ++g_launches;
     i = j;
   }
+  p->dev_err = reinterpret_cast<int*>(base + off_err);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
   if (off_frags != SIZE_MAX && e == cudaSuccess) {
     p->tc_frags = reinterpret_cast<uint32_t*>(base + off_frags);
     e = launch_tc_frags(p->tc_frags, precision, s);
@@ -724,6 +818,8 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
         for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[batch_view[k]].hpos[axis];
         const int G = tc_rows_per_cta();
         e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tw[L], plan->tc_frags, s);
+      } else if (persistent_eligible(plan, L, kind, b)) {
+        e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);
       } else {
         const int G = pass_rows_per_cta(L);
         e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
@@ -959,16 +1055,15 @@ int shifted_fresnel_execute_batch(sf_plan plan, const void* const* holos, int n_
 
 int shifted_fresnel_batch_status(sf_plan plan, void* stream) {
   if (!plan) return SF_ERR_INVALID_ARG;
-  if (!plan->batch.init) return SF_OK;
   DeviceGuard guard(plan->device);
   int err = 0;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
-      cudaMemcpy(&err, plan->batch.d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaMemcpy(&err, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaGetLastError();
     return SF_ERR_CUDA;
   }
   if (err) {
-    cudaMemset(plan->batch.d_error, 0, sizeof(int));
+    cudaMemset(plan->dev_err, 0, sizeof(int));
     return SF_ERR_TIMEOUT;
   }
   return SF_OK;

@@ -29,26 +29,49 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+// One tile of a length with a factor 3 (24 values per thread).  Not inlined:
+// under the batch kernel's 128-register budget these tiles spill a little,
+// and a separate function keeps that spill code out of the power-of-two paths.
+template <int LL, int KIND_X>
+__device__ __noinline__ void mixed_tile(const PassDesc& d, int phase, int tile, float2* smem, const float4* tw) {
+  constexpr bool spare = PassShape<LL>::THREADS < kBatchThreads;
+  if (phase == 0) row_tile<LL, KIND_X, false, spare>(d, tile * PassShape<LL>::G, smem, tw);
+  else row_tile<LL, PASS_Y, true, spare>(d, tile * PassShape<LL>::G, smem, tw);
+}
+
 template <int KIND_X>
 __device__ __forceinline__ void run_item(const PassDesc& d, int phase, int L, int tile, float2* smem,
                                          const float4* const* tw) {
-#define SF_BATCH_CASE(LL, LG)                                                                   \
-  static_assert(PassShape<LL>::THREADS == kBatchThreads, "batch tiles assume the pass CTA size"); \
-  case LL:                                                                                      \
-    if (phase == 0) row_tile<LL, KIND_X, false>(d, tile * PassShape<LL>::G, smem, tw[LG]);      \
-    else row_tile<LL, PASS_Y, true>(d, tile * PassShape<LL>::G, smem, tw[LG]);                  \
-    break;
+  // a tile of G T <= kBatchThreads threads; the rest of the CTA idles through it
+#define SF_BATCH_CASE(LL)                                                                              \
+  static_assert(PassShape<LL>::THREADS <= kBatchThreads, "batch tiles must fit the batch CTA");        \
+  case LL: {                                                                                           \
+    constexpr bool spare = PassShape<LL>::THREADS < kBatchThreads;                                     \
+    const float4* t = tw[fft_length_slot_of<LL>()];                                                    \
+    if (phase == 0) row_tile<LL, KIND_X, false, spare>(d, tile * PassShape<LL>::G, smem, t);           \
+    else row_tile<LL, PASS_Y, true, spare>(d, tile * PassShape<LL>::G, smem, t);                       \
+    break;                                                                                             \
+  }
+#define SF_BATCH_MIXED_CASE(LL)                                                                        \
+  static_assert(PassShape<LL>::THREADS <= kBatchThreads, "batch tiles must fit the batch CTA");        \
+  case LL: mixed_tile<LL, KIND_X>(d, phase, tile, smem, tw[fft_length_slot_of<LL>()]); break;
   switch (L) {
-    SF_BATCH_CASE(64, 6)
-    SF_BATCH_CASE(128, 7)
-    SF_BATCH_CASE(256, 8)
-    SF_BATCH_CASE(512, 9)
-    SF_BATCH_CASE(1024, 10)
-    SF_BATCH_CASE(2048, 11)
-    SF_BATCH_CASE(4096, 12)
+    SF_BATCH_CASE(64)
+    SF_BATCH_CASE(128)
+    SF_BATCH_CASE(256)
+    SF_BATCH_CASE(512)
+    SF_BATCH_CASE(1024)
+    SF_BATCH_MIXED_CASE(1536)
+    SF_BATCH_CASE(2048)
+    SF_BATCH_MIXED_CASE(2304)
+    SF_BATCH_MIXED_CASE(3072)
+    SF_BATCH_CASE(4096)
+    SF_BATCH_MIXED_CASE(4608)
+    SF_BATCH_MIXED_CASE(6144)
     default: break;
   }
 #undef SF_BATCH_CASE
+#undef SF_BATCH_MIXED_CASE
 }
 
 template <int KIND_X>
@@ -124,17 +147,15 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const __grid_constan
 
 }  // namespace
 
-bool batch_length_supported(int L) { return L >= 64 && L <= 4096 && (L & (L - 1)) == 0; }
+bool batch_length_supported(int L) { return fft_length_supported(L) && L <= 6144; }
 
 int batch_tile_rows(int L) {
   switch (L) {
-    case 64: return PassShape<64>::G;
-    case 128: return PassShape<128>::G;
-    case 256: return PassShape<256>::G;
-    case 512: return PassShape<512>::G;
-    case 1024: return PassShape<1024>::G;
-    case 2048: return PassShape<2048>::G;
-    case 4096: return PassShape<4096>::G;
+#define SF_BATCH_ROWS(LL) case LL: return PassShape<LL>::G;
+    SF_BATCH_ROWS(64) SF_BATCH_ROWS(128) SF_BATCH_ROWS(256) SF_BATCH_ROWS(512) SF_BATCH_ROWS(1024)
+    SF_BATCH_ROWS(1536) SF_BATCH_ROWS(2048) SF_BATCH_ROWS(2304) SF_BATCH_ROWS(3072) SF_BATCH_ROWS(4096)
+    SF_BATCH_ROWS(4608) SF_BATCH_ROWS(6144)
+#undef SF_BATCH_ROWS
     default: return 0;
   }
 }
@@ -148,13 +169,10 @@ int batch_item_tiles(int L) {
 
 size_t batch_smem_bytes() {
   size_t m = 0;
-  m = std::max(m, PassShape<64>::SMEM);
-  m = std::max(m, PassShape<128>::SMEM);
-  m = std::max(m, PassShape<256>::SMEM);
-  m = std::max(m, PassShape<512>::SMEM);
-  m = std::max(m, PassShape<1024>::SMEM);
-  m = std::max(m, PassShape<2048>::SMEM);
-  m = std::max(m, PassShape<4096>::SMEM);
+  for (size_t b : {PassShape<64>::SMEM, PassShape<128>::SMEM, PassShape<256>::SMEM, PassShape<512>::SMEM,
+                   PassShape<1024>::SMEM, PassShape<1536>::SMEM, PassShape<2048>::SMEM, PassShape<2304>::SMEM,
+                   PassShape<3072>::SMEM, PassShape<4096>::SMEM, PassShape<4608>::SMEM, PassShape<6144>::SMEM})
+    m = std::max(m, b);
   return m;
 }
 

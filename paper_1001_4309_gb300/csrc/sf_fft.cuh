@@ -10,6 +10,11 @@
 //   K M' + n + j M (j < R) are replaced by  y_k = W_{M'}^{n k} sum_j x_j W_R^{j k}
 //   at positions K M' + n + k M.
 //
+// Power-of-two lengths use E = 16 (radix-16 stages, the last one taking the
+// remaining factor).  Lengths with a factor 3 (1536, 2304, 3072, 4608, 6144)
+// use E = 24 and an explicit radix sequence whose first radix (24) holds the
+// factor 3, so every later sub-length is a power of two.
+//
 // After the last stage position p holds frequency f(p), the mixed-radix digit
 // reversal of p.  The convolution never needs natural frequency order: the
 // kernel spectrum is produced by the same network (so it sits in the same
@@ -24,6 +29,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <utility>
 
 namespace sf {
 
@@ -164,44 +171,153 @@ __device__ __forceinline__ void dft16(float2* x) {
   }
 }
 
+// cos(2 pi e / 24), e = 0..23 (multiples of 15 degrees)
+constexpr float kCos24[24] = {1.f, 0.96592582628906829f, 0.86602540378443865f, 0.70710678118654752f,
+                              0.5f, 0.25881904510252076f, 0.f, -0.25881904510252076f,
+                              -0.5f, -0.70710678118654752f, -0.86602540378443865f, -0.96592582628906829f,
+                              -1.f, -0.96592582628906829f, -0.86602540378443865f, -0.70710678118654752f,
+                              -0.5f, -0.25881904510252076f, 0.f, 0.25881904510252076f,
+                              0.5f, 0.70710678118654752f, 0.86602540378443865f, 0.96592582628906829f};
+
+// a * W_24^E24 with W_24 = exp(-2 pi i / 24) (conjugated for the inverse);
+// multiples of 45 degrees go through mul_w16.
+template <bool INV, int E24>
+__device__ __forceinline__ float2 mul_w24(float2 a) {
+  constexpr int e = ((E24 % 24) + 24) % 24;
+  if constexpr (e % 3 == 0) {
+    return mul_w16<INV, 2 * e / 3>(a);
+  } else {
+    constexpr float wr = kCos24[e];
+    constexpr float wi0 = -kCos24[(e + 18) % 24];  // -sin(2 pi e / 24)
+    constexpr float wi = INV ? -wi0 : wi0;
+    return make_float2(fmaf(wr, a.x, -wi * a.y), fmaf(wr, a.y, wi * a.x));
+  }
+}
+
+// Radix 3: with s = x1 + x2, d = x1 - x2 and m = x0 - s / 2,
+// X0 = x0 + s, X1 = m -+ i (sqrt(3) / 2) d, X2 = m +- i (sqrt(3) / 2) d.
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2) {
+  constexpr float kS3 = 0.86602540378443865f;  // sin(pi / 3)
+  const float2 s = cadd(a1, a2), d = csub(a1, a2);
+  const float2 m = make_float2(fmaf(-0.5f, s.x, a0.x), fmaf(-0.5f, s.y, a0.y));
+  a0 = cadd(a0, s);
+  const float2 r = INV ? make_float2(-kS3 * d.y, kS3 * d.x) : make_float2(kS3 * d.y, -kS3 * d.x);
+  a1 = cadd(m, r);
+  a2 = csub(m, r);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* x);
+
+// Twiddles W_R^{j2 k1} of a Cooley-Tukey split, element I = R1 j2 + k1.
+template <bool INV, int R, int R1, int... I>
+__device__ __forceinline__ void ct_twiddle(float2* a, std::integer_sequence<int, I...>) {
+  static_assert(24 % R == 0, "constant twiddles are multiples of 15 degrees");
+  ((a[I] = mul_w24<INV, (24 / R) * ((I / R1) * (I % R1))>(a[I])), ...);
+}
+
+// Radix R = R1 R2 by one Cooley-Tukey split: j = R2 j1 + j2, k = k1 + R1 k2,
+// X[k] = sum_j2 W_R2^{j2 k2} [W_R^{j2 k1} sum_j1 x[j] W_R1^{j1 k1}].
+template <int R1, int R2, bool INV>
+__device__ __forceinline__ void dft_ct(float2* x) {
+  constexpr int R = R1 * R2;
+  float2 a[R];
+#pragma unroll
+  for (int j2 = 0; j2 < R2; ++j2) {
+    float2 c[R1];
+#pragma unroll
+    for (int j1 = 0; j1 < R1; ++j1) c[j1] = x[R2 * j1 + j2];
+    dft<R1, INV>(c);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[R1 * j2 + k1] = c[k1];
+  }
+  ct_twiddle<INV, R, R1>(a, std::make_integer_sequence<int, R>{});
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 c[R2];
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) c[j2] = a[R1 * j2 + k1];
+    dft<R2, INV>(c);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = c[k2];
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* x) {
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
     dft2<INV>(x[0], x[1]);
+  } else if constexpr (R == 3) {
+    dft3<INV>(x[0], x[1], x[2]);
   } else if constexpr (R == 4) {
     dft4<INV>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (R == 6) {
+    dft_ct<3, 2, INV>(x);
   } else if constexpr (R == 8) {
     dft8<INV>(x);
+  } else if constexpr (R == 12) {
+    dft_ct<3, 4, INV>(x);
   } else if constexpr (R == 16) {
     dft16<INV>(x);
+  } else if constexpr (R == 24) {
+    dft_ct<3, 8, INV>(x);
   } else {
     static_assert(R == 16, "unsupported radix");
   }
 }
 
 // ------------------------------------------------------------- stage layout
-constexpr int stage_count(int L, int E) {
-  int s = 0, M = L;
-  while (M > 1) { M /= (M > E ? E : M); ++s; }
-  return s;
+constexpr bool is_pow2(int L) { return L > 0 && (L & (L - 1)) == 0; }
+
+// Radix sequences of the lengths with a factor 3 (E = 24); 1 past the last stage.
+constexpr int mixed_radix(int L, int s) {
+  return L == 1536   ? (s == 0 ? 24 : s < 3 ? 8 : 1)
+         : L == 2304 ? (s == 0 ? 24 : s == 1 ? 12 : s == 2 ? 8 : 1)
+         : L == 3072 ? (s == 0 ? 24 : s < 3 ? 8 : s == 3 ? 2 : 1)
+         : L == 4608 ? (s < 2 ? 24 : s == 2 ? 8 : 1)
+         : L == 6144 ? (s == 0 ? 24 : s < 3 ? 8 : s == 3 ? 4 : 1)
+                     : 1;
+}
+
+// radix of stage s (1 past the last stage)
+constexpr int stage_radix(int L, int E, int s) {
+  if (!is_pow2(L)) return mixed_radix(L, s);
+  int M = L;
+  for (int i = 0; i < s; ++i) M /= (M > E ? E : M);
+  return M > E ? E : M;
 }
 // sub-length M' entering stage s
 constexpr int stage_mprev(int L, int E, int s) {
   int M = L;
-  for (int i = 0; i < s; ++i) M /= (M > E ? E : M);
+  for (int i = 0; i < s; ++i) M /= stage_radix(L, E, i);
   return M;
 }
-constexpr int stage_radix(int L, int E, int s) {
-  return stage_mprev(L, E, s) > E ? E : stage_mprev(L, E, s);
+constexpr int stage_count(int L, int E) {
+  int s = 0;
+  while (stage_mprev(L, E, s) > 1) ++s;
+  return s;
 }
 
 // Shared-memory address of a row position (8-byte elements): one pad slot
-// every 16 positions.  Stage positions are sums of disjoint power-of-two bit
-// fields, over which phys is additive, so every access is a per-thread base
-// plus a compile-time offset.
+// every 16 positions.  A stage position is base + k M; for the radix
+// sequences used here the two terms never carry across a multiple of 16, so
+// phys is additive over them (Stage checks this at compile time) and every
+// access is a per-thread base plus a compile-time offset.
 __host__ __device__ constexpr int phys(int p) { return p + (p >> 4); }
 __host__ __device__ constexpr int buf_elems(int L) { return phys(L - 1) + 1; }
+
+// phys(base + k M) == phys(base) + phys(k M) for every position of stage s
+constexpr bool stage_phys_additive(int L, int E, int s) {
+  const int T = L / E, MP = stage_mprev(L, E, s), R = stage_radix(L, E, s), M = MP / R;
+  for (int b = 0; b < T * (E / R); ++b) {
+    const int base = (b / M) * MP + b % M;
+    for (int k = 0; k < R; ++k)
+      if (phys(base + k * M) != phys(base) + phys(k * M)) return false;
+  }
+  return true;
+}
 
 // Position of element j of butterfly u (u < E / R) of thread t in stage s.
 template <int L, int E, int S>
@@ -212,6 +328,7 @@ struct Stage {
   static constexpr int M = MP / R;
   static constexpr int NB = E / R;
   static_assert(E % R == 0, "radix must divide the per-thread element count");
+  static_assert(stage_phys_additive(L, E, S), "padded addresses must split into base + offset");
   __device__ __forceinline__ static int base(int t, int u) {
     int b = t + T * u;
     return (b / M) * MP + (b % M);

@@ -19,6 +19,17 @@ constexpr int kTcE = 16;           // radix of the tensor-core network's stages
 
 enum PassKind : int { PASS_X_REAL = 0, PASS_X_CPLX = 1, PASS_Y = 2 };
 
+// Supported FFT lengths: powers of two (radix-16 network) and 3 x powers of
+// two / 9 x 256 (radix-24 first stage), ascending.
+constexpr int kNumFftLengths = 13;
+constexpr int kFftLengths[kNumFftLengths] = {64, 128, 256, 512, 1024, 1536, 2048, 2304, 3072, 4096, 4608, 6144, 8192};
+template <int L>
+constexpr int fft_length_slot_of() {
+  int i = 0;
+  while (i < kNumFftLengths && kFftLengths[i] != L) ++i;
+  return i;
+}
+
 // One separable half of one view (Section 2.2, steps 2-9 along one axis).
 // Row r is read from src[r * src_ld + p] (p < n0); output p of row r goes to
 // dst[p * dst_ld + r] (p < n1).
@@ -71,7 +82,7 @@ struct BatchArgs {
   int* done;                 // [n_holos][n_groups] completed items
   int* next;                 // item counter
   int* error;                // set to 1 when a bounded wait expires
-  const float4* tw[13];      // per-stage twiddle tables indexed by log2(L)
+  const float4* tw[kNumFftLengths];  // per-stage twiddle tables, indexed by fft_length_slot(L)
   int n_holos, n_groups, n_views, items_per_holo, total_items;
   int poison_group;          // -1; a group index makes its dependency unsatisfiable (tests)
   long long spin_limit;      // sleeps before a wait gives up
@@ -81,6 +92,25 @@ int batch_tile_rows(int L);
 int batch_item_tiles(int L);
 size_t batch_smem_bytes();
 const void* batch_kernel(PassKind kind_x);
+
+// Persistent row pass with TMA row prefetch (sf_persist.cu)
+struct PersistArgs {
+  int total_tiles;
+  int tile_off[kMaxPassBatch + 1];  // first tile of each descriptor
+  int off_cin, off_cout, off_h, off_rows, off_mbar;  // shared-memory byte offsets
+  int row_bytes;                    // stride of the staged rows
+  long long spin_limit;             // bounded mbarrier waits
+  int* err;                         // device error word
+};
+bool tma_length_supported(int L);
+size_t tma_layout(int L, PassKind kind, int n0max, int n1max, PersistArgs& pa);
+int tma_occupancy(int L, PassKind kind, size_t smem);
+cudaError_t launch_pass_tma(int L, PassKind kind, const PassBatch& b, const float4* tw, const PersistArgs& pa, int grid,
+                            size_t smem, cudaStream_t s);
+// Whole persistent launch of one pass batch: layout, occupancy-sized grid
+// (falls back to the grid kernel when the staged tile does not fit).
+cudaError_t launch_pass_persistent(int L, PassKind kind, const PassBatch& b, const float4* tw, int* err, int sms,
+                                   cudaStream_t s);
 
 // Mixed-precision row pass (sf_tc.cu)
 bool tc_length_supported(int L);
@@ -93,8 +123,17 @@ cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, i
 
 // host helpers shared by the entry points (defined in sf_api.cu)
 int validate_view(const sf_view& v);
-void axis_coefficients(const sf_view& v, int axis, AxisCoef& a);
-void adjoint_axis_coefficients(const sf_view& v, int axis, AxisCoef& a);
+// smallest supported FFT length >= need (powers of two only unless allow_mixed)
+int next_fft_length(int need, bool allow_mixed);
+// L = 0: the smallest supported length that holds the axis's linear convolution
+void axis_coefficients(const sf_view& v, int axis, AxisCoef& a, int L = 0);
+void adjoint_axis_coefficients(const sf_view& v, int axis, AxisCoef& a, int L = 0);
+
+// Autotuner (sf_tune.cu): SF_AUTOTUNE=1 selects measured choices; row_cost_ns
+// is the measured time per row (ns) of a pass of length L, kind and kernel
+// (0 one tile per CTA, 1 persistent), < 0 when not available.
+int autotune_mode();
+double row_cost_ns(int device, int L, PassKind kind, int impl, int sms, cudaStream_t s);
 
 // Inner products for d(loss)/dz of one view (see shifted_fresnel_adjoint).
 struct ZGradArgs {
@@ -126,5 +165,6 @@ int pass_rows_per_cta(int L);
 int pass_threads(int L);
 size_t pass_smem_bytes(int L);
 bool fft_length_supported(int L);
+int fft_length_slot(int L);  // index in kFftLengths, -1 if unsupported
 
 }  // namespace sf

@@ -14,8 +14,9 @@
 // The x pass reads hologram rows and writes the intermediate transposed,
 // [nx1][ny0]; the y pass then reads those rows (hologram columns) and writes
 // the view [ny1][nx1] transposed back.  Both passes load contiguous rows.
-// A CTA holds G = max(1, 256 / T) groups of T = L / 16 threads; group g
-// handles row blockIdx.x * G + g of pass blockIdx.y.
+// A CTA holds G = max(1, 256 / T) groups of T = L / E threads (E = 16 for
+// power-of-two lengths, 24 for the lengths with a factor 3); group g handles
+// row blockIdx.x * G + g of pass blockIdx.y.
 #pragma once
 
 #include <climits>
@@ -32,13 +33,21 @@
 
 namespace sf {
 
+// complex values per thread of the FFT network of length L
+constexpr int fft_e(int L) { return is_pow2(L) ? kE : 24; }
+
+// Powers of two: CTAs of up to 256 threads, registers for 16 warps per SM
+// (128 per thread).  Lengths with a factor 3 hold 24 values per thread: CTAs
+// of up to 192 threads, registers for 12 warps per SM (up to 168 per thread).
 template <int L>
 struct PassShape {
-  static constexpr int T = L / kE;
-  static constexpr int G = (SF_PASS_CTA_THREADS / T) > 0 ? (SF_PASS_CTA_THREADS / T) : 1;
+  static constexpr int T = L / fft_e(L);
+  static constexpr int CTA_TARGET = is_pow2(L) ? SF_PASS_CTA_THREADS : 192;
+  static constexpr int MIN_WARPS = is_pow2(L) ? SF_PASS_MIN_WARPS : 12;
+  static constexpr int G = (CTA_TARGET / T) > 0 ? (CTA_TARGET / T) : 1;
   static constexpr int THREADS = G * T;
-  // CTAs per SM the register budget is set for (2 x 256 threads: 128 registers)
-  static constexpr int MIN_BLOCKS = SF_PASS_MIN_WARPS / (THREADS / 32) > 0 ? SF_PASS_MIN_WARPS / (THREADS / 32) : 1;
+  // CTAs per SM the register budget is set for
+  static constexpr int MIN_BLOCKS = MIN_WARPS / (THREADS / 32) > 0 ? MIN_WARPS / (THREADS / 32) : 1;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)G * buf_elems(L);
   // group g synchronises on named barrier 1 + g when its T threads are whole
   // warps; hardware barrier ids are 0..15
@@ -58,54 +67,88 @@ __device__ __forceinline__ float phase_of(float2 u) {
   return p <= -3.14159265358979f ? 3.14159265358979f : p;  // (-pi, pi]
 }
 
-// One tile of a pass: group g of the CTA transforms source row r = row0 + g,
-// read contiguously (src[r * src_ld + p], p < n0), and the n1 outputs are
-// written transposed (dst[p * dst_ld + r]) through a shared-memory tile so
-// the G rows of the tile leave as G-element contiguous runs.  COHERENT reads
-// the source through L2 only, for data written earlier in the same launch.
-template <int L, int KIND, bool COHERENT>
-__device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw) {
-  using Sh = PassShape<L>;
-  constexpr int T = Sh::T, G = Sh::G, E = kE;
-  const int g = threadIdx.x / T, t = threadIdx.x % T;
-  const int row = row0 + g;
-  const bool valid = row < d.rows;
-  float2* buf = smem + g * buf_elems(L);
-
-  float2 v[E];
-#pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const int p = t + T * j;
-    v[j] = make_float2(0.f, 0.f);
-    if (valid && p < d.n0) {
-      const float2 c = __ldg(d.cin + p);
-      if constexpr (KIND == PASS_X_REAL) {
-        const float x = __ldg(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + p);
-        v[j] = cscale(c, x);
-      } else {
-        const float2* sp = static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + p;
-        const float2 x = COHERENT ? __ldcg(sp) : __ldg(sp);
-        v[j] = cmul(x, c);
-      }
+// Where a row tile reads its chirp-multiplied input, kernel spectrum and output
+// chirp from: global memory (rows through L1, or through L2 only when
+// COHERENT, for data written earlier in the same launch) ...
+template <int KIND, bool COHERENT>
+struct GlobalSrc {
+  const PassDesc& d;
+  __device__ __forceinline__ float2 in(int g, int row, int p) const {
+    const float2 c = __ldg(d.cin + p);
+    if constexpr (KIND == PASS_X_REAL) {
+      return cscale(c, __ldg(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + p));
+    } else {
+      const float2* sp = static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + p;
+      return cmul(COHERENT ? __ldcg(sp) : __ldg(sp), c);
     }
   }
+  __device__ __forceinline__ float2 h(int i) const { return __ldg(d.H + i); }
+  __device__ __forceinline__ float2 co(int p) const { return __ldg(d.cout + p); }
+};
 
-  fft_forward<L, E>(v, t, g, buf, tw);
-#pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(d.H + e * T + t));
-  fft_inverse<L, E>(v, t, g, buf, tw);
+// ... or shared memory: the view's vectors and the tile's rows staged there
+// (row g of the tile at rows + g * row_bytes).
+template <int KIND>
+struct StagedSrc {
+  const float2* cin;
+  const float2* H;
+  const float2* cout;
+  const unsigned char* rows;
+  int row_bytes;
+  __device__ __forceinline__ float2 in(int g, int, int p) const {
+    const float2 c = cin[p];
+    if constexpr (KIND == PASS_X_REAL) return cscale(c, reinterpret_cast<const float*>(rows + g * row_bytes)[p]);
+    else return cmul(reinterpret_cast<const float2*>(rows + g * row_bytes)[p], c);
+  }
+  __device__ __forceinline__ float2 h(int i) const { return H[i]; }
+  __device__ __forceinline__ float2 co(int p) const { return cout[p]; }
+};
 
-  // output chirp, then the transposed store through the tile [n1][G]
+// One tile of a pass: group g of the CTA transforms source row r = row0 + g
+// (input positions p < n0, zero-padded to L), and the n1 outputs are written
+// transposed (dst[p * dst_ld + r]) through a shared-memory tile so the G rows
+// of the tile leave as G-element contiguous runs.  With SPARE, the CTA may
+// have more threads than the tile's G T (a CTA sized for another length):
+// those only join the CTA barriers and the final store loop.
+template <int L, int KIND, typename Src, bool SPARE = false>
+__device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw,
+                                             const Src& src) {
+  using Sh = PassShape<L>;
+  constexpr int T = Sh::T, G = Sh::G, E = fft_e(L);
+  const int g = threadIdx.x / T, t = threadIdx.x % T;
+  const int row = row0 + g;
+  const bool active = !SPARE || threadIdx.x < Sh::THREADS;
+  const bool valid = row < d.rows;
+  float2* buf = smem + g * buf_elems(L);
   const int n1 = d.n1;
-  __syncthreads();
+
+  if (active) {
+    float2 v[E];
 #pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const int p = t + T * j;
-    if (p < n1) smem[p * G + g] = cmul(v[j], __ldg(d.cout + p));
+    for (int j = 0; j < E; ++j) {
+      const int p = t + T * j;
+      v[j] = (valid && p < d.n0) ? src.in(g, row, p) : make_float2(0.f, 0.f);
+    }
+
+    fft_forward<L, E>(v, t, g, buf, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], src.h(e * T + t));
+    fft_inverse<L, E>(v, t, g, buf, tw);
+
+    // output chirp, then the transposed store through the tile [n1][G]
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int p = t + T * j;
+      if (p < n1) smem[p * G + g] = cmul(v[j], src.co(p));
+    }
+  } else {
+    __syncthreads();
   }
   __syncthreads();
   const int rows_here = min(G, d.rows - row0);
-  for (int i = threadIdx.x; i < n1 * G; i += Sh::THREADS) {
+  const int stride = SPARE ? (int)blockDim.x : Sh::THREADS;
+  for (int i = threadIdx.x; i < n1 * G; i += stride) {
     const int p = i / G, gg = i - p * G;
     if (gg < rows_here) {
       const float2 u = smem[i];
@@ -119,6 +162,11 @@ __device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* sm
       }
     }
   }
+}
+
+template <int L, int KIND, bool COHERENT, bool SPARE = false>
+__device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw) {
+  row_tile_src<L, KIND, GlobalSrc<KIND, COHERENT>, SPARE>(d, row0, smem, tw, GlobalSrc<KIND, COHERENT>{d});
 }
 
 // Row pass: tile blockIdx.x of pass blockIdx.y.
@@ -137,8 +185,9 @@ k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
 // p > L - n0, 0 elsewhere; pushed through the same forward network so it
 // lands in register order.
 template <int L>
-__global__ void __launch_bounds__(L / kE) k_hspec(const AxisCoef* __restrict__ axes, const float4* __restrict__ tw) {
-  constexpr int T = L / kE, E = kE;
+__global__ void __launch_bounds__(L / fft_e(L)) k_hspec(const AxisCoef* __restrict__ axes,
+                                                        const float4* __restrict__ tw) {
+  constexpr int T = L / fft_e(L), E = fft_e(L);
   extern __shared__ float2 smem[];
   const AxisCoef a = axes[blockIdx.x];
   const int t = threadIdx.x;
@@ -183,7 +232,7 @@ cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float4* t
     cudaError_t e = cudaFuncSetAttribute(k_hspec<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_hspec<L><<<n_axes, L / kE, smem, s>>>(axes_dev, tw);
+  k_hspec<L><<<n_axes, L / fft_e(L), smem, s>>>(axes_dev, tw);
   return cudaGetLastError();
 }
 

@@ -14,13 +14,19 @@ SF_DECLARE_LENGTH(1024)
 SF_DECLARE_LENGTH(2048)
 SF_DECLARE_LENGTH(4096)
 SF_DECLARE_LENGTH(8192)
+SF_DECLARE_LENGTH(1536)
+SF_DECLARE_LENGTH(2304)
+SF_DECLARE_LENGTH(3072)
+SF_DECLARE_LENGTH(4608)
+SF_DECLARE_LENGTH(6144)
 
-bool fft_length_supported(int L) {
-  switch (L) {
-    case 64: case 128: case 256: case 512: case 1024: case 2048: case 4096: case 8192: return true;
-    default: return false;
-  }
+int fft_length_slot(int L) {
+  for (int i = 0; i < kNumFftLengths; ++i)
+    if (kFftLengths[i] == L) return i;
+  return -1;
 }
+
+bool fft_length_supported(int L) { return fft_length_slot(L) >= 0; }
 
 #define SF_LENGTH_SWITCH(L, CALL)                 \
   switch (L) {                                    \
@@ -32,6 +38,11 @@ bool fft_length_supported(int L) {
     case 2048: { constexpr int LL = 2048; CALL; } \
     case 4096: { constexpr int LL = 4096; CALL; } \
     case 8192: { constexpr int LL = 8192; CALL; } \
+    case 1536: { constexpr int LL = 1536; CALL; } \
+    case 2304: { constexpr int LL = 2304; CALL; } \
+    case 3072: { constexpr int LL = 3072; CALL; } \
+    case 4608: { constexpr int LL = 4608; CALL; } \
+    case 6144: { constexpr int LL = 6144; CALL; } \
     default: break;                               \
   }
 
@@ -81,7 +92,7 @@ cudaError_t launch_chirps(const AxisCoef* axes_dev, int n_axes, int max_n, cudaS
   return cudaGetLastError();
 }
 
-size_t twiddle_entries(int L) { return (size_t)tw_table_entries(L, kE); }
+size_t twiddle_entries(int L) { return (size_t)tw_table_entries(L, fft_e(L)); }
 
 // Per-stage twiddle tables (layout described at stage_tw_entries), built in
 // double precision on the host and rounded to float.
@@ -92,10 +103,11 @@ void build_twiddles(int L, float4* tab) {
     re = (float)std::cos(a);
     im = (float)-std::sin(a);
   };
-  for (int st = 0; st < stage_count(L, kE); ++st) {
-    const int MP = stage_mprev(L, kE, st), R = stage_radix(L, kE, st), M = MP / R;
+  const int E = fft_e(L);
+  for (int st = 0; st < stage_count(L, E); ++st) {
+    const int MP = stage_mprev(L, E, st), R = stage_radix(L, E, st), M = MP / R;
     if (M <= 1) continue;
-    float4* base = tab + stage_tw_offset(L, kE, st);
+    float4* base = tab + stage_tw_offset(L, E, st);
     for (int q = 0; q < R / 2; ++q)
       for (int n = 0; n < M; ++n) {
         float4 f;

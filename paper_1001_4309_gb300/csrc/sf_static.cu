@@ -42,7 +42,8 @@ constexpr size_t kOffTwX = 0, kOffTwY = kTwBytes, kOffVec = 2 * kTwBytes;
 constexpr size_t kOffWork = kOffVec + 6 * kVecBytes;
 static_assert(kOffWork + sizeof(float2) * (size_t)SF_STATIC_MAX_WORKSPACE_ELEMS <= SF_STATIC_SCRATCH_BYTES,
               "scratch layout exceeds the declared size");
-static_assert(sizeof(float4) * tw_table_entries(SF_STATIC_MAX_FFT_LENGTH, kE) <= kTwBytes,
+static_assert(sizeof(float4) * tw_table_entries(SF_STATIC_MAX_FFT_LENGTH, fft_e(SF_STATIC_MAX_FFT_LENGTH)) <= kTwBytes &&
+                  sizeof(float4) * tw_table_entries(1536, fft_e(1536)) <= kTwBytes,
               "twiddle table slot too small");
 static_assert(sizeof(float2) * SF_STATIC_MAX_FFT_LENGTH <= kVecBytes, "vector slot too small");
 
@@ -84,12 +85,13 @@ int check_device_pointer(const void* p, int dev) {
 // thread per float4 entry, from double-precision sincospi.
 __global__ void k_static_twiddles(float4* tab, int L) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ns = stage_count(L, kE);
-  if (i >= stage_tw_offset(L, kE, ns)) return;
+  const int E = fft_e(L);
+  const int ns = stage_count(L, E);
+  if (i >= stage_tw_offset(L, E, ns)) return;
   int st = 0;
-  while (st + 1 < ns && i >= stage_tw_offset(L, kE, st + 1)) ++st;
-  const int MP = stage_mprev(L, kE, st), R = stage_radix(L, kE, st), M = MP / R;
-  const int local = i - stage_tw_offset(L, kE, st), q = local / M, n = local - q * M;
+  while (st + 1 < ns && i >= stage_tw_offset(L, E, st + 1)) ++st;
+  const int MP = stage_mprev(L, E, st), R = stage_radix(L, E, st), M = MP / R;
+  const int local = i - stage_tw_offset(L, E, st), q = local / M, n = local - q * M;
   double s0, c0, s1, c1;
   sincospi(-2.0 * (double)(((long long)n * (2 * q) * (L / MP)) % L) / (double)L, &s0, &c0);
   sincospi(-2.0 * (double)(((long long)n * (2 * q + 1) * (L / MP)) % L) / (double)L, &s1, &c1);
@@ -114,8 +116,8 @@ __global__ void k_static_chirps(AxisCoef ax, AxisCoef ay) {
 
 // Kernel spectrum of one axis (coefficients by value), register order.
 template <int L>
-__global__ void __launch_bounds__(L / kE) k_static_hspec(AxisCoef a, const float4* __restrict__ tw) {
-  constexpr int T = L / kE, E = kE;
+__global__ void __launch_bounds__(L / fft_e(L)) k_static_hspec(AxisCoef a, const float4* __restrict__ tw) {
+  constexpr int T = L / fft_e(L), E = fft_e(L);
   extern __shared__ float2 smem[];
   const int t = threadIdx.x;
   float2 v[E];
@@ -135,12 +137,13 @@ __global__ void __launch_bounds__(L / kE) k_static_hspec(AxisCoef a, const float
 cudaError_t launch_static_hspec(const AxisCoef& a, const float4* tw, cudaStream_t s) {
   switch (a.L) {
 #define SF_STATIC_HSPEC_CASE(LL) \
-  case LL: k_static_hspec<LL><<<1, LL / kE, sizeof(float2) * buf_elems(LL), s>>>(a, tw); return cudaGetLastError();
+  case LL: k_static_hspec<LL><<<1, LL / fft_e(LL), sizeof(float2) * buf_elems(LL), s>>>(a, tw); return cudaGetLastError();
     SF_STATIC_HSPEC_CASE(64)
     SF_STATIC_HSPEC_CASE(128)
     SF_STATIC_HSPEC_CASE(256)
     SF_STATIC_HSPEC_CASE(512)
     SF_STATIC_HSPEC_CASE(1024)
+    SF_STATIC_HSPEC_CASE(1536)
     SF_STATIC_HSPEC_CASE(2048)
 #undef SF_STATIC_HSPEC_CASE
     default: return cudaErrorInvalidValue;

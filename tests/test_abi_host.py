@@ -102,3 +102,19 @@ def test_valid_plan_without_gpu_reports_cuda_error(lib):
     rc, h = lib.shifted_fresnel_plan([base_view()], check=False)
     assert rc == lib.SF_ERR_CUDA
     assert not h.value
+
+
+def test_fft_length_choice_without_gpu():
+    """Smallest supported length >= n0 + n1 - 1 (Section 2.2, step 2's zero padding), host only."""
+    from paper_1001_4309_gb300 import shifted_fresnel_fft_length as fl, SF_ERR_INVALID_ARG, SF_ERR_UNSUPPORTED_SIZE
+    # the paper's 1024 -> 1024 views pad to 2N = 2048
+    assert fl(1024 + 1024 - 1) == 2048
+    cases = {1: 64, 64: 64, 65: 128, 1025: 1536, 1535: 1536, 1536: 1536, 1537: 2048, 2048: 2048,
+             2049: 2304, 2303: 2304, 2305: 3072, 3071: 3072, 3073: 4096, 4095: 4096, 4097: 4608,
+             4608: 4608, 4609: 6144, 6143: 6144, 6145: 8192, 8192: 8192}
+    for need, L in cases.items():
+        assert fl(need) == L, need
+        p2 = fl(need, allow_mixed=False)
+        assert p2 >= need and p2 & (p2 - 1) == 0 and p2 // 2 < max(need, 64)
+    assert fl(0) == SF_ERR_INVALID_ARG
+    assert fl(8193) == SF_ERR_UNSUPPORTED_SIZE
