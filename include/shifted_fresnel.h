@@ -121,6 +121,12 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
  * overlapping the rest of the computation; the caller's stream waits for the
  * last copy, so the caller synchronises its stream before reading host
  * outputs.  Every view needs at least one non-NULL output.
+ * With device outputs and two or more views, the views are split into two
+ * halves of about equal work run on `stream` and on a plan-owned second
+ * stream (x pass then y pass each), so one half's y pass overlaps the other's
+ * x pass; `stream` waits for both before the call's work is complete.
+ * SF_EXECUTE_SINGLE_STREAM=1, or profiling events set with
+ * shifted_fresnel_set_profile_events, keeps everything on `stream`.
  * Implementation: each pass runs a one-tile-per-CTA kernel, or, where the
  * plan chose it (SF_PASS_IMPL=tma or the autotuner, see
  * shifted_fresnel_fft_length) and the rows' address, stride and length are
@@ -135,33 +141,48 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
 /*
  * shifted_fresnel_execute_batch -- reconstruct every view of the plan for
  * each of n_holos holograms (the paper's per-frame loop of Section 2.2,
- * steps 1-11, over a stream of frames) in ONE persistent kernel launch,
- * issued as a CUDA graph (descriptor upload, counter reset, kernel).
+ * steps 1-11, over a stream of frames) with one of two implementations:
+ *
+ *   persistent  ONE persistent kernel launch for the whole batch, issued as
+ *               a CUDA graph (descriptor upload, counter reset, kernel).
+ *               CTAs take (hologram, pass, view, row tile) items in order
+ *               from a counter; a y-pass item waits for the x-pass tiles of
+ *               its hologram and view, an x-pass item for hologram h waits
+ *               for the y pass of hologram h - 2 (two intermediate slots per
+ *               view).  The waits are bounded; if one expires the launch
+ *               ends early and shifted_fresnel_batch_status reports
+ *               SF_ERR_TIMEOUT.  FFT lengths up to 6144.
+ *   streams     execute's per-length row-pass kernels, even holograms on one
+ *               plan-owned stream and odd ones on another (one intermediate
+ *               slot each), joined back into `stream`; consecutive holograms
+ *               overlap.  Any FFT length.
+ *
+ * Choice: SF_BATCH_IMPL=persistent|streams forces one; with SF_AUTOTUNE=1 the
+ * first call for each n_holos times both on its own buffers (blocking) and
+ * later calls use the faster; otherwise the streams (faster on every
+ * workload measured, launch-bound 256^2 views included).  Both compute with
+ * the same row-tile code as execute, so outputs equal execute's bit for bit.
  *
  *   holos      n_holos device pointers, each a hologram as for execute.
  *   view_out   n_holos * n_views device pointers (index h * n_views + v) to
  *              complex64 [ny1][nx1] views, or NULL; entries may be NULL.
  *   intensity  same layout, float32 |u1|^2 images, or NULL.
  *   phase      same layout, float32 phase images, or NULL.
- *   stream     stream to launch the graph on.
+ *   stream     stream the batch is ordered on.
  * Every (hologram, view) needs at least one non-NULL output.  All buffers
  * must be device memory of the plan's device (SF_ERR_INVALID_ARG otherwise).
- * Views may have different sizes (ragged); every FFT length must be at most
- * 4096 (SF_ERR_UNSUPPORTED_SIZE otherwise).
+ * Views may have different sizes (ragged).  The persistent kernel forced on
+ * a plan with an FFT length above 6144 returns SF_ERR_UNSUPPORTED_SIZE.
  *
- * Inside the launch, CTAs take (hologram, pass, view, row tile) items in
- * order from a counter; a y-pass item waits for the x-pass tiles of its
- * hologram and view, an x-pass item for hologram h waits for the y pass of
- * hologram h - 2 (two intermediate slots per view).  The waits are bounded;
- * if one expires the launch ends early and shifted_fresnel_batch_status
- * reports SF_ERR_TIMEOUT.  The first call (and a call with a new n_holos)
- * allocates per-view second intermediate slots, descriptor tables (pinned
- * and device) and builds the graph; calls return after launching and may
- * block the host only until the call two back has finished.  Calls on one
- * plan must not overlap with other calls on another stream.
- * Testing aids read when the graph is built: SF_BATCH_SPIN_LIMIT (sleeps
- * before a wait gives up, default 4194304) and SF_BATCH_POISON_GROUP (an
- * item group whose dependency is made unsatisfiable).
+ * The first call allocates per-view second intermediate slots and two
+ * streams; the persistent kernel also allocates, per n_holos, descriptor
+ * tables (pinned and device) and its graph.  Calls return after launching
+ * and may block the host only until the persistent call two back has
+ * finished.  Calls on one plan must not overlap with other calls on another
+ * stream.  Testing aids read when the persistent graph is built:
+ * SF_BATCH_SPIN_LIMIT (sleeps before a wait gives up, default 4194304) and
+ * SF_BATCH_POISON_GROUP (an item group whose dependency is made
+ * unsatisfiable).
  * Errors: SF_ERR_INVALID_ARG, SF_ERR_UNSUPPORTED_SIZE, SF_ERR_OOM, SF_ERR_CUDA.
  */
 int shifted_fresnel_execute_batch(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,

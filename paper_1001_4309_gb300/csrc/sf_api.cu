@@ -59,7 +59,12 @@ struct BatchState {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int flip = 0;
+  // the per-length kernels on two streams (even / odd holograms, one slot each)
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+  std::map<int, int> choice;             // hologram count -> BATCH_PERSISTENT / BATCH_STREAMS (autotuned)
 };
+enum { BATCH_PERSISTENT = 0, BATCH_STREAMS = 1 };
 
 }  // namespace
 
@@ -92,6 +97,9 @@ struct sf_plan_s {
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> view_done;
   cudaEvent_t copies_done = nullptr;
+  // execute's second compute stream (half of the views), created on first use
+  cudaStream_t split_stream = nullptr;
+  cudaEvent_t split_fork = nullptr, split_join = nullptr;
 };
 
 namespace sf {
@@ -239,13 +247,40 @@ void free_plan(sf_plan p) {
   for (cudaEvent_t e : p->view_done) cudaEventDestroy(e);
   if (p->copies_done) cudaEventDestroy(p->copies_done);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->split_fork) cudaEventDestroy(p->split_fork);
+  if (p->split_join) cudaEventDestroy(p->split_join);
+  if (p->split_stream) cudaStreamDestroy(p->split_stream);
   free_batch_sized(p->batch);
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 2; ++k) {
     if (p->batch.ev[k]) cudaEventDestroy(p->batch.ev[k]);
+    if (p->batch.join[k]) cudaEventDestroy(p->batch.join[k]);
+    if (p->batch.st[k]) cudaStreamDestroy(p->batch.st[k]);
+  }
+  if (p->batch.fork) cudaEventDestroy(p->batch.fork);
   if (p->batch.d_fixed) cudaFree(p->batch.d_fixed);
   for (void* s : p->staging) cudaFree(s);
   if (p->arena) cudaFree(p->arena);
   delete p;
+}
+
+// Second compute stream and its fork / join events.
+int ensure_split_resources(sf_plan p) {
+  if (p->split_stream) return SF_OK;
+  cudaStream_t st = nullptr;
+  cudaEvent_t f = nullptr, j = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (f) cudaEventDestroy(f);
+    if (j) cudaEventDestroy(j);
+    if (st) cudaStreamDestroy(st);
+    return SF_ERR_CUDA;
+  }
+  p->split_stream = st;
+  p->split_fork = f;
+  p->split_join = j;
+  return SF_OK;
 }
 
 // Copy stream and events for overlapping device-to-host copies with compute.
@@ -333,6 +368,11 @@ cudaError_t run_pass(sf_plan p, int L, PassKind kind, const PassDesc* descs, int
   return launch_pass(L, kind, b, (max_rows + G - 1) / G, p->tw[L], s);
 }
 
+bool env_is(const char* name, const char* value) {
+  const char* v = std::getenv(name);
+  return v && std::strcmp(v, value) == 0;
+}
+
 long long env_ll(const char* name, long long dflt) {
   const char* v = std::getenv(name);
   return v && *v ? std::atoll(v) : dflt;
@@ -340,9 +380,18 @@ long long env_ll(const char* name, long long dflt) {
 
 // Build (or rebuild for a new hologram count) the batch graph:
 // memcpy(descriptors <- pinned table), memset(counters), persistent kernel.
-int batch_prepare(sf_plan p, int n_holos) {
+// Every FFT length of the plan fits the persistent batch kernel.
+bool batch_persistent_supported(sf_plan p) {
+  for (const ViewState& vs : p->views)
+    for (int ph = 0; ph < 2; ++ph)
+      if (!batch_length_supported(vs.ax[ph].L)) return false;
+  return true;
+}
+
+int batch_prepare(sf_plan p, int n_holos, bool persistent) {
   BatchState& b = p->batch;
   const int nv = (int)p->views.size();
+  if (persistent && !batch_persistent_supported(p)) return SF_ERR_UNSUPPORTED_SIZE;
   if (!b.init) {
     b.groups.clear();
     int first = 0;
@@ -350,8 +399,8 @@ int batch_prepare(sf_plan p, int n_holos) {
       for (int v = 0; v < nv; ++v) {
         const ViewState& vs = p->views[v];
         const int L = vs.ax[ph].L;
-        if (!batch_length_supported(L)) return SF_ERR_UNSUPPORTED_SIZE;
-        const int rows = ph == 0 ? vs.v.ny0 : vs.v.nx1, G = batch_tile_rows(L), chunk = batch_item_tiles(L);
+        const int G = std::max(1, batch_tile_rows(L)), chunk = std::max(1, batch_item_tiles(L));
+        const int rows = ph == 0 ? vs.v.ny0 : vs.v.nx1;
         const int tiles = (rows + G - 1) / G, items = (tiles + chunk - 1) / chunk;
         b.groups.push_back({first, items, tiles, chunk, L, ph});
         first += items;
@@ -383,10 +432,14 @@ int batch_prepare(sf_plan p, int n_holos) {
       return SF_ERR_CUDA;
     b.grid = sms * per_sm;
     for (int k = 0; k < 2; ++k)
-      if (cudaEventCreateWithFlags(&b.ev[k], cudaEventDisableTiming) != cudaSuccess) return SF_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&b.ev[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b.join[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&b.st[k], cudaStreamNonBlocking) != cudaSuccess)
+        return SF_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return SF_ERR_CUDA;
     b.init = true;
   }
-  if (b.n_holos == n_holos) return SF_OK;
+  if (!persistent || b.n_holos == n_holos) return SF_OK;
   free_batch_sized(b);
   const int ng = (int)b.groups.size();
   const size_t n_desc = (size_t)n_holos * ng, n_cnt = n_desc + 1;
@@ -471,6 +524,75 @@ bool persistent_eligible(sf_plan p, int L, PassKind kind, const PassBatch& b) {
   return true;
 }
 
+// Every view's pass along one axis (0: x, 1: y), launched in groups of views
+// with equal FFT length (at most max_per_launch views per launch).  Pass
+// sources: x reads `src` (the hologram) into work[v]; y reads work[v] into the
+// view outputs dout/dint/dph[v].  after(views, n) runs after each launch.
+template <typename After>
+cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* work, float2* const* dout,
+                        float* const* dint, float* const* dph, int max_per_launch, cudaStream_t s, After&& after,
+                        const std::vector<int>* subset = nullptr) {
+  std::vector<int> order;
+  if (subset) {
+    order = *subset;
+  } else {
+    for (int i = 0; i < (int)plan->views.size(); ++i) order.push_back(i);
+  }
+  const int nv = (int)order.size();
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return plan->views[a].ax[axis].L < plan->views[b].ax[axis].L; });
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < nv && e == cudaSuccess;) {
+    const int L = plan->views[order[i]].ax[axis].L;
+    PassBatch b;
+    std::memset(&b, 0, sizeof(b));
+    int max_rows = 0;
+    int batch_view[kMaxPassBatch];
+    while (i < nv && b.count < std::min(max_per_launch, kMaxPassBatch) && plan->views[order[i]].ax[axis].L == L) {
+      const int vi = order[i++];
+      batch_view[b.count] = vi;
+      ViewState& vs = plan->views[vi];
+      const AxisCoef& c = vs.ax[axis];
+      PassDesc& d = b.d[b.count++];
+      d.cin = c.cin;
+      d.cout = c.cout;
+      d.H = c.H;
+      d.n0 = c.n0;
+      d.n1 = c.n1;
+      if (axis == 0) {
+        d.src = src;
+        d.dst = work[vi];
+        d.rows = vs.v.ny0;
+        d.src_ld = vs.v.nx0;
+        d.dst_ld = vs.v.ny0;
+      } else {
+        d.src = work[vi];
+        d.dst = dout[vi];
+        d.inten = dint[vi];
+        d.phase = dph[vi];
+        d.rows = vs.v.nx1;
+        d.src_ld = vs.v.ny0;
+        d.dst_ld = vs.v.nx1;
+      }
+      max_rows = std::max(max_rows, d.rows);
+    }
+    const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
+    if (plan->tc_frags && tc_length_supported(L)) {
+      for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[batch_view[k]].hpos[axis];
+      const int G = tc_rows_per_cta();
+      e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tw[L], plan->tc_frags, s);
+    } else if (persistent_eligible(plan, L, kind, b)) {
+      e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);
+    } else {
+      const int G = pass_rows_per_cta(L);
+      e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
+    }
+    ++g_launches;
+    if (e == cudaSuccess) e = after(batch_view, b.count);
+  }
+  return e;
+}
+
 // FFT length per (view, axis) and row-pass kernel per (length, kind).
 //   default: the smallest supported length (SF_FFT_LENGTHS=pow2 keeps powers
 //            of two only); the one-tile-per-CTA kernel (SF_PASS_IMPL=tma
@@ -531,6 +653,110 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
       if (used) best(L, (PassKind)k, &c.impl[slot][k]);
     }
   return c;
+}
+
+// The persistent kernel: one graph launch for the whole batch.
+int run_batch_persistent(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
+                         float* const* intensity, float* const* phase, cudaStream_t s) {
+  const int nv = (int)plan->views.size();
+  int rc = batch_prepare(plan, n_holos, true);
+  if (rc) return rc;
+  BatchState& b = plan->batch;
+  const int k = b.flip;
+  if (cudaEventSynchronize(b.ev[k]) != cudaSuccess) {  // the call two back has finished reading this table
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  const int ng = (int)b.groups.size();
+  for (int h = 0; h < n_holos; ++h)
+    for (int g = 0; g < ng; ++g) {
+      const int v = g % nv, ph = g / nv;
+      ViewState& vs = plan->views[v];
+      float2* slot = (h & 1) ? b.slot1[v] : vs.work;
+      const AxisCoef& c = vs.ax[ph];
+      PassDesc& d = b.h_descs[k][(size_t)h * ng + g];
+      std::memset(&d, 0, sizeof(d));
+      d.cin = c.cin; d.cout = c.cout; d.H = c.H; d.n0 = c.n0; d.n1 = c.n1;
+      if (ph == 0) {
+        d.src = holos[h]; d.dst = slot; d.rows = vs.v.ny0; d.src_ld = vs.v.nx0; d.dst_ld = vs.v.ny0;
+      } else {
+        const size_t i = (size_t)h * nv + v;
+        d.src = slot;
+        d.dst = view_out ? static_cast<float2*>(view_out[i]) : nullptr;
+        d.inten = intensity ? intensity[i] : nullptr;
+        d.phase = phase ? phase[i] : nullptr;
+        d.rows = vs.v.nx1; d.src_ld = vs.v.ny0; d.dst_ld = vs.v.nx1;
+      }
+    }
+  cudaError_t e = cudaGraphLaunch(b.exec[k], s);
+  if (e == cudaSuccess) e = cudaEventRecord(b.ev[k], s);
+  ++g_launches;
+  b.flip ^= 1;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+
+// The per-length row-pass kernels, holograms alternating between two streams
+// (and two intermediate slots), so one hologram's passes overlap the next's.
+int run_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
+                      float* const* intensity, float* const* phase, cudaStream_t s) {
+  int rc = batch_prepare(plan, n_holos, false);
+  if (rc) return rc;
+  BatchState& b = plan->batch;
+  const int nv = (int)plan->views.size();
+  cudaError_t e = cudaEventRecord(b.fork, s);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b.st[k], b.fork, 0);
+  std::vector<float2*> work(nv), dout(nv);
+  std::vector<float*> dint(nv), dph(nv);
+  auto none = [](const int*, int) { return cudaSuccess; };
+  for (int h = 0; h < n_holos && e == cudaSuccess; ++h) {
+    for (int v = 0; v < nv; ++v) {
+      const size_t i = (size_t)h * nv + v;
+      work[v] = (h & 1) ? b.slot1[v] : plan->views[v].work;
+      dout[v] = view_out ? static_cast<float2*>(view_out[i]) : nullptr;
+      dint[v] = intensity ? intensity[i] : nullptr;
+      dph[v] = phase ? phase[i] : nullptr;
+    }
+    for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis)
+      e = launch_axis(plan, axis, holos[h], work.data(), dout.data(), dint.data(), dph.data(), kMaxPassBatch,
+                      b.st[h & 1], none);
+  }
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b.join[k], b.st[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.join[k], 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+int run_batch(sf_plan plan, int impl, const void* const* holos, int n_holos, void* const* view_out,
+              float* const* intensity, float* const* phase, cudaStream_t s) {
+  return impl == BATCH_PERSISTENT ? run_batch_persistent(plan, holos, n_holos, view_out, intensity, phase, s)
+                                  : run_batch_streams(plan, holos, n_holos, view_out, intensity, phase, s);
+}
+
+// Batch implementation for this plan and hologram count; -1: measure (autotuner).
+//   SF_BATCH_IMPL=persistent|streams forces one; SF_AUTOTUNE=1 measures both
+//   once per hologram count; otherwise the per-length kernels on two streams,
+//   which measured faster than the persistent kernel on every workload tried
+//   (paper-scale views, ragged 2048^2 views, 256^2 single views).
+int batch_choice(sf_plan p, int n_holos) {
+  const char* env = std::getenv("SF_BATCH_IMPL");
+  if (env && std::string(env) == "persistent") return BATCH_PERSISTENT;
+  if (env && std::string(env) == "streams") return BATCH_STREAMS;
+  if (!batch_persistent_supported(p)) return BATCH_STREAMS;
+  if (autotune_mode() == 1) {
+    auto it = p->batch.choice.find(n_holos);
+    return it == p->batch.choice.end() ? -1 : it->second;
+  }
+  return BATCH_STREAMS;
 }
 
 }  // namespace
@@ -767,73 +993,68 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   // y passes run one view per launch and each view's copies start on the copy
   // stream as soon as its pass is done, overlapping the remaining compute.
   const bool overlap = !d2h.empty();
+  std::vector<float2*> work(nv);
+  for (int i = 0; i < nv; ++i) work[i] = plan->views[i].work;
   if (overlap) {
     int rc = ensure_copy_resources(plan);
     if (rc) return rc;
   }
+  // Device outputs, no profiling events, two or more views: the views are
+  // split into two halves of about equal work, each run (x pass, then y pass)
+  // on its own stream, so one half's y pass overlaps the other's x pass.
+  if (!overlap && !plan->prof[0] && nv >= 2 && !env_is("SF_EXECUTE_SINGLE_STREAM", "1")) {
+    int rc = ensure_split_resources(plan);
+    if (rc) return rc;
+    std::vector<int> order(nv), half[2];
+    double load[2] = {0, 0};
+    for (int i = 0; i < nv; ++i) order[i] = i;
+    auto cost = [&](int v) {
+      const ViewState& vs = plan->views[v];
+      return (double)vs.v.ny0 * vs.ax[0].L + (double)vs.v.nx1 * vs.ax[1].L;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    for (int v : order) {
+      const int k = load[1] < load[0] ? 1 : 0;
+      half[k].push_back(v);
+      load[k] += cost(v);
+    }
+    for (int k = 0; k < 2; ++k) std::sort(half[k].begin(), half[k].end());
+    auto none = [](const int*, int) { return cudaSuccess; };
+    e = cudaEventRecord(plan->split_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->split_stream, plan->split_fork, 0);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      cudaStream_t cs = k == 0 ? s : plan->split_stream;
+      for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis)
+        e = launch_axis(plan, axis, src, work.data(), dout.data(), dint.data(), dph.data(), kMaxPassBatch, cs, none,
+                        &half[k]);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(plan->split_join, plan->split_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->split_join, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return SF_ERR_CUDA;
+    }
+    return SF_OK;
+  }
+
   if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);
   for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
     if (axis == 1 && plan->prof[1]) e = cudaEventRecord(plan->prof[1], s);
-    std::vector<int> order(nv);
-    for (int i = 0; i < nv; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return plan->views[a].ax[axis].L < plan->views[b].ax[axis].L; });
-    for (int i = 0; i < nv && e == cudaSuccess;) {
-      const int L = plan->views[order[i]].ax[axis].L;
-      PassBatch b;
-      std::memset(&b, 0, sizeof(b));
-      int max_rows = 0;
-      int batch_view[kMaxPassBatch];
-      const int max_count = (overlap && axis == 1) ? 1 : kMaxPassBatch;
-      while (i < nv && b.count < max_count && plan->views[order[i]].ax[axis].L == L) {
-        const int vi = order[i++];
-        batch_view[b.count] = vi;
-        ViewState& vs = plan->views[vi];
-        const AxisCoef& c = vs.ax[axis];
-        PassDesc& d = b.d[b.count++];
-        d.cin = c.cin;
-        d.cout = c.cout;
-        d.H = c.H;
-        d.n0 = c.n0;
-        d.n1 = c.n1;
-        if (axis == 0) {
-          d.src = src;
-          d.dst = vs.work;
-          d.rows = vs.v.ny0;
-          d.src_ld = vs.v.nx0;
-          d.dst_ld = vs.v.ny0;
-        } else {
-          d.src = vs.work;
-          d.dst = dout[vi];
-          d.inten = dint[vi];
-          d.phase = dph[vi];
-          d.rows = vs.v.nx1;
-          d.src_ld = vs.v.ny0;
-          d.dst_ld = vs.v.nx1;
-        }
-        max_rows = std::max(max_rows, d.rows);
-      }
-      const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
-      if (plan->tc_frags && tc_length_supported(L)) {
-        for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[batch_view[k]].hpos[axis];
-        const int G = tc_rows_per_cta();
-        e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tw[L], plan->tc_frags, s);
-      } else if (persistent_eligible(plan, L, kind, b)) {
-        e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);
-      } else {
-        const int G = pass_rows_per_cta(L);
-        e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
-      }
-      ++g_launches;
-      if (overlap && axis == 1 && e == cudaSuccess) {
-        const int vi = batch_view[0];
-        e = cudaEventRecord(plan->view_done[vi], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->copy_stream, plan->view_done[vi], 0);
-        for (const Copy& c : d2h)
-          if (e == cudaSuccess && c.view == vi)
-            e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
-      }
-    }
+    auto after = [&](const int* views, int n) -> cudaError_t {
+      cudaError_t r = cudaSuccess;
+      if (!(overlap && axis == 1)) return r;
+      const int vi = views[0];
+      r = cudaEventRecord(plan->view_done[vi], s);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, plan->view_done[vi], 0);
+      for (const Copy& c : d2h)
+        if (r == cudaSuccess && c.view == vi)
+          r = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
+      (void)n;
+      return r;
+    };
+    if (e == cudaSuccess)
+      e = launch_axis(plan, axis, src, work.data(), dout.data(), dint.data(), dph.data(),
+                      (overlap && axis == 1) ? 1 : kMaxPassBatch, s, after);
   }
   if (e == cudaSuccess && plan->prof[2]) e = cudaEventRecord(plan->prof[2], s);
   if (overlap && e == cudaSuccess) {
@@ -1012,45 +1233,34 @@ int shifted_fresnel_execute_batch(sf_plan plan, const void* const* holos, int n_
         if (q && classify(q, plan->device) != PTR_DEVICE) return SF_ERR_INVALID_ARG;
     }
   }
-  int rc = batch_prepare(plan, n_holos);
-  if (rc) return rc;
-  BatchState& b = plan->batch;
-  const int k = b.flip;
-  if (cudaEventSynchronize(b.ev[k]) != cudaSuccess) {  // the call two back has finished reading this table
-    cudaGetLastError();
-    return SF_ERR_CUDA;
-  }
-  const int ng = (int)b.groups.size();
-  for (int h = 0; h < n_holos; ++h)
-    for (int g = 0; g < ng; ++g) {
-      const int v = g % nv, ph = g / nv;
-      ViewState& vs = plan->views[v];
-      float2* slot = (h & 1) ? b.slot1[v] : vs.work;
-      const AxisCoef& c = vs.ax[ph];
-      PassDesc& d = b.h_descs[k][(size_t)h * ng + g];
-      std::memset(&d, 0, sizeof(d));
-      d.cin = c.cin; d.cout = c.cout; d.H = c.H; d.n0 = c.n0; d.n1 = c.n1;
-      if (ph == 0) {
-        d.src = holos[h]; d.dst = slot; d.rows = vs.v.ny0; d.src_ld = vs.v.nx0; d.dst_ld = vs.v.ny0;
-      } else {
-        const size_t i = (size_t)h * nv + v;
-        d.src = slot;
-        d.dst = view_out ? static_cast<float2*>(view_out[i]) : nullptr;
-        d.inten = intensity ? intensity[i] : nullptr;
-        d.phase = phase ? phase[i] : nullptr;
-        d.rows = vs.v.nx1; d.src_ld = vs.v.ny0; d.dst_ld = vs.v.nx1;
+  cudaStream_t s = (cudaStream_t)stream;
+  int impl = batch_choice(plan, n_holos);
+  if (impl < 0) {  // autotune: time both implementations on this call's buffers, keep the faster
+    float ms[2] = {-1.f, -1.f};
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t t0 = nullptr, t1 = nullptr;
+      int rc = SF_OK;
+      if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) rc = SF_ERR_CUDA;
+      for (int rep = 0; rep < 2 && rc == SF_OK; ++rep) {  // the first run warms up (graph build, caches)
+        if (cudaEventRecord(t0, s) != cudaSuccess) rc = SF_ERR_CUDA;
+        if (rc == SF_OK) rc = run_batch(plan, k, holos, n_holos, view_out, intensity, phase, s);
+        if (rc == SF_OK && (cudaEventRecord(t1, s) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
+          rc = SF_ERR_CUDA;
+      }
+      if (rc == SF_OK) cudaEventElapsedTime(&ms[k], t0, t1);
+      if (t0) cudaEventDestroy(t0);
+      if (t1) cudaEventDestroy(t1);
+      if (rc != SF_OK && rc != SF_ERR_UNSUPPORTED_SIZE) {
+        cudaGetLastError();
+        return rc;
       }
     }
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaGraphLaunch(b.exec[k], s);
-  if (e == cudaSuccess) e = cudaEventRecord(b.ev[k], s);
-  ++g_launches;
-  b.flip ^= 1;
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return SF_ERR_CUDA;
+    impl = (ms[BATCH_PERSISTENT] > 0 && (ms[BATCH_STREAMS] < 0 || ms[BATCH_PERSISTENT] < ms[BATCH_STREAMS]))
+               ? BATCH_PERSISTENT : BATCH_STREAMS;
+    plan->batch.choice[n_holos] = impl;
+    return SF_OK;  // the outputs were written by the timed runs
   }
-  return SF_OK;
+  return run_batch(plan, impl, holos, n_holos, view_out, intensity, phase, s);
 }
 
 int shifted_fresnel_batch_status(sf_plan plan, void* stream) {

@@ -146,19 +146,26 @@ __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2
     __syncthreads();
   }
   __syncthreads();
+  // descriptor fields in registers: a descriptor in global memory (batch
+  // kernel) would otherwise be re-read after every store
   const int rows_here = min(G, d.rows - row0);
   const int stride = SPARE ? (int)blockDim.x : Sh::THREADS;
+  float2* const dst = d.dst;
+  float* const inten = d.inten;
+  float* const phase = d.phase;
+  const size_t dst_ld = (size_t)d.dst_ld;
+  const bool acc = d.accumulate != 0;
   for (int i = threadIdx.x; i < n1 * G; i += stride) {
     const int p = i / G, gg = i - p * G;
     if (gg < rows_here) {
       const float2 u = smem[i];
-      const size_t o = (size_t)p * d.dst_ld + row0 + gg;
+      const size_t o = (size_t)p * dst_ld + row0 + gg;
       if constexpr (KIND != PASS_Y) {
-        d.dst[o] = u;
+        dst[o] = u;
       } else {
-        if (d.dst) d.dst[o] = d.accumulate ? cadd(d.dst[o], u) : u;
-        if (d.inten) d.inten[o] = fmaf(u.x, u.x, u.y * u.y);
-        if (d.phase) d.phase[o] = phase_of(u);
+        if (dst) dst[o] = acc ? cadd(dst[o], u) : u;
+        if (inten) inten[o] = fmaf(u.x, u.x, u.y * u.y);
+        if (phase) phase[o] = phase_of(u);
       }
     }
   }

@@ -1,12 +1,13 @@
-"""Persistent batched execution of ragged views over a stream of holograms.
+"""Batched execution of ragged views over a stream of holograms.
 
-shifted_fresnel_execute_batch runs every (hologram, view) of a call in one
-graph launch of the persistent kernel; its outputs must equal, bit for bit,
-shifted_fresnel_execute on each hologram (same arithmetic), across
-power-of-two and mixed (factor 3) FFT lengths in one launch, more holograms than intermediate slots,
-changing hologram counts and repeated calls.  A host-poisoned work queue
-must end the launch through its bounded waits and be reported as
-SF_ERR_TIMEOUT.
+shifted_fresnel_execute_batch runs every (hologram, view) of a call either
+as one graph launch of the persistent kernel or as the per-length row-pass
+kernels on two streams; with either implementation its outputs must equal,
+bit for bit, shifted_fresnel_execute on each hologram (same arithmetic),
+across power-of-two and mixed (factor 3) FFT lengths in one call, more
+holograms than intermediate slots, changing hologram counts and repeated
+calls.  A host-poisoned work queue must end the persistent launch through
+its bounded waits and be reported as SF_ERR_TIMEOUT.
 """
 
 import os
@@ -70,8 +71,13 @@ def check_equal(outs, ref):
             assert np.array_equal(outs["intensity"][h][v].cpu().numpy(), i_ref[v].cpu().numpy()), (h, v)
 
 
-def test_batch_equals_per_hologram_execute(P):
+IMPLS = ["persistent", "streams"]
+
+
+@pytest.mark.parametrize("impl", IMPLS)
+def test_batch_equals_per_hologram_execute(P, impl, monkeypatch):
     import torch
+    monkeypatch.setenv("SF_BATCH_IMPL", impl)
     vs = ragged_views()
     sf = P.ShiftedFresnel(vs)
     try:
@@ -102,9 +108,11 @@ def test_batch_equals_per_hologram_execute(P):
         sf.close()
 
 
-def test_batch_paper_sized_ragged_views(P):
+@pytest.mark.parametrize("impl", IMPLS)
+def test_batch_paper_sized_ragged_views(P, impl, monkeypatch):
     """2048^2 holograms with views of 256^2 .. 2048^2 (FFT lengths 2304, 3072 and 4096)."""
     import torch
+    monkeypatch.setenv("SF_BATCH_IMPL", impl)
     _, all_views = synth.config_c3(n_holos=1, n_views=64, with_holograms=False)
     picked = {}
     for v in all_views[0]:
@@ -142,10 +150,20 @@ def test_batch_rejects_bad_arguments(P):
     big = view(WAVELENGTH, 0.05, PITCH, PITCH, n0=(6000, 4), n1=(200, 4))  # FFT length 8192
     sfb = P.ShiftedFresnel([big])
     try:
-        hb = torch.zeros((4, 4000), dtype=torch.float32, device="cuda")
+        hb = torch.from_numpy(random_field(4, 6000, seed=1).real.astype(np.float32)).cuda()
         fb = torch.empty((4, 200), dtype=torch.complex64, device="cuda")
-        rc = P.shifted_fresnel_execute_batch(sfb.handle, [hb.data_ptr()], [fb.data_ptr()], check=False)
+        os.environ["SF_BATCH_IMPL"] = "persistent"  # beyond the persistent kernel's lengths
+        try:
+            rc = P.shifted_fresnel_execute_batch(sfb.handle, [hb.data_ptr()], [fb.data_ptr()], check=False)
+        finally:
+            del os.environ["SF_BATCH_IMPL"]
         assert rc == P.SF_ERR_UNSUPPORTED_SIZE
+        # the default falls back to the per-length kernels, which take any length
+        rc = P.shifted_fresnel_execute_batch(sfb.handle, [hb.data_ptr()], [fb.data_ptr()], check=False)
+        assert rc == P.SF_OK
+        ref = sfb.reconstruct(hb, field=True)["field"][0]
+        torch.cuda.synchronize()
+        assert torch.equal(fb, ref)
     finally:
         sfb.close()
 
@@ -156,6 +174,7 @@ def test_poisoned_queue_times_out_and_is_reported(P):
     vs = ragged_views()[:3]
     os.environ["SF_BATCH_POISON_GROUP"] = str(len(vs))  # the first y-pass group never sees its x tiles
     os.environ["SF_BATCH_SPIN_LIMIT"] = "2000"
+    os.environ["SF_BATCH_IMPL"] = "persistent"
     try:
         sf = P.ShiftedFresnel(vs)
         outs = sf.alloc_batch_outputs(2, field=True)
@@ -167,6 +186,7 @@ def test_poisoned_queue_times_out_and_is_reported(P):
     finally:
         del os.environ["SF_BATCH_POISON_GROUP"]
         del os.environ["SF_BATCH_SPIN_LIMIT"]
+        del os.environ["SF_BATCH_IMPL"]
     # the context is still usable
     sf = P.ShiftedFresnel(vs)
     try:
@@ -176,5 +196,23 @@ def test_poisoned_queue_times_out_and_is_reported(P):
         sf.execute_batch(holos, outs)
         torch.cuda.synchronize()
         check_equal(outs, ref)
+    finally:
+        sf.close()
+
+
+def test_batch_autotuned_implementation(P, monkeypatch):
+    """SF_AUTOTUNE=1: the first call per hologram count times both implementations; outputs stay exact."""
+    import torch
+    monkeypatch.setenv("SF_AUTOTUNE", "1")
+    vs = ragged_views()[:4]
+    sf = P.ShiftedFresnel(vs)
+    try:
+        holos = holograms(3, seed=7)
+        ref = per_hologram(sf, holos)
+        for _ in range(2):  # the first call measures, the second uses the choice
+            outs = sf.alloc_batch_outputs(3, field=True, intensity=True)
+            sf.execute_batch(holos, outs)
+            torch.cuda.synchronize()
+            check_equal(outs, ref)
     finally:
         sf.close()
