@@ -67,12 +67,12 @@ def measured_peaks():
 
 
 def source_hash():
-    """Hash of the device-code sources (every csrc file but the host API file);
-    ncu traffic figures are only used while it matches the captured version."""
+    """Hash of the sources the row-pass kernel k_pass is compiled from; ncu
+    traffic figures are only used while it matches the captured version."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1001_4309_gb300", "csrc", "*"))):
-        if os.path.basename(p) == "sf_api.cu":
-            continue
+    csrc = os.path.join(ROOT, "paper_1001_4309_gb300", "csrc")
+    files = [os.path.join(csrc, n) for n in ("sf_fft.cuh", "sf_kernels.cuh", "sf_internal.h", "sf_launch.cu")]
+    for p in sorted(files + glob.glob(os.path.join(csrc, "sf_inst_*.cu"))):
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())
