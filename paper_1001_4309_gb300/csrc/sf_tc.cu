@@ -7,19 +7,32 @@
 //
 //   C (2R x L/R) = A_R (2R x 2R) * B (2R x L/R)
 //
-// with A_R the real block [[Wr, -Wi], [Wi, Wr]] of the radix-R DFT matrix
-// (its conjugate for the inverse) and column b of B the 2R real inputs of
-// butterfly b (re of elements 0..R-1, then im).  B lives in shared memory as
-// [b][2R + 8] halves (inputs contiguous, rows padded by 16 bytes so ldmatrix
-// is conflict-free).  Each stage epilogue works in FP32 on the accumulator
-// fragments: it applies the stage's twiddle (forward) or the next stage's
-// conjugated twiddle (inverse), a 1/sqrt(R) scale that keeps values in
-// half-precision range, and scatters the values into the next stage's
-// layout.  The last forward epilogue multiplies by the kernel spectrum (in
-// position order, scaled by 1/sqrt(L)) and keeps the layout for the first
-// inverse stage; the last inverse epilogue undoes the scales, applies the
-// output chirp and stores the row.  Rows are normalised by their largest
-// input magnitude before the first conversion to half precision.
+// with A_R the real block [[Wr, -Wi], [Wi, Wr]] / sqrt(R) of the radix-R DFT
+// matrix (its conjugate for the inverse; the unitary scale keeps values in
+// half-precision range) and column b of B the 2R real inputs of butterfly b
+// (re of elements 0..R-1, then im).
+//
+// Shared-memory layout: per row, a real plane and an imaginary plane of L
+// halves indexed by network position p (the same positions as the FP32
+// network), with 16-byte chunks XOR-swizzled (swz) so that every access
+// below is free of bank conflicts.  Butterfly b of stage s reads element j
+// at p = (b / M) M' + b % M + j M.  When M >= 8, eight consecutive
+// butterflies read eight consecutive positions for each j, so the B operand
+// of an 8-butterfly tile is eight 16-byte rows indexed by j: ldmatrix.trans.
+// When M = 1 (the last stage) a butterfly's R elements are consecutive:
+// plain ldmatrix with rows indexed by butterfly.  The accumulator of a lane
+// holds outputs (k, b) and (k, b + 1): for M >= 2 these sit at consecutive
+// positions, so the epilogue (FP32 twiddle, conversion) stores one 4-byte
+// pair per plane.
+//
+// Epilogues: forward stage s multiplies by its twiddle W_{M'}^{n k}; the last
+// forward stage multiplies by the kernel spectrum in position order (scaled
+// by 1/sqrt(L)); inverse stage s (conjugate DFT) multiplies by the conjugated
+// twiddle of stage s - 1, since the adjoint network applies it before that
+// stage's DFT; the last inverse stage undoes the three 1/sqrt(L) scales and
+// the row normalisation, applies the output chirp and stores the row.  Rows
+// are normalised by their largest input component before the first
+// conversion to half precision.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -31,29 +44,38 @@ namespace tc {
 constexpr int kRows = 4;       // rows per CTA
 constexpr int kThreads = 256;  // 8 warps
 
-template <int R>
-__host__ __device__ constexpr int bstride() { return 2 * R + 8; }  // halves per butterfly row
-
-template <int L>
-__host__ __device__ constexpr int buf_halves() {
-  return (L / 16) * bstride<16>() > (L / 8) * bstride<8>() ? (L / 16) * bstride<16>() : (L / 8) * bstride<8>();
+// swizzled half index of position p within a plane (bijective on 0..L-1)
+__host__ __device__ constexpr int swz(int p) {
+  return (((p >> 3) ^ (((p >> 6) ^ (p >> 9)) & 7)) << 3) | (p & 7);
 }
 
 template <int L>
 struct TcShape {
-  static constexpr int BUF = buf_halves<L>();
-  static constexpr size_t SMEM = sizeof(uint16_t) * 2 * kRows * (size_t)BUF + 16 * kRows;
+  static constexpr int BUF = 2 * kRows * L;  // halves per buffer: re and im planes of kRows rows
+  static constexpr size_t SMEM = sizeof(uint16_t) * 2 * (size_t)BUF + 16 * kRows;
+  // the output tile [n1][kRows] (float2) is staged in the free buffer when it fits
+  static constexpr int TILE_N1 = (int)(sizeof(uint16_t) * BUF / (sizeof(float2) * kRows));
 };
 
 template <int PREC>
-__device__ __forceinline__ void st_half(uint16_t* p, float v) {
-  v = fminf(fmaxf(v, -65504.f), 65504.f);
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if constexpr (PREC == SF_PREC_BF16TC) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ uint16_t pack1(float v) {
   if constexpr (PREC == SF_PREC_BF16TC) {
     __nv_bfloat16 h = __float2bfloat16_rn(v);
-    *p = *reinterpret_cast<uint16_t*>(&h);
+    return *reinterpret_cast<uint16_t*>(&h);
   } else {
     __half h = __float2half_rn(v);
-    *p = *reinterpret_cast<uint16_t*>(&h);
+    return *reinterpret_cast<uint16_t*>(&h);
   }
 }
 
@@ -74,18 +96,24 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], 
   }
 }
 
-__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const uint16_t* p) {
+template <bool TRANS>
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const uint16_t* p) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(a));
+  if constexpr (TRANS)
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+  else
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
 }
 
-// W_{M'}^{n k} of stage S (conjugated when CONJ), from the FP32 network's table.
-template <int L, int S, bool CONJ>
-__device__ __forceinline__ float2 twiddle(const float4* __restrict__ tw, int n, int k) {
-  using St = Stage<L, kTcE, S>;
-  const float4 w = __ldg(tw + stage_tw_offset(L, kTcE, S) + (k >> 1) * St::M + n);
-  const float2 v = (k & 1) ? make_float2(w.z, w.w) : make_float2(w.x, w.y);
-  return CONJ ? make_float2(v.x, -v.y) : v;
+template <bool TRANS>
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[4], const uint16_t* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  if constexpr (TRANS)
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+  else
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
 }
 
 template <int L, int S>
@@ -94,38 +122,50 @@ __device__ __forceinline__ int pos_of(int b, int k) {
   return (b / St::M) * St::MP + (b % St::M) + k * St::M;
 }
 
-template <int L, int S>
-__device__ __forceinline__ void bk_of(int p, int& b, int& k) {
-  using St = Stage<L, kTcE, S>;
-  const int K = p / St::MP, rem = p - K * St::MP;
-  const int n = rem % St::M;
-  k = rem / St::M;
-  b = K * St::M + n;
+// Twiddle tables of the tensor-core network, stage s (with M > 1) as
+// [k][n] = W_{M'}^{n k}, n < M, k < R, complex FP32; stages concatenated.
+template <int L>
+__host__ __device__ constexpr int tw_offset(int S) {
+  int o = 0;
+  for (int i = 0; i < S; ++i)
+    o += (stage_mprev(L, kTcE, i) / stage_radix(L, kTcE, i)) > 1 ? stage_mprev(L, kTcE, i) : 0;
+  return o;
 }
-
-// Store one complex value at position p of row `row` in stage S's input layout.
-template <int L, int S, int PREC>
-__device__ __forceinline__ void put(uint16_t* buf, int row, int p, float2 v) {
-  constexpr int R = Stage<L, kTcE, S>::R;
-  int b, k;
-  bk_of<L, S>(p, b, k);
-  uint16_t* q = buf + row * TcShape<L>::BUF + b * bstride<R>();
-  st_half<PREC>(q + k, v.x);
-  st_half<PREC>(q + R + k, v.y);
-}
+template <int L>
+__host__ __device__ constexpr int tw_entries() { return tw_offset<L>(stage_count(L, kTcE)); }
 
 // Per-lane A fragments: [dir][mt][kt][q][lane] for radix 16, then for radix 8.
 __host__ __device__ constexpr int frag_words(int R) { return 2 * (R / 8) * (R / 8) * 4 * 32; }
 
-// One stage's GEMM over all rows of the CTA; epi(row, butterfly, element, value).
+__device__ __forceinline__ uint16_t* plane(uint16_t* buf, int L, int row, int im) {
+  return buf + (row * 2 + im) * L;
+}
+
+// Store the pair (b, k), (b + 1, k) at positions p, p + 1 (p even).
+template <int L, int PREC>
+__device__ __forceinline__ void put_pair(uint16_t* buf, int row, int p, float2 v0, float2 v1) {
+  const int a = swz(p);
+  *reinterpret_cast<uint32_t*>(plane(buf, L, row, 0) + a) = pack2<PREC>(v0.x, v1.x);
+  *reinterpret_cast<uint32_t*>(plane(buf, L, row, 1) + a) = pack2<PREC>(v0.y, v1.y);
+}
+
+template <int L, int PREC>
+__device__ __forceinline__ void put_one(uint16_t* buf, int row, int p, float2 v) {
+  const int a = swz(p);
+  plane(buf, L, row, 0)[a] = pack1<PREC>(v.x);
+  plane(buf, L, row, 1)[a] = pack1<PREC>(v.y);
+}
+
+// One stage's GEMM over all rows of the CTA; epi(row, b, k, value of b, value of b + 1).
 template <int L, int S, int PREC, bool INV, typename Epi>
-__device__ __forceinline__ void stage_gemm(const uint16_t* in, const uint32_t* __restrict__ frags, Epi&& epi) {
+__device__ __forceinline__ void stage_gemm(uint16_t* in, const uint32_t* __restrict__ frags, Epi&& epi) {
   using St = Stage<L, kTcE, S>;
-  constexpr int R = St::R;
+  constexpr int R = St::R, M = St::M;
   static_assert(R == 16 || R == 8, "tensor-core stages need radix 8 or 16");
+  static_assert(M >= 8 || M == 1, "operand tiles need M >= 8 or M = 1");
   constexpr int NT = L / R / 8;   // n-tiles (8 butterflies) per row
   constexpr int T2 = 2 * R / 16;  // m-tiles = k-steps of the real block
-  constexpr int BS = bstride<R>();
+  constexpr bool TRANS = M >= 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, tig = lane & 3;
   const uint32_t* fp = frags + (R == 16 ? 0 : frag_words(16)) + (INV ? frag_words(R) / 2 : 0);
@@ -136,100 +176,105 @@ __device__ __forceinline__ void stage_gemm(const uint16_t* in, const uint32_t* _
     for (int kt = 0; kt < T2; ++kt)
 #pragma unroll
       for (int q = 0; q < 4; ++q) a[mt][kt][q] = __ldg(fp + ((mt * T2 + kt) * 4 + q) * 32 + lane);
+  // this lane's ldmatrix row: matrix m = lane / 8 (R = 16: re j 0-7, re j 8-15, im j 0-7, im j 8-15;
+  // R = 8: re j 0-7, im j 0-7), row rr = lane % 8 (element j0 + rr, or butterfly b0 + rr when M = 1)
+  const int m = (lane >> 3) & (R == 16 ? 3 : 1), rr = lane & 7;
+  const int im = R == 16 ? (m >> 1) : m, j0 = R == 16 ? (m & 1) * 8 : 0;
   for (int unit = warp; unit < kRows * NT; unit += kThreads / 32) {
-    const int row = unit / NT, nt = unit - row * NT;
-    const uint16_t* bb = in + row * TcShape<L>::BUF + (nt * 8 + (lane & 7)) * BS + ((lane >> 3) & 1) * 8;
+    const int row = unit / NT, b0 = (unit - row * NT) * 8;
+    const int p = TRANS ? pos_of<L, S>(b0, j0 + rr) : pos_of<L, S>(b0 + rr, j0);
+    const uint16_t* src = plane(in, L, row, im) + swz(p);
+    uint32_t bf[4];
+    if constexpr (R == 16) ldsm_x4<TRANS>(bf, src);
+    else ldsm_x2<TRANS>(bf, src);
     float c[T2][4];
 #pragma unroll
     for (int mt = 0; mt < T2; ++mt) c[mt][0] = c[mt][1] = c[mt][2] = c[mt][3] = 0.f;
 #pragma unroll
-    for (int kt = 0; kt < T2; ++kt) {
-      uint32_t b0, b1;
-      ldsm_x2(b0, b1, bb + kt * 16);
+    for (int kt = 0; kt < T2; ++kt)
 #pragma unroll
-      for (int mt = 0; mt < T2; ++mt) mma16816<PREC>(c[mt], a[mt][kt], b0, b1);
-    }
-    const int bi = nt * 8 + 2 * tig;
+      for (int mt = 0; mt < T2; ++mt) mma16816<PREC>(c[mt], a[mt][kt], bf[2 * kt], bf[2 * kt + 1]);
+    const int bi = b0 + 2 * tig;
     if constexpr (R == 16) {
       // tile 0: re of elements 0..15, tile 1: im; rows g and g + 8, columns bi, bi + 1
-      epi(row, bi, g, make_float2(c[0][0], c[1][0]));
-      epi(row, bi + 1, g, make_float2(c[0][1], c[1][1]));
-      epi(row, bi, g + 8, make_float2(c[0][2], c[1][2]));
-      epi(row, bi + 1, g + 8, make_float2(c[0][3], c[1][3]));
+      epi(row, bi, g, make_float2(c[0][0], c[1][0]), make_float2(c[0][1], c[1][1]));
+      epi(row, bi, g + 8, make_float2(c[0][2], c[1][2]), make_float2(c[0][3], c[1][3]));
     } else {
       // one tile: row g = re of element g, row g + 8 = im of element g
-      epi(row, bi, g, make_float2(c[0][0], c[0][2]));
-      epi(row, bi + 1, g, make_float2(c[0][1], c[0][3]));
+      epi(row, bi, g, make_float2(c[0][0], c[0][2]), make_float2(c[0][1], c[0][3]));
     }
   }
 }
 
-template <int R>
-__device__ __forceinline__ constexpr float inv_sqrt_radix() {
-  return R == 16 ? 0.25f : (R == 8 ? 0.35355339059327373f : 1.0f);
-}
-
-// Forward stages S.. of the network; returns the buffer holding the layout of
-// the last stage after the spectrum multiply.
+// Forward stages S.. of the network; returns the buffer holding the last
+// stage's positions after the spectrum multiply.
 template <int L, int S, int PREC>
 __device__ __forceinline__ uint16_t* forward(uint16_t* cur, uint16_t* oth, const uint32_t* frags,
-                                             const float4* __restrict__ tw, const float2* __restrict__ Hpos,
-                                             float hs) {
+                                             const float2* __restrict__ tw, const float2* __restrict__ Hpos) {
   using St = Stage<L, kTcE, S>;
   constexpr int NS = stage_count(L, kTcE);
-  constexpr float f = inv_sqrt_radix<St::R>();
   if constexpr (S + 1 < NS) {
-    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 v) {
-      const float2 w = twiddle<L, S, false>(tw, b % St::M, k);
-      put<L, S + 1, PREC>(oth, row, pos_of<L, S>(b, k),
-                          make_float2(f * (v.x * w.x - v.y * w.y), f * (v.x * w.y + v.y * w.x)));
+    static_assert(St::M >= 2, "twiddled stages pair adjacent butterflies");
+    const float2* t = tw + tw_offset<L>(S);
+    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 v0, float2 v1) {
+      const float4 w = __ldg(reinterpret_cast<const float4*>(t + k * St::M + b % St::M));
+      put_pair<L, PREC>(oth, row, pos_of<L, S>(b, k), cmul(v0, make_float2(w.x, w.y)),
+                        cmul(v1, make_float2(w.z, w.w)));
     });
     __syncthreads();
-    return forward<L, S + 1, PREC>(oth, cur, frags, tw, Hpos, hs);
+    return forward<L, S + 1, PREC>(oth, cur, frags, tw, Hpos);
   } else {
-    const float sc = f * hs;
-    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 v) {
-      const int p = pos_of<L, S>(b, k);
-      const float2 h = __ldg(Hpos + p);
-      put<L, S, PREC>(oth, row, p, make_float2(sc * (v.x * h.x - v.y * h.y), sc * (v.x * h.y + v.y * h.x)));
+    static_assert(St::M == 1, "the last stage has unit stride");
+    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 v0, float2 v1) {
+      const int p0 = b * St::R + k, p1 = p0 + St::R;
+      put_one<L, PREC>(oth, row, p0, cmul(v0, __ldg(Hpos + p0)));
+      put_one<L, PREC>(oth, row, p1, cmul(v1, __ldg(Hpos + p1)));
     });
     __syncthreads();
     return oth;
   }
 }
 
-// Inverse stages S..0; the last one hands (row, natural position, value) to `out`.
+// Inverse stages S..0; the last one hands (row, position, value, value at
+// position + 1) to `out` (natural, even positions).
 template <int L, int S, int PREC, typename Out>
 __device__ __forceinline__ void inverse(uint16_t* cur, uint16_t* oth, const uint32_t* frags,
-                                        const float4* __restrict__ tw, Out&& out) {
+                                        const float2* __restrict__ tw, Out&& out) {
   using St = Stage<L, kTcE, S>;
-  constexpr float f = inv_sqrt_radix<St::R>();
   if constexpr (S > 0) {
     using Sp = Stage<L, kTcE, S - 1>;
-    stage_gemm<L, S, PREC, true>(cur, frags, [&](int row, int b, int k, float2 v) {
-      const int p = pos_of<L, S>(b, k);
-      int bp, kp;
-      bk_of<L, S - 1>(p, bp, kp);
-      const float2 w = twiddle<L, S - 1, true>(tw, bp % Sp::M, kp);
-      put<L, S - 1, PREC>(oth, row, p, make_float2(f * (v.x * w.x - v.y * w.y), f * (v.x * w.y + v.y * w.x)));
+    const float2* t = tw + tw_offset<L>(S - 1);
+    stage_gemm<L, S, PREC, true>(cur, frags, [&](int row, int b, int j, float2 v0, float2 v1) {
+      if constexpr (St::M >= 2) {
+        // positions p, p + 1 of stage S - 1: n = p mod M, k = (p mod M') / M there
+        const int p = pos_of<L, S>(b, j);
+        const int n = p % Sp::M, k = (p % Sp::MP) / Sp::M;
+        const float4 w = __ldg(reinterpret_cast<const float4*>(t + k * Sp::M + n));
+        put_pair<L, PREC>(oth, row, p, cmulc(v0, make_float2(w.x, w.y)), cmulc(v1, make_float2(w.z, w.w)));
+      } else {
+        const int p0 = b * St::R + j, p1 = p0 + St::R;
+        put_one<L, PREC>(oth, row, p0, cmulc(v0, __ldg(t + ((p0 % Sp::MP) / Sp::M) * Sp::M + p0 % Sp::M)));
+        put_one<L, PREC>(oth, row, p1, cmulc(v1, __ldg(t + ((p1 % Sp::MP) / Sp::M) * Sp::M + p1 % Sp::M)));
+      }
     });
     __syncthreads();
     inverse<L, S - 1, PREC>(oth, cur, frags, tw, out);
   } else {
-    stage_gemm<L, 0, PREC, true>(cur, frags, [&](int row, int b, int k, float2 v) {
-      out(row, pos_of<L, 0>(b, k), make_float2(f * v.x, f * v.y));
+    static_assert(St::M >= 2, "the first stage pairs adjacent positions");
+    stage_gemm<L, 0, PREC, true>(cur, frags, [&](int row, int b, int j, float2 v0, float2 v1) {
+      out(row, pos_of<L, 0>(b, j), v0, v1);
     });
   }
 }
 
 template <int L, int KIND, int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-k_pass_tc(const __grid_constant__ PassBatch pb, const float4* __restrict__ tw, const uint32_t* __restrict__ frags) {
+k_pass_tc(const __grid_constant__ PassBatch pb, const float2* __restrict__ tw, const uint32_t* __restrict__ frags) {
   extern __shared__ __align__(16) uint16_t sm[];
   constexpr int BUF = TcShape<L>::BUF;
   uint16_t* buf0 = sm;
-  uint16_t* buf1 = sm + kRows * BUF;
-  unsigned* rowmax = reinterpret_cast<unsigned*>(sm + 2 * kRows * BUF);
+  uint16_t* buf1 = sm + BUF;
+  unsigned* rowmax = reinterpret_cast<unsigned*>(sm + 2 * BUF);
   const PassDesc& d = pb.d[blockIdx.y];
   const int row0 = blockIdx.x * kRows;
   if (row0 >= d.rows) return;
@@ -246,7 +291,7 @@ k_pass_tc(const __grid_constant__ PassBatch pb, const float4* __restrict__ tw, c
     }
   };
 
-  // 1. largest input magnitude of each row
+  // 1. largest input component of each row
   if (tid < kRows) rowmax[tid] = 0u;
   __syncthreads();
   for (int r = 0; r < kRows; ++r) {
@@ -261,32 +306,38 @@ k_pass_tc(const __grid_constant__ PassBatch pb, const float4* __restrict__ tw, c
     if (lane == 0 && m > 0.f) atomicMax(rowmax + r, __float_as_uint(m));
   }
   __syncthreads();
-  // 2. normalised input in the layout of stage 0 (implicit zero padding)
+  // 2. normalised input at natural positions (stage 0's layout), pairs of positions, zero padding
   for (int r = 0; r < kRows; ++r) {
     const int row = row0 + r;
     const float mx = __uint_as_float(rowmax[r]);
     const float s0 = mx > 0.f ? 1.0f / mx : 0.f;
-    for (int p = tid; p < L; p += kThreads) {
-      float2 v = make_float2(0.f, 0.f);
-      if (row < d.rows && p < d.n0) {
-        v = load(row, p);
-        v = make_float2(v.x * s0, v.y * s0);
+    for (int p = 2 * tid; p < L; p += 2 * kThreads) {
+      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+      if (row < d.rows) {
+        if (p < d.n0) v0 = load(row, p);
+        if (p + 1 < d.n0) v1 = load(row, p + 1);
       }
-      put<L, 0, PREC>(buf0, r, p, v);
+      put_pair<L, PREC>(buf0, r, p, make_float2(v0.x * s0, v0.y * s0), make_float2(v1.x * s0, v1.y * s0));
     }
   }
   __syncthreads();
 
   // 3. forward network and spectrum, 4. inverse network and output
-  const float hs = rsqrtf((float)L);
-  uint16_t* spec = forward<L, 0, PREC>(buf0, buf1, frags, tw, reinterpret_cast<const float2*>(d.H), hs);
+  uint16_t* spec = forward<L, 0, PREC>(buf0, buf1, frags, tw, reinterpret_cast<const float2*>(d.H));
   uint16_t* other = spec == buf0 ? buf1 : buf0;
   const float undo = (float)L * sqrtf((float)L);  // the three 1/sqrt(L) scales
-  inverse<L, stage_count(L, kTcE) - 1, PREC>(spec, other, frags, tw, [&](int r, int p, float2 v) {
+  const int n1 = d.n1;
+  const bool staged = n1 <= TcShape<L>::TILE_N1;
+  float2* tile = reinterpret_cast<float2*>(other);  // free during the last inverse stage
+  auto emit = [&](int r, int p, float2 v) {
     const int row = row0 + r;
-    if (row >= d.rows || p >= d.n1) return;
     const float s = undo * __uint_as_float(rowmax[r]);
     const float2 u = cmul(make_float2(v.x * s, v.y * s), __ldg(reinterpret_cast<const float2*>(d.cout) + p));
+    if (staged) {
+      tile[p * kRows + r] = u;
+      return;
+    }
+    if (row >= d.rows) return;
     const size_t o = (size_t)p * d.dst_ld + row;
     if constexpr (KIND != PASS_Y) {
       d.dst[o] = u;
@@ -295,11 +346,38 @@ k_pass_tc(const __grid_constant__ PassBatch pb, const float4* __restrict__ tw, c
       if (d.inten) d.inten[o] = fmaf(u.x, u.x, u.y * u.y);
       if (d.phase) d.phase[o] = phase_of(u);
     }
+  };
+  inverse<L, stage_count(L, kTcE) - 1, PREC>(spec, other, frags, tw, [&](int r, int p, float2 v0, float2 v1) {
+    if (p < n1) emit(r, p, v0);
+    if (p + 1 < n1) emit(r, p + 1, v1);
   });
+  if (!staged) return;
+  __syncthreads();
+  // 5. the staged tile [n1][kRows] leaves as kRows-element runs of the transposed output
+  float2* const dst = d.dst;
+  float* const inten = d.inten;
+  float* const phase = d.phase;
+  const size_t dst_ld = (size_t)d.dst_ld;
+  const bool acc = d.accumulate != 0;
+  const int rows_here = min(kRows, d.rows - row0);
+  for (int i = tid; i < n1 * kRows; i += kThreads) {
+    const int p = i / kRows, r = i - p * kRows;
+    if (r >= rows_here) continue;
+    const float2 u = tile[i];
+    const size_t o = (size_t)p * dst_ld + row0 + r;
+    if constexpr (KIND != PASS_Y) {
+      dst[o] = u;
+    } else {
+      if (dst) dst[o] = acc ? cadd(dst[o], u) : u;
+      if (inten) inten[o] = fmaf(u.x, u.x, u.y * u.y);
+      if (phase) phase[o] = phase_of(u);
+    }
+  }
 }
 
-// Per-lane A fragments of the real-block DFT matrices, built once per
-// precision: for R = 16 then R = 8, forward then inverse, [mt][kt][q][lane].
+// Per-lane A fragments of the real-block DFT matrices with the unitary scale
+// 1/sqrt(R), built once per precision: for R = 16 then R = 8, forward then
+// inverse, [mt][kt][q][lane].
 template <int PREC>
 __global__ void k_tc_frags(uint32_t* out) {
   const int lane = threadIdx.x;
@@ -307,16 +385,17 @@ __global__ void k_tc_frags(uint32_t* out) {
   int base = 0;
   for (int R = 16; R >= 8; R /= 2) {
     const int T2 = 2 * R / 16;
+    const double scale = 1.0 / sqrt((double)R);
     for (int inv = 0; inv < 2; ++inv) {
       auto A = [&](int r, int c) -> float {
         const int k = r % R, j = c % R;
         double s, co;
         sincospi((inv ? 2.0 : -2.0) * (double)((j * k) % R) / (double)R, &s, &co);
         const bool rre = r < R, cre = c < R;
-        if (rre && cre) return (float)co;
-        if (rre && !cre) return (float)-s;
-        if (!rre && cre) return (float)s;
-        return (float)co;
+        if (rre && cre) return (float)(scale * co);
+        if (rre && !cre) return (float)(-scale * s);
+        if (!rre && cre) return (float)(scale * s);
+        return (float)(scale * co);
       };
       for (int mt = 0; mt < T2; ++mt)
         for (int kt = 0; kt < T2; ++kt) {
@@ -325,42 +404,53 @@ __global__ void k_tc_frags(uint32_t* out) {
                                  {A(r0 + 8, c0), A(r0 + 8, c0 + 1)},
                                  {A(r0, c0 + 8), A(r0, c0 + 9)},
                                  {A(r0 + 8, c0 + 8), A(r0 + 8, c0 + 9)}};
-          for (int q = 0; q < 4; ++q) {
-            uint32_t w;
-            if (PREC == SF_PREC_BF16TC) {
-              __nv_bfloat162 h = __floats2bfloat162_rn(v[q][0], v[q][1]);
-              w = *reinterpret_cast<uint32_t*>(&h);
-            } else {
-              __half2 h = __floats2half2_rn(v[q][0], v[q][1]);
-              w = *reinterpret_cast<uint32_t*>(&h);
-            }
-            out[base + ((mt * T2 + kt) * 4 + q) * 32 + lane] = w;
-          }
+          for (int q = 0; q < 4; ++q) out[base + ((mt * T2 + kt) * 4 + q) * 32 + lane] = pack2<PREC>(v[q][0], v[q][1]);
         }
       base += frag_words(R) / 2;
     }
   }
 }
 
-// Kernel spectrum from register order (FP32 network) to position order.
+// Twiddle tables of one length ([k][n] = W_{M'}^{n k} per stage with M > 1),
+// double-precision sincospi rounded to float; one thread per entry.
+template <int L>
+__global__ void k_tc_twiddles(float2* tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= tw_entries<L>()) return;
+  int s = 0;
+  while (tw_offset<L>(s + 1) <= i) ++s;
+  const int MP = stage_mprev(L, kTcE, s), R = stage_radix(L, kTcE, s), M = MP / R;
+  const int local = i - tw_offset<L>(s), k = local / M, n = local - k * M;
+  double sn, cs;
+  sincospi(-2.0 * (double)(((long long)n * k) % MP) / (double)MP, &sn, &cs);
+  tab[i] = make_float2((float)cs, (float)sn);
+}
+
+// Kernel spectrum from register order (FP32 network) to position order,
+// scaled by 1/sqrt(L) (the unitary scale of the spectrum multiply).
 template <int L>
 __global__ void k_hpos(const float2* __restrict__ Hreg, float2* __restrict__ Hpos) {
   constexpr int T = L / kE;
+  const float hs = rsqrtf((float)L);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
 #pragma unroll
-  for (int e = 0; e < kE; ++e) Hpos[last_pos<L, kE>(t, e)] = Hreg[e * T + t];
+  for (int e = 0; e < kE; ++e) {
+    const float2 h = Hreg[e * T + t];
+    Hpos[last_pos<L, kE>(t, e)] = make_float2(h.x * hs, h.y * hs);
+  }
 }
 
 template <int L, int PREC>
-cudaError_t launch_tc_t(PassKind kind, const PassBatch& b, int grid_x, const float4* tw, const uint32_t* frags,
-                        cudaStream_t s) {
+cudaError_t launch_tc_t(PassKind kind, const PassBatch& b, int grid_x, const uint32_t* tables, cudaStream_t s) {
   const dim3 grid(grid_x, b.count), block(kThreads);
   constexpr size_t smem = TcShape<L>::SMEM;
+  const float2* tw = reinterpret_cast<const float2*>(tables + frag_words(16) + frag_words(8)) +
+                     (L == 4096 ? tw_entries<2048>() : 0);
   auto go = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, block, smem, s>>>(b, tw, frags);
+    kern<<<grid, block, smem, s>>>(b, tw, tables);
     return cudaGetLastError();
   };
   switch (kind) {
@@ -377,11 +467,19 @@ cudaError_t launch_tc_t(PassKind kind, const PassBatch& b, int grid_x, const flo
 // networks must share their radix plan.
 bool tc_length_supported(int L) { return kE == kTcE && (L == 2048 || L == 4096); }
 int tc_rows_per_cta() { return tc::kRows; }
-size_t tc_frag_words() { return (size_t)tc::frag_words(16) + tc::frag_words(8); }
+// A fragments, then the twiddle tables of 2048 and 4096 (float2)
+size_t tc_frag_words() {
+  return (size_t)tc::frag_words(16) + tc::frag_words(8) + 2 * (tc::tw_entries<2048>() + tc::tw_entries<4096>());
+}
 
 cudaError_t launch_tc_frags(uint32_t* out, int prec, cudaStream_t s) {
   if (prec == SF_PREC_BF16TC) tc::k_tc_frags<SF_PREC_BF16TC><<<1, 32, 0, s>>>(out);
   else tc::k_tc_frags<SF_PREC_FP16TC><<<1, 32, 0, s>>>(out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  float2* tw = reinterpret_cast<float2*>(out + tc::frag_words(16) + tc::frag_words(8));
+  tc::k_tc_twiddles<2048><<<(tc::tw_entries<2048>() + 255) / 256, 256, 0, s>>>(tw);
+  tc::k_tc_twiddles<4096><<<(tc::tw_entries<4096>() + 255) / 256, 256, 0, s>>>(tw + tc::tw_entries<2048>());
   return cudaGetLastError();
 }
 
@@ -396,12 +494,13 @@ cudaError_t launch_hpos(int L, const float2* Hreg, float2* Hpos, cudaStream_t s)
 
 cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, int grid_x, const float4* tw,
                            const uint32_t* frags, cudaStream_t s) {
+  (void)tw;  // the tensor-core network has its own twiddle tables (after the fragments)
   if (prec == SF_PREC_BF16TC) {
-    if (L == 2048) return tc::launch_tc_t<2048, SF_PREC_BF16TC>(kind, b, grid_x, tw, frags, s);
-    if (L == 4096) return tc::launch_tc_t<4096, SF_PREC_BF16TC>(kind, b, grid_x, tw, frags, s);
+    if (L == 2048) return tc::launch_tc_t<2048, SF_PREC_BF16TC>(kind, b, grid_x, frags, s);
+    if (L == 4096) return tc::launch_tc_t<4096, SF_PREC_BF16TC>(kind, b, grid_x, frags, s);
   } else {
-    if (L == 2048) return tc::launch_tc_t<2048, SF_PREC_FP16TC>(kind, b, grid_x, tw, frags, s);
-    if (L == 4096) return tc::launch_tc_t<4096, SF_PREC_FP16TC>(kind, b, grid_x, tw, frags, s);
+    if (L == 2048) return tc::launch_tc_t<2048, SF_PREC_FP16TC>(kind, b, grid_x, frags, s);
+    if (L == 4096) return tc::launch_tc_t<4096, SF_PREC_FP16TC>(kind, b, grid_x, frags, s);
   }
   return cudaErrorInvalidValue;
 }
