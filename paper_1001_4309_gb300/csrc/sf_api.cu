@@ -579,7 +579,7 @@ cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* 
     const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
     if (plan->tc_frags && tc_length_supported(L)) {
       for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[batch_view[k]].hpos[axis];
-      const int G = tc_rows_per_cta();
+      const int G = tc_rows_per_cta(L);
       e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tw[L], plan->tc_frags, s);
     } else if (persistent_eligible(plan, L, kind, b)) {
       e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);

@@ -114,7 +114,7 @@ cudaError_t launch_pass_persistent(int L, PassKind kind, const PassBatch& b, con
 
 // Mixed-precision row pass (sf_tc.cu)
 bool tc_length_supported(int L);
-int tc_rows_per_cta();
+int tc_rows_per_cta(int L);
 size_t tc_frag_words();
 cudaError_t launch_tc_frags(uint32_t* out, int prec, cudaStream_t s);
 cudaError_t launch_hpos(int L, const float2* Hreg, float2* Hpos, cudaStream_t s);

@@ -41,8 +41,17 @@
 namespace sf {
 namespace tc {
 
-constexpr int kRows = 4;       // rows per CTA
 constexpr int kThreads = 256;  // 8 warps
+// unroll of the per-warp tile loop (measured best at 2048 within the
+// register budget of three CTAs per SM; 4096 spills when unrolled)
+template <int L>
+__host__ __device__ constexpr int unroll_of() { return L == 2048 ? 4 : 1; }
+// rows per CTA: 64 KiB of half-precision buffers per CTA at either length
+template <int L>
+__host__ __device__ constexpr int rows_of() { return L == 4096 ? 2 : 4; }
+// CTAs per SM the register budget is set for (shared memory allows three)
+template <int L>
+__host__ __device__ constexpr int ctas_of() { return 3; }
 
 // swizzled half index of position p within a plane (bijective on 0..L-1)
 __host__ __device__ constexpr int swz(int p) {
@@ -51,6 +60,7 @@ __host__ __device__ constexpr int swz(int p) {
 
 template <int L>
 struct TcShape {
+  static constexpr int kRows = rows_of<L>();
   static constexpr int BUF = 2 * kRows * L;  // halves per buffer: re and im planes of kRows rows
   static constexpr size_t SMEM = sizeof(uint16_t) * 2 * (size_t)BUF + 16 * kRows;
   // the output tile [n1][kRows] (float2) is staged in the free buffer when it fits
@@ -141,12 +151,13 @@ __device__ __forceinline__ uint16_t* plane(uint16_t* buf, int L, int row, int im
   return buf + (row * 2 + im) * L;
 }
 
-// Store the pair (b, k), (b + 1, k) at positions p, p + 1 (p even).
+// Store butterflies b, b + 1 of one output element at positions p, p + 1
+// (p even): X = their real parts, Y = their imaginary parts.
 template <int L, int PREC>
-__device__ __forceinline__ void put_pair(uint16_t* buf, int row, int p, float2 v0, float2 v1) {
+__device__ __forceinline__ void put_pair(uint16_t* buf, int row, int p, float2 X, float2 Y) {
   const int a = swz(p);
-  *reinterpret_cast<uint32_t*>(plane(buf, L, row, 0) + a) = pack2<PREC>(v0.x, v1.x);
-  *reinterpret_cast<uint32_t*>(plane(buf, L, row, 1) + a) = pack2<PREC>(v0.y, v1.y);
+  *reinterpret_cast<uint32_t*>(plane(buf, L, row, 0) + a) = pack2<PREC>(X.x, X.y);
+  *reinterpret_cast<uint32_t*>(plane(buf, L, row, 1) + a) = pack2<PREC>(Y.x, Y.y);
 }
 
 template <int L, int PREC>
@@ -156,7 +167,28 @@ __device__ __forceinline__ void put_one(uint16_t* buf, int row, int p, float2 v)
   plane(buf, L, row, 1)[a] = pack1<PREC>(v.y);
 }
 
-// One stage's GEMM over all rows of the CTA; epi(row, b, k, value of b, value of b + 1).
+// (X + i Y) * (WX + i WY) for two values at once (packed f32x2 arithmetic);
+// CONJ multiplies by the conjugate.  The results overwrite X and Y.
+template <bool CONJ>
+__device__ __forceinline__ void cmul_pair(float2& X, float2& Y, float2 WX, float2 WY) {
+  const float2 nwy = __fmul2_rn(WY, make_float2(-1.f, -1.f));
+  float2 re, im;
+  if constexpr (!CONJ) {
+    re = __ffma2_rn(Y, nwy, __fmul2_rn(X, WX));  // X WX - Y WY
+    im = __ffma2_rn(X, WY, __fmul2_rn(Y, WX));   // X WY + Y WX
+  } else {
+    re = __ffma2_rn(Y, WY, __fmul2_rn(X, WX));   // X WX + Y WY
+    im = __ffma2_rn(X, nwy, __fmul2_rn(Y, WX));  // Y WX - X WY
+  }
+  X = re;
+  Y = im;
+}
+
+// One stage's GEMM over all rows of the CTA.  Warp w takes n-tiles
+// nt = 8 q + w of every row (q < NT / 8), so a tile's row and first
+// butterfly are compile-time functions of the unrolled step.  Epilogue:
+// epi(row, b, k, X, Y) with X / Y the real / imaginary parts of output k of
+// butterflies b and b + 1.
 template <int L, int S, int PREC, bool INV, typename Epi>
 __device__ __forceinline__ void stage_gemm(uint16_t* in, const uint32_t* __restrict__ frags, Epi&& epi) {
   using St = Stage<L, kTcE, S>;
@@ -164,8 +196,11 @@ __device__ __forceinline__ void stage_gemm(uint16_t* in, const uint32_t* __restr
   static_assert(R == 16 || R == 8, "tensor-core stages need radix 8 or 16");
   static_assert(M >= 8 || M == 1, "operand tiles need M >= 8 or M = 1");
   constexpr int NT = L / R / 8;   // n-tiles (8 butterflies) per row
+  constexpr int Q = NT / 8;       // n-tiles per warp and row
+  static_assert(NT % 8 == 0, "every warp takes the same number of tiles");
   constexpr int T2 = 2 * R / 16;  // m-tiles = k-steps of the real block
   constexpr bool TRANS = M >= 8;
+  constexpr int kRows = rows_of<L>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, tig = lane & 3;
   const uint32_t* fp = frags + (R == 16 ? 0 : frag_words(16)) + (INV ? frag_words(R) / 2 : 0);
@@ -180,8 +215,9 @@ __device__ __forceinline__ void stage_gemm(uint16_t* in, const uint32_t* __restr
   // R = 8: re j 0-7, im j 0-7), row rr = lane % 8 (element j0 + rr, or butterfly b0 + rr when M = 1)
   const int m = (lane >> 3) & (R == 16 ? 3 : 1), rr = lane & 7;
   const int im = R == 16 ? (m >> 1) : m, j0 = R == 16 ? (m & 1) * 8 : 0;
-  for (int unit = warp; unit < kRows * NT; unit += kThreads / 32) {
-    const int row = unit / NT, b0 = (unit - row * NT) * 8;
+#pragma unroll(unroll_of<L>())
+  for (int i = 0; i < kRows * Q; ++i) {
+    const int row = i / Q, b0 = 64 * (i % Q) + 8 * warp;
     const int p = TRANS ? pos_of<L, S>(b0, j0 + rr) : pos_of<L, S>(b0 + rr, j0);
     const uint16_t* src = plane(in, L, row, im) + swz(p);
     uint32_t bf[4];
@@ -197,17 +233,18 @@ __device__ __forceinline__ void stage_gemm(uint16_t* in, const uint32_t* __restr
     const int bi = b0 + 2 * tig;
     if constexpr (R == 16) {
       // tile 0: re of elements 0..15, tile 1: im; rows g and g + 8, columns bi, bi + 1
-      epi(row, bi, g, make_float2(c[0][0], c[1][0]), make_float2(c[0][1], c[1][1]));
-      epi(row, bi, g + 8, make_float2(c[0][2], c[1][2]), make_float2(c[0][3], c[1][3]));
+      epi(row, bi, g, make_float2(c[0][0], c[0][1]), make_float2(c[1][0], c[1][1]));
+      epi(row, bi, g + 8, make_float2(c[0][2], c[0][3]), make_float2(c[1][2], c[1][3]));
     } else {
       // one tile: row g = re of element g, row g + 8 = im of element g
-      epi(row, bi, g, make_float2(c[0][0], c[0][2]), make_float2(c[0][1], c[0][3]));
+      epi(row, bi, g, make_float2(c[0][0], c[0][1]), make_float2(c[0][2], c[0][3]));
     }
   }
 }
 
 // Forward stages S.. of the network; returns the buffer holding the last
-// stage's positions after the spectrum multiply.
+// stage's positions after the spectrum multiply.  Twiddle tables hold, per
+// (k, even n), the float4 (Re W_n, Re W_n+1, Im W_n, Im W_n+1).
 template <int L, int S, int PREC>
 __device__ __forceinline__ uint16_t* forward(uint16_t* cur, uint16_t* oth, const uint32_t* frags,
                                              const float2* __restrict__ tw, const float2* __restrict__ Hpos) {
@@ -216,27 +253,36 @@ __device__ __forceinline__ uint16_t* forward(uint16_t* cur, uint16_t* oth, const
   if constexpr (S + 1 < NS) {
     static_assert(St::M >= 2, "twiddled stages pair adjacent butterflies");
     const float2* t = tw + tw_offset<L>(S);
-    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 v0, float2 v1) {
+    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 X, float2 Y) {
       const float4 w = __ldg(reinterpret_cast<const float4*>(t + k * St::M + b % St::M));
-      put_pair<L, PREC>(oth, row, pos_of<L, S>(b, k), cmul(v0, make_float2(w.x, w.y)),
-                        cmul(v1, make_float2(w.z, w.w)));
+      cmul_pair<false>(X, Y, make_float2(w.x, w.y), make_float2(w.z, w.w));
+      put_pair<L, PREC>(oth, row, pos_of<L, S>(b, k), X, Y);
     });
     __syncthreads();
     return forward<L, S + 1, PREC>(oth, cur, frags, tw, Hpos);
   } else {
     static_assert(St::M == 1, "the last stage has unit stride");
-    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 v0, float2 v1) {
+    stage_gemm<L, S, PREC, false>(cur, frags, [&](int row, int b, int k, float2 X, float2 Y) {
       const int p0 = b * St::R + k, p1 = p0 + St::R;
-      put_one<L, PREC>(oth, row, p0, cmul(v0, __ldg(Hpos + p0)));
-      put_one<L, PREC>(oth, row, p1, cmul(v1, __ldg(Hpos + p1)));
+      put_one<L, PREC>(oth, row, p0, cmul(make_float2(X.x, Y.x), __ldg(Hpos + p0)));
+      put_one<L, PREC>(oth, row, p1, cmul(make_float2(X.y, Y.y), __ldg(Hpos + p1)));
     });
     __syncthreads();
     return oth;
   }
 }
 
-// Inverse stages S..0; the last one hands (row, position, value, value at
-// position + 1) to `out` (natural, even positions).
+// Twiddle W of stage S at position p (any parity), from the paired table.
+template <int L, int S>
+__device__ __forceinline__ float2 twiddle_at(const float2* __restrict__ t, int p) {
+  using St = Stage<L, kTcE, S>;
+  const int idx = ((p % St::MP) / St::M) * St::M + p % St::M;
+  const float4 w = __ldg(reinterpret_cast<const float4*>(t + (idx & ~1)));
+  return (idx & 1) ? make_float2(w.y, w.w) : make_float2(w.x, w.z);
+}
+
+// Inverse stages S..0; the last one hands (row, position p, X, Y) for the
+// natural, even position p and p + 1 to `out`.
 template <int L, int S, int PREC, typename Out>
 __device__ __forceinline__ void inverse(uint16_t* cur, uint16_t* oth, const uint32_t* frags,
                                         const float2* __restrict__ tw, Out&& out) {
@@ -244,32 +290,34 @@ __device__ __forceinline__ void inverse(uint16_t* cur, uint16_t* oth, const uint
   if constexpr (S > 0) {
     using Sp = Stage<L, kTcE, S - 1>;
     const float2* t = tw + tw_offset<L>(S - 1);
-    stage_gemm<L, S, PREC, true>(cur, frags, [&](int row, int b, int j, float2 v0, float2 v1) {
+    stage_gemm<L, S, PREC, true>(cur, frags, [&](int row, int b, int j, float2 X, float2 Y) {
       if constexpr (St::M >= 2) {
         // positions p, p + 1 of stage S - 1: n = p mod M, k = (p mod M') / M there
         const int p = pos_of<L, S>(b, j);
         const int n = p % Sp::M, k = (p % Sp::MP) / Sp::M;
         const float4 w = __ldg(reinterpret_cast<const float4*>(t + k * Sp::M + n));
-        put_pair<L, PREC>(oth, row, p, cmulc(v0, make_float2(w.x, w.y)), cmulc(v1, make_float2(w.z, w.w)));
+        cmul_pair<true>(X, Y, make_float2(w.x, w.y), make_float2(w.z, w.w));
+        put_pair<L, PREC>(oth, row, p, X, Y);
       } else {
         const int p0 = b * St::R + j, p1 = p0 + St::R;
-        put_one<L, PREC>(oth, row, p0, cmulc(v0, __ldg(t + ((p0 % Sp::MP) / Sp::M) * Sp::M + p0 % Sp::M)));
-        put_one<L, PREC>(oth, row, p1, cmulc(v1, __ldg(t + ((p1 % Sp::MP) / Sp::M) * Sp::M + p1 % Sp::M)));
+        put_one<L, PREC>(oth, row, p0, cmulc(make_float2(X.x, Y.x), twiddle_at<L, S - 1>(t, p0)));
+        put_one<L, PREC>(oth, row, p1, cmulc(make_float2(X.y, Y.y), twiddle_at<L, S - 1>(t, p1)));
       }
     });
     __syncthreads();
     inverse<L, S - 1, PREC>(oth, cur, frags, tw, out);
   } else {
     static_assert(St::M >= 2, "the first stage pairs adjacent positions");
-    stage_gemm<L, 0, PREC, true>(cur, frags, [&](int row, int b, int j, float2 v0, float2 v1) {
-      out(row, pos_of<L, 0>(b, j), v0, v1);
+    stage_gemm<L, 0, PREC, true>(cur, frags, [&](int row, int b, int j, float2 X, float2 Y) {
+      out(row, pos_of<L, 0>(b, j), X, Y);
     });
   }
 }
 
 template <int L, int KIND, int PREC>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, ctas_of<L>())
 k_pass_tc(const __grid_constant__ PassBatch pb, const float2* __restrict__ tw, const uint32_t* __restrict__ frags) {
+  constexpr int kRows = rows_of<L>();
   extern __shared__ __align__(16) uint16_t sm[];
   constexpr int BUF = TcShape<L>::BUF;
   uint16_t* buf0 = sm;
@@ -317,7 +365,7 @@ k_pass_tc(const __grid_constant__ PassBatch pb, const float2* __restrict__ tw, c
         if (p < d.n0) v0 = load(row, p);
         if (p + 1 < d.n0) v1 = load(row, p + 1);
       }
-      put_pair<L, PREC>(buf0, r, p, make_float2(v0.x * s0, v0.y * s0), make_float2(v1.x * s0, v1.y * s0));
+      put_pair<L, PREC>(buf0, r, p, make_float2(v0.x * s0, v1.x * s0), make_float2(v0.y * s0, v1.y * s0));
     }
   }
   __syncthreads();
@@ -347,9 +395,9 @@ k_pass_tc(const __grid_constant__ PassBatch pb, const float2* __restrict__ tw, c
       if (d.phase) d.phase[o] = phase_of(u);
     }
   };
-  inverse<L, stage_count(L, kTcE) - 1, PREC>(spec, other, frags, tw, [&](int r, int p, float2 v0, float2 v1) {
-    if (p < n1) emit(r, p, v0);
-    if (p + 1 < n1) emit(r, p + 1, v1);
+  inverse<L, stage_count(L, kTcE) - 1, PREC>(spec, other, frags, tw, [&](int r, int p, float2 X, float2 Y) {
+    if (p < n1) emit(r, p, make_float2(X.x, Y.x));
+    if (p + 1 < n1) emit(r, p + 1, make_float2(X.y, Y.y));
   });
   if (!staged) return;
   __syncthreads();
@@ -411,19 +459,22 @@ __global__ void k_tc_frags(uint32_t* out) {
   }
 }
 
-// Twiddle tables of one length ([k][n] = W_{M'}^{n k} per stage with M > 1),
-// double-precision sincospi rounded to float; one thread per entry.
+// Twiddle tables of one length: per stage with M > 1, entry k M + n (n even)
+// and its successor hold the float4 (Re W_n, Re W_n+1, Im W_n, Im W_n+1) of
+// W_n = W_{M'}^{n k}; double-precision sincospi rounded to float, one thread
+// per (k, even n).
 template <int L>
 __global__ void k_tc_twiddles(float2* tab) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (i >= tw_entries<L>()) return;
   int s = 0;
   while (tw_offset<L>(s + 1) <= i) ++s;
   const int MP = stage_mprev(L, kTcE, s), R = stage_radix(L, kTcE, s), M = MP / R;
   const int local = i - tw_offset<L>(s), k = local / M, n = local - k * M;
-  double sn, cs;
-  sincospi(-2.0 * (double)(((long long)n * k) % MP) / (double)MP, &sn, &cs);
-  tab[i] = make_float2((float)cs, (float)sn);
+  double s0, c0, s1, c1;
+  sincospi(-2.0 * (double)(((long long)n * k) % MP) / (double)MP, &s0, &c0);
+  sincospi(-2.0 * (double)(((long long)(n + 1) * k) % MP) / (double)MP, &s1, &c1);
+  reinterpret_cast<float4*>(tab)[i / 2] = make_float4((float)c0, (float)c1, (float)s0, (float)s1);
 }
 
 // Kernel spectrum from register order (FP32 network) to position order,
@@ -466,7 +517,7 @@ cudaError_t launch_tc_t(PassKind kind, const PassBatch& b, int grid_x, const uin
 // The spectrum is converted from the FP32 network's register order, so both
 // networks must share their radix plan.
 bool tc_length_supported(int L) { return kE == kTcE && (L == 2048 || L == 4096); }
-int tc_rows_per_cta() { return tc::kRows; }
+int tc_rows_per_cta(int L) { return L == 4096 ? tc::rows_of<4096>() : tc::rows_of<2048>(); }
 // A fragments, then the twiddle tables of 2048 and 4096 (float2)
 size_t tc_frag_words() {
   return (size_t)tc::frag_words(16) + tc::frag_words(8) + 2 * (tc::tw_entries<2048>() + tc::tw_entries<4096>());
@@ -478,8 +529,8 @@ cudaError_t launch_tc_frags(uint32_t* out, int prec, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   float2* tw = reinterpret_cast<float2*>(out + tc::frag_words(16) + tc::frag_words(8));
-  tc::k_tc_twiddles<2048><<<(tc::tw_entries<2048>() + 255) / 256, 256, 0, s>>>(tw);
-  tc::k_tc_twiddles<4096><<<(tc::tw_entries<4096>() + 255) / 256, 256, 0, s>>>(tw + tc::tw_entries<2048>());
+  tc::k_tc_twiddles<2048><<<(tc::tw_entries<2048>() / 2 + 255) / 256, 256, 0, s>>>(tw);
+  tc::k_tc_twiddles<4096><<<(tc::tw_entries<4096>() / 2 + 255) / 256, 256, 0, s>>>(tw + tc::tw_entries<2048>());
   return cudaGetLastError();
 }
 
