@@ -58,6 +58,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest x over all ranks of the default process group (x itself for one rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(views_per_rank_step, steps, world, total_ms):
+    """Whole-job throughput: every rank's views over the slowest rank's time (views/s)."""
+    return world * views_per_rank_step * steps / (total_ms * 1e-3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -71,7 +87,7 @@ def source_hash():
     traffic figures are only used while it matches the captured version."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1001_4309_gb300", "csrc")
-    files = [os.path.join(csrc, n) for n in ("sf_fft.cuh", "sf_kernels.cuh", "sf_internal.h", "sf_launch.cu")]
+    files = [os.path.join(csrc, n) for n in ("sf_fft.cuh", "sf_kernels.cuh", "sf_pass.h")]
     for p in sorted(files + glob.glob(os.path.join(csrc, "sf_inst_*.cu"))):
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
@@ -234,13 +250,9 @@ def run_ours(a):
     P.shifted_fresnel_set_profile_events(sf.handle, None)
     x_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(n_prof)]
     y_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(n_prof)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / a.steps
-    value = world * V * a.steps / (total_ms * 1e-3)
+    value = job_value(V, a.steps, world, total_ms)
 
     # roofline of the dominant kernel (the longer pass; within 2 % the two
     # passes tie and the y pass, which moves more bytes, is reported), from
@@ -277,12 +289,8 @@ def run_ours(a):
     for _ in range(a.steps):
         P.shifted_fresnel_execute(sf.handle, h_host.data_ptr(), [o.data_ptr() for o in o_host], stream=sptr)
         stream.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": round(world * V * a.steps / e2e_s, 1), "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": round(job_value(V, a.steps, world, e2e_s * 1e3), 1), "unit": UNIT,
            "h2d_bytes_per_step": int(h_host.numel() * 4),
            "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in o_host)),
            "path": "shifted_fresnel_execute with pinned host buffers (library-staged copies), stream sync per step"}

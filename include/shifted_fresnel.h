@@ -116,10 +116,10 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
  * Each of holo and the output buffers may be device memory or host memory
  * (pinned or pageable).  Host buffers are staged through plan-owned device
  * buffers that the first call with a host buffer allocates.  With host
- * outputs the y passes run one view at a time and each view's copies to the
- * host start on a plan-owned copy stream as soon as that view is done,
- * overlapping the rest of the computation; the caller's stream waits for the
- * last copy, so the caller synchronises its stream before reading host
+ * outputs the views run one at a time (x pass, then y pass) and each view's
+ * copies to the host start on a plan-owned copy stream as soon as that view
+ * is done, overlapping the following views; the caller's stream waits for
+ * the last copy, so the caller synchronises its stream before reading host
  * outputs.  Every view needs at least one non-NULL output.
  * With device outputs and two or more views, the views are split into two
  * halves of about equal work run on `stream` and on a plan-owned second

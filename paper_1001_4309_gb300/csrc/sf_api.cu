@@ -989,9 +989,9 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
     if (rc) return rc;
   }
 
-  // x passes then y passes, each grouped by FFT length.  With host outputs the
-  // y passes run one view per launch and each view's copies start on the copy
-  // stream as soon as its pass is done, overlapping the remaining compute.
+  // Device outputs: x passes then y passes, each grouped by FFT length (on
+  // two streams, see below).  Host outputs: one view at a time, with its
+  // copies to the host overlapping the following views' passes.
   const bool overlap = !d2h.empty();
   std::vector<float2*> work(nv);
   for (int i = 0; i < nv; ++i) work[i] = plan->views[i].work;
@@ -1037,24 +1037,35 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
     return SF_OK;
   }
 
-  if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);
-  for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
-    if (axis == 1 && plan->prof[1]) e = cudaEventRecord(plan->prof[1], s);
-    auto after = [&](const int* views, int n) -> cudaError_t {
-      cudaError_t r = cudaSuccess;
-      if (!(overlap && axis == 1)) return r;
+  if (overlap) {
+    // Host outputs: view by view (x pass, y pass), each view's copies to the
+    // host starting on the copy stream as soon as its y pass is done, so the
+    // copies (the bound of this path) start after the first view instead of
+    // after every view's x pass.
+    auto none = [](const int*, int) { return cudaSuccess; };
+    auto copies = [&](const int* views, int) -> cudaError_t {
       const int vi = views[0];
-      r = cudaEventRecord(plan->view_done[vi], s);
+      cudaError_t r = cudaEventRecord(plan->view_done[vi], s);
       if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, plan->view_done[vi], 0);
       for (const Copy& c : d2h)
         if (r == cudaSuccess && c.view == vi)
           r = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
-      (void)n;
       return r;
     };
-    if (e == cudaSuccess)
-      e = launch_axis(plan, axis, src, work.data(), dout.data(), dint.data(), dph.data(),
-                      (overlap && axis == 1) ? 1 : kMaxPassBatch, s, after);
+    for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+      const std::vector<int> one{vi};
+      e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, none, &one);
+      if (e == cudaSuccess)
+        e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, copies, &one);
+    }
+  } else {
+    if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);
+    auto none = [](const int*, int) { return cudaSuccess; };
+    for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
+      if (axis == 1 && plan->prof[1]) e = cudaEventRecord(plan->prof[1], s);
+      if (e == cudaSuccess)
+        e = launch_axis(plan, axis, src, work.data(), dout.data(), dint.data(), dph.data(), kMaxPassBatch, s, none);
+    }
   }
   if (e == cudaSuccess && plan->prof[2]) e = cudaEventRecord(plan->prof[2], s);
   if (overlap && e == cudaSuccess) {

@@ -7,52 +7,9 @@
 #include <algorithm>
 
 #include "shifted_fresnel.h"
+#include "sf_pass.h"
 
 namespace sf {
-
-constexpr int kMaxPassBatch = 16;  // (view, axis) passes per launch
-#ifndef SF_FFT_E
-#define SF_FFT_E 16
-#endif
-constexpr int kE = SF_FFT_E;       // complex values per thread in the FP32 FFT network
-constexpr int kTcE = 16;           // radix of the tensor-core network's stages
-
-enum PassKind : int { PASS_X_REAL = 0, PASS_X_CPLX = 1, PASS_Y = 2 };
-
-// Supported FFT lengths: powers of two (radix-16 network) and 3 x powers of
-// two / 9 x 256 (radix-24 first stage), ascending.
-constexpr int kNumFftLengths = 13;
-constexpr int kFftLengths[kNumFftLengths] = {64, 128, 256, 512, 1024, 1536, 2048, 2304, 3072, 4096, 4608, 6144, 8192};
-template <int L>
-constexpr int fft_length_slot_of() {
-  int i = 0;
-  while (i < kNumFftLengths && kFftLengths[i] != L) ++i;
-  return i;
-}
-
-// One separable half of one view (Section 2.2, steps 2-9 along one axis).
-// Row r is read from src[r * src_ld + p] (p < n0); output p of row r goes to
-// dst[p * dst_ld + r] (p < n1).
-//   X pass: src = hologram [rows = ny0][src_ld = nx0], dst = workspace [nx1][dst_ld = ny0]
-//   Y pass: src = workspace [rows = nx1][src_ld = ny0], dst = view [ny1][dst_ld = nx1]
-struct PassDesc {
-  const void* src;
-  float2* dst;        // complex output (Y: may be null)
-  float* inten;       // Y only, may be null
-  float* phase;       // Y only, may be null
-  const float2* cin;  // input chirp, n0 entries
-  const float2* cout; // output chirp (with 1/L and, on Y, the constant of Eq. 2), n1 entries
-  const float2* H;    // kernel spectrum in register order, L entries
-  int n0, n1;         // convolution input / output lengths along this axis
-  int rows;           // independent rows of this pass
-  int src_ld, dst_ld;
-  int accumulate;     // Y only: add into dst instead of overwriting it
-};
-
-struct PassBatch {
-  PassDesc d[kMaxPassBatch];
-  int count;
-};
 
 // Per-axis phase polynomials in units of pi, as 64-bit fixed point (2^63 = pi).
 struct AxisCoef {
