@@ -128,11 +128,11 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
  * SF_EXECUTE_SINGLE_STREAM=1, or profiling events set with
  * shifted_fresnel_set_profile_events, keeps everything on `stream`.
  * Implementation: each pass runs a one-tile-per-CTA kernel, or, where the
- * plan chose it (SF_PASS_IMPL=tma or the autotuner, see
- * shifted_fresnel_fft_length) and the rows' address, stride and length are
- * multiples of 16 bytes (FFT length 256 .. 4096), a persistent kernel that
- * prefetches the next rows with bulk copies while transforming the current
- * ones.
+ * plan chose it (by default at FFT length 4096; SF_PASS_IMPL or the
+ * autotuner, see shifted_fresnel_fft_length) and the rows' address, stride
+ * and length are multiples of 16 bytes (FFT length 256 .. 4096), a
+ * persistent kernel that prefetches the next rows with bulk copies while
+ * transforming the current ones.
  * Errors: SF_ERR_INVALID_ARG, SF_ERR_DEVICE_MISMATCH, SF_ERR_OOM, SF_ERR_CUDA.
  */
 int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out,
@@ -320,7 +320,9 @@ uint64_t shifted_fresnel_kernel_launches(void);
  *
  * Plan-time choices (environment, read by shifted_fresnel_plan):
  *   SF_FFT_LENGTHS=pow2   powers of two only.
- *   SF_PASS_IMPL=tma      persistent row-pass kernel for every eligible pass.
+ *   SF_PASS_IMPL=grid|tma one-tile-per-CTA row-pass kernel everywhere, or the
+ *                         persistent one for every eligible pass (default:
+ *                         persistent at 4096 only).
  *   SF_AUTOTUNE=1         measure instead: per axis the cheaper of the two
  *                         candidate lengths (next power of two, next length
  *                         with a factor 3), per (length, pass kind) the

@@ -23,6 +23,12 @@
 namespace sf {
 namespace {
 
+// Row tiles of the batch kernel: the pass kernel's tile shape, capped at the
+// batch CTA size.
+constexpr int batch_cta(int L) { return pass_cta_target(L) < kBatchThreads ? pass_cta_target(L) : kBatchThreads; }
+template <int L>
+using BatchShape = PassShape<L, batch_cta(L)>;
+
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -34,9 +40,10 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 // and a separate function keeps that spill code out of the power-of-two paths.
 template <int LL, int KIND_X>
 __device__ __noinline__ void mixed_tile(const PassDesc& d, int phase, int tile, float2* smem, const float4* tw) {
-  constexpr bool spare = PassShape<LL>::THREADS < kBatchThreads;
-  if (phase == 0) row_tile<LL, KIND_X, false, spare>(d, tile * PassShape<LL>::G, smem, tw);
-  else row_tile<LL, PASS_Y, true, spare>(d, tile * PassShape<LL>::G, smem, tw);
+  using Sh = BatchShape<LL>;
+  constexpr bool spare = Sh::THREADS < kBatchThreads;
+  if (phase == 0) row_tile<LL, KIND_X, false, spare, batch_cta(LL)>(d, tile * Sh::G, smem, tw);
+  else row_tile<LL, PASS_Y, true, spare, batch_cta(LL)>(d, tile * Sh::G, smem, tw);
 }
 
 template <int KIND_X>
@@ -44,16 +51,16 @@ __device__ __forceinline__ void run_item(const PassDesc& d, int phase, int L, in
                                          const float4* const* tw) {
   // a tile of G T <= kBatchThreads threads; the rest of the CTA idles through it
 #define SF_BATCH_CASE(LL)                                                                              \
-  static_assert(PassShape<LL>::THREADS <= kBatchThreads, "batch tiles must fit the batch CTA");        \
+  static_assert(BatchShape<LL>::THREADS <= kBatchThreads, "batch tiles must fit the batch CTA");       \
   case LL: {                                                                                           \
-    constexpr bool spare = PassShape<LL>::THREADS < kBatchThreads;                                     \
+    constexpr bool spare = BatchShape<LL>::THREADS < kBatchThreads;                                    \
     const float4* t = tw[fft_length_slot_of<LL>()];                                                    \
-    if (phase == 0) row_tile<LL, KIND_X, false, spare>(d, tile * PassShape<LL>::G, smem, t);           \
-    else row_tile<LL, PASS_Y, true, spare>(d, tile * PassShape<LL>::G, smem, t);                       \
+    if (phase == 0) row_tile<LL, KIND_X, false, spare, batch_cta(LL)>(d, tile * BatchShape<LL>::G, smem, t); \
+    else row_tile<LL, PASS_Y, true, spare, batch_cta(LL)>(d, tile * BatchShape<LL>::G, smem, t);     \
     break;                                                                                             \
   }
 #define SF_BATCH_MIXED_CASE(LL)                                                                        \
-  static_assert(PassShape<LL>::THREADS <= kBatchThreads, "batch tiles must fit the batch CTA");        \
+  static_assert(BatchShape<LL>::THREADS <= kBatchThreads, "batch tiles must fit the batch CTA");       \
   case LL: mixed_tile<LL, KIND_X>(d, phase, tile, smem, tw[fft_length_slot_of<LL>()]); break;
   switch (L) {
     SF_BATCH_CASE(64)
@@ -151,7 +158,7 @@ bool batch_length_supported(int L) { return fft_length_supported(L) && L <= 6144
 
 int batch_tile_rows(int L) {
   switch (L) {
-#define SF_BATCH_ROWS(LL) case LL: return PassShape<LL>::G;
+#define SF_BATCH_ROWS(LL) case LL: return BatchShape<LL>::G;
     SF_BATCH_ROWS(64) SF_BATCH_ROWS(128) SF_BATCH_ROWS(256) SF_BATCH_ROWS(512) SF_BATCH_ROWS(1024)
     SF_BATCH_ROWS(1536) SF_BATCH_ROWS(2048) SF_BATCH_ROWS(2304) SF_BATCH_ROWS(3072) SF_BATCH_ROWS(4096)
     SF_BATCH_ROWS(4608) SF_BATCH_ROWS(6144)
@@ -169,9 +176,9 @@ int batch_item_tiles(int L) {
 
 size_t batch_smem_bytes() {
   size_t m = 0;
-  for (size_t b : {PassShape<64>::SMEM, PassShape<128>::SMEM, PassShape<256>::SMEM, PassShape<512>::SMEM,
-                   PassShape<1024>::SMEM, PassShape<1536>::SMEM, PassShape<2048>::SMEM, PassShape<2304>::SMEM,
-                   PassShape<3072>::SMEM, PassShape<4096>::SMEM, PassShape<4608>::SMEM, PassShape<6144>::SMEM})
+  for (size_t b : {BatchShape<64>::SMEM, BatchShape<128>::SMEM, BatchShape<256>::SMEM, BatchShape<512>::SMEM,
+                   BatchShape<1024>::SMEM, BatchShape<1536>::SMEM, BatchShape<2048>::SMEM, BatchShape<2304>::SMEM,
+                   BatchShape<3072>::SMEM, BatchShape<4096>::SMEM, BatchShape<4608>::SMEM, BatchShape<6144>::SMEM})
     m = std::max(m, b);
   return m;
 }

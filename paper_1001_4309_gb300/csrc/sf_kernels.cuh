@@ -36,15 +36,20 @@ namespace sf {
 // complex values per thread of the FFT network of length L
 constexpr int fft_e(int L) { return is_pow2(L) ? kE : 24; }
 
-// Powers of two: CTAs of up to 256 threads, registers for 16 warps per SM
-// (128 per thread).  Lengths with a factor 3 hold 24 values per thread: CTAs
-// of up to 192 threads, registers for 12 warps per SM (up to 168 per thread).
-template <int L>
+// CTA size a row pass aims for: 256 threads for powers of two (512 at 4096,
+// where a 256-thread CTA holds a single row and two rows per CTA measured 9 %
+// faster per row), 192 for the lengths with a factor 3 (24 values per thread).
+constexpr int pass_cta_target(int L) {
+  return !is_pow2(L) ? 192 : (L == 4096 ? 2 * SF_PASS_CTA_THREADS : SF_PASS_CTA_THREADS);
+}
+
+// G rows of T = L / E threads per CTA.  Registers: powers of two for 16 warps
+// per SM (128 per thread), the lengths with a factor 3 for 12 (up to 168).
+template <int L, int CTA = pass_cta_target(L)>
 struct PassShape {
   static constexpr int T = L / fft_e(L);
-  static constexpr int CTA_TARGET = is_pow2(L) ? SF_PASS_CTA_THREADS : 192;
   static constexpr int MIN_WARPS = is_pow2(L) ? SF_PASS_MIN_WARPS : 12;
-  static constexpr int G = (CTA_TARGET / T) > 0 ? (CTA_TARGET / T) : 1;
+  static constexpr int G = (CTA / T) > 0 ? (CTA / T) : 1;
   static constexpr int THREADS = G * T;
   // CTAs per SM the register budget is set for
   static constexpr int MIN_BLOCKS = MIN_WARPS / (THREADS / 32) > 0 ? MIN_WARPS / (THREADS / 32) : 1;
@@ -110,10 +115,10 @@ struct StagedSrc {
 // of the tile leave as G-element contiguous runs.  With SPARE, the CTA may
 // have more threads than the tile's G T (a CTA sized for another length):
 // those only join the CTA barriers and the final store loop.
-template <int L, int KIND, typename Src, bool SPARE = false>
+template <int L, int KIND, typename Src, bool SPARE = false, int CTA = pass_cta_target(L)>
 __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw,
                                              const Src& src) {
-  using Sh = PassShape<L>;
+  using Sh = PassShape<L, CTA>;
   constexpr int T = Sh::T, G = Sh::G, E = fft_e(L);
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   const int row = row0 + g;
@@ -171,9 +176,9 @@ __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2
   }
 }
 
-template <int L, int KIND, bool COHERENT, bool SPARE = false>
+template <int L, int KIND, bool COHERENT, bool SPARE = false, int CTA = pass_cta_target(L)>
 __device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw) {
-  row_tile_src<L, KIND, GlobalSrc<KIND, COHERENT>, SPARE>(d, row0, smem, tw, GlobalSrc<KIND, COHERENT>{d});
+  row_tile_src<L, KIND, GlobalSrc<KIND, COHERENT>, SPARE, CTA>(d, row0, smem, tw, GlobalSrc<KIND, COHERENT>{d});
 }
 
 // Row pass: tile blockIdx.x of pass blockIdx.y.

@@ -230,3 +230,19 @@ def test_plain_cufft_comparison_path_matches_oracle(P):
             assert rel_l2(o.cpu().numpy(), oracle.forward(holo, v)) <= TOL
     finally:
         pp.close()
+
+
+@pytest.mark.parametrize("n0,n1", [(1024, 1024), (2048, 2048), (1500, 1200)])
+def test_row_pass_kernels_agree(P, n0, n1, monkeypatch):
+    """The one-tile-per-CTA and the persistent (bulk-copy prefetch) row passes give identical views."""
+    ny0, ny1 = 24, 20
+    v = view(WAVELENGTH, 0.045, PITCH, 1.9e-6, o1=(1e-4, 2e-5), n0=(n0, ny0), n1=(n1, ny1))
+    holo = random_field(ny0, n0, seed=n0 + 11).real
+    res = {}
+    for impl in ("grid", "tma"):
+        monkeypatch.setenv("SF_PASS_IMPL", impl)
+        res[impl] = run(P, [v], holo, intensity=False, phase=False)["field"][0]
+    assert np.array_equal(res["grid"], res["tma"])
+    for cols in sample_columns(n1):
+        check_view({"field": [res["tma"][:, cols[0]:cols[1]]], "intensity": [None], "phase": [None]}, 0,
+                   oracle.forward(holo, v, cols=cols))
