@@ -75,7 +75,7 @@ struct sf_plan_s {
   std::vector<ViewState> views;
   std::map<int, float4*> tw;  // per-stage twiddle tables per FFT length
   int precision = SF_PREC_FP32;
-  uint32_t* tc_frags = nullptr;  // per-lane DFT fragments of the tensor-core pass
+  uint32_t* tc_frags = nullptr;  // per-lane DFT fragments and twiddle tables of the tensor-core pass
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
   int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA
   int sms = 0;
@@ -580,7 +580,7 @@ cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* 
     if (plan->tc_frags && tc_length_supported(L)) {
       for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[batch_view[k]].hpos[axis];
       const int G = tc_rows_per_cta(L);
-      e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tw[L], plan->tc_frags, s);
+      e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tc_frags, s);
     } else if (persistent_eligible(plan, L, kind, b)) {
       e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);
     } else {
@@ -852,7 +852,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       off_hpos[2 * i + a] = (precision != SF_PREC_FP32 && tc_length_supported(vs.ax[a].L))
                                 ? ar.take(sizeof(float2) * vs.ax[a].L) : SIZE_MAX;
   }
-  const size_t off_frags = precision != SF_PREC_FP32 ? ar.take(sizeof(uint32_t) * tc_frag_words()) : SIZE_MAX;
+  const size_t off_frags = precision != SF_PREC_FP32 ? ar.take(sizeof(uint32_t) * tc_table_words()) : SIZE_MAX;
   const size_t off_err = ar.take(sizeof(int));
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
   if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
@@ -910,8 +910,8 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
   if (off_frags != SIZE_MAX && e == cudaSuccess) {
     p->tc_frags = reinterpret_cast<uint32_t*>(base + off_frags);
-    e = launch_tc_frags(p->tc_frags, precision, s);
-    ++g_launches;
+    e = launch_tc_tables(p->tc_frags, precision, s);
+    g_launches += 3;  // fragments and the twiddle tables of both lengths
     for (ViewState& vs : p->views)
       for (int a = 0; a < 2 && e == cudaSuccess; ++a)
         if (vs.hpos[a]) {

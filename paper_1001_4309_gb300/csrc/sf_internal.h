@@ -72,11 +72,11 @@ cudaError_t launch_pass_persistent(int L, PassKind kind, const PassBatch& b, con
 // Mixed-precision row pass (sf_tc.cu)
 bool tc_length_supported(int L);
 int tc_rows_per_cta(int L);
-size_t tc_frag_words();
-cudaError_t launch_tc_frags(uint32_t* out, int prec, cudaStream_t s);
+size_t tc_table_words();  // DFT fragments and twiddle tables of the tensor-core pass (32-bit words)
+cudaError_t launch_tc_tables(uint32_t* out, int prec, cudaStream_t s);
 cudaError_t launch_hpos(int L, const float2* Hreg, float2* Hpos, cudaStream_t s);
-cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, int grid_x, const float4* tw,
-                           const uint32_t* frags, cudaStream_t s);
+cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, int grid_x, const uint32_t* tables,
+                           cudaStream_t s);
 
 // host helpers shared by the entry points (defined in sf_api.cu)
 int validate_view(const sf_view& v);
@@ -119,8 +119,6 @@ cudaError_t launch_chirps(const AxisCoef* axes_dev, int n_axes, int max_n, cudaS
 size_t twiddle_entries(int L);
 void build_twiddles(int L, float4* host_table);
 int pass_rows_per_cta(int L);
-int pass_threads(int L);
-size_t pass_smem_bytes(int L);
 bool fft_length_supported(int L);
 int fft_length_slot(int L);  // index in kFftLengths, -1 if unsupported
 

@@ -60,14 +60,6 @@ int pass_rows_per_cta(int L) {
   SF_LENGTH_SWITCH(L, return PassShape<LL>::G)
   return 0;
 }
-int pass_threads(int L) {
-  SF_LENGTH_SWITCH(L, return PassShape<LL>::THREADS)
-  return 0;
-}
-size_t pass_smem_bytes(int L) {
-  SF_LENGTH_SWITCH(L, return PassShape<LL>::SMEM)
-  return 0;
-}
 
 // Input and output chirp vectors of every (view, axis): blockIdx.y = axis,
 // blockIdx.z = 0 for exp(i pi psi_in(m0)), 1 for out_scale exp(i pi psi_out(m1)).

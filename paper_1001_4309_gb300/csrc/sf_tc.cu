@@ -519,11 +519,11 @@ cudaError_t launch_tc_t(PassKind kind, const PassBatch& b, int grid_x, const uin
 bool tc_length_supported(int L) { return kE == kTcE && (L == 2048 || L == 4096); }
 int tc_rows_per_cta(int L) { return L == 4096 ? tc::rows_of<4096>() : tc::rows_of<2048>(); }
 // A fragments, then the twiddle tables of 2048 and 4096 (float2)
-size_t tc_frag_words() {
+size_t tc_table_words() {
   return (size_t)tc::frag_words(16) + tc::frag_words(8) + 2 * (tc::tw_entries<2048>() + tc::tw_entries<4096>());
 }
 
-cudaError_t launch_tc_frags(uint32_t* out, int prec, cudaStream_t s) {
+cudaError_t launch_tc_tables(uint32_t* out, int prec, cudaStream_t s) {
   if (prec == SF_PREC_BF16TC) tc::k_tc_frags<SF_PREC_BF16TC><<<1, 32, 0, s>>>(out);
   else tc::k_tc_frags<SF_PREC_FP16TC><<<1, 32, 0, s>>>(out);
   cudaError_t e = cudaGetLastError();
@@ -543,9 +543,8 @@ cudaError_t launch_hpos(int L, const float2* Hreg, float2* Hpos, cudaStream_t s)
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, int grid_x, const float4* tw,
-                           const uint32_t* frags, cudaStream_t s) {
-  (void)tw;  // the tensor-core network has its own twiddle tables (after the fragments)
+cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, int grid_x, const uint32_t* frags,
+                           cudaStream_t s) {
   if (prec == SF_PREC_BF16TC) {
     if (L == 2048) return tc::launch_tc_t<2048, SF_PREC_BF16TC>(kind, b, grid_x, frags, s);
     if (L == 4096) return tc::launch_tc_t<4096, SF_PREC_BF16TC>(kind, b, grid_x, frags, s);
