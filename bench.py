@@ -37,6 +37,37 @@ UNIT = "views/s"
 WORKLOAD = ("1024^2 float32 in-line hologram -> 4 complex64 1024^2 views "
             "(z = 3/5/7/10 cm, p1 = 4.65/2/1/0.5 um, offsets within +-1 mm), FFT length 2048 per axis")
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2, written between timed steps
+PAPER_CONTEXT = {  # the paper's own figures (Section 3), other hardware: context only, not a target
+    "gpu": "four 1024^2 views (2048^2 padded) in about 60 ms (about 67 views/s) on four GT200 chips "
+           "(2x GTX 295, CUDA 2.3, CUFFT), loop including host copies",
+    "cpu": "the same four views in 9,542 ms (about 0.42 views/s) on a Core2Quad Q6600"}
+ERROR_COLS = 8  # columns per sampled block (first, middle, last block of every view)
+
+
+def view_errors(holo_np, views, fields):
+    """Per view: relative L2 and max-abs error (relative to the largest reference magnitude) of the
+    complex field against the FP64 oracle, on three blocks of output columns (first, middle, last)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    out = []
+    for v, f in zip(views, fields):
+        n = v["nx1"]
+        w = min(ERROR_COLS, n)
+        blocks = sorted({(0, w), (n // 2 - w // 2, n // 2 - w // 2 + w), (n - w, n)})
+        num = den = 0.0
+        mx_err = mx_ref = 0.0
+        for c0, c1 in blocks:
+            r = oracle.forward(holo_np, v, cols=(c0, c1))
+            g = f[:, c0:c1].astype(np.complex128)
+            num += float(np.sum(np.abs(g - r) ** 2))
+            den += float(np.sum(np.abs(r) ** 2))
+            mx_err = max(mx_err, float(np.max(np.abs(g - r))))
+            mx_ref = max(mx_ref, float(np.max(np.abs(r))))
+        out.append({"view": f"{v['nx1']}x{v['ny1']} z={v['z']:g}", "rel_l2": float(f"{(num / den) ** 0.5:.3e}"),
+                    "max_abs_rel": float(f"{mx_err / mx_ref:.3e}"),
+                    "sample": f"columns {', '.join(f'{c0}-{c1 - 1}' for c0, c1 in blocks)}"})
+    return out
 
 
 def parse():
@@ -201,7 +232,10 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     holo_np, views = synth.config_c2()
     V = len(views)
-    sf = P.ShiftedFresnel(views, device=local)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter()
+    sf = P.ShiftedFresnel(views, device=local)  # plan creation synchronises its stream
+    plan_ms = (time.perf_counter() - t_plan) * 1e3
     lengths = [sf.sizes(i)[:2] for i in range(V)]
     holo = torch.from_numpy(holo_np).to(dev)
     outs = sf.alloc_outputs(field=True)
@@ -303,6 +337,13 @@ def run_ours(a):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(holo_np, views, a.cpu_seconds)
+    # accuracy of the timed step's views (the outputs of its last call) against the FP64 oracle
+    accuracy = None
+    if rank == 0:
+        sf.execute(holo, outs)
+        torch.cuda.synchronize()
+        accuracy = view_errors(holo_np, views, [o.cpu().numpy() for o in outs["field"]])
+    io_bytes = 4 * views[0]["nx0"] * views[0]["ny0"] + sum(8 * v["nx1"] * v["ny1"] for v in views)
 
     sf.close()
     if rank == 0:
@@ -320,6 +361,12 @@ def run_ours(a):
             "step_algorithmic_bytes": step_bytes,
             "step_nominal_tflops": round(step_flops / (ms_per_step * 1e-3) / 1e12, 2),
             "passes": passes,
+            "io_lower_bound": {"bytes_per_step": io_bytes,
+                               "hbm_frac": round(io_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak, 4),
+                               "what": "hologram read once + complex views written once"},
+            "accuracy_fp32": accuracy,
+            "plan_ms": round(plan_ms, 2),
+            "paper_context": PAPER_CONTEXT,
             "plain_path": plain,
             "batched": batched,
             "mixed_precision": mixed,
@@ -424,26 +471,20 @@ def batched_runs(holo_np, views, dev, stream, flush, hbm_peak):
     return res
 
 
-def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm_peak, fp32_value):
-    """The same 4-view step with the DFT stages on tensor cores; error vs the oracle on sampled columns."""
-    import numpy as np
+def time_precision(views, holo, prec, dev, stream, flush, steps, warmup):
+    """Mean ms of one execute of `views` at precision `prec` (L2 flushed between steps) and its fields."""
     import torch
-    import oracle
     import paper_1001_4309_gb300 as P
-    oracle.build()
-    cols = (500, 508)
-    refs = [oracle.forward(holo_np, v, cols=cols) for v in views]
-    res = {"fp32_value": round(fp32_value, 1)}
-    for name, prec in (("fp16tc", P.binding.SF_PREC_FP16TC), ("bf16tc", P.binding.SF_PREC_BF16TC)):
-        h = P.shifted_fresnel_plan(views, precision=prec, device=dev.index, stream=stream.cuda_stream)
+    h = P.shifted_fresnel_plan(views, precision=prec, device=dev.index, stream=stream.cuda_stream)
+    try:
         outs = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64, device=dev) for v in views]
         ptrs = [o.data_ptr() for o in outs]
-        for _ in range(a.warmup):
+        for _ in range(warmup):
             P.shifted_fresnel_execute(h, holo.data_ptr(), ptrs, stream=stream.cuda_stream)
             flush.zero_()
         torch.cuda.synchronize()
         ev = []
-        for _ in range(a.steps):
+        for _ in range(steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -451,18 +492,41 @@ def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm
             e1.record(stream)
             ev.append((e0, e1))
         torch.cuda.synchronize()
-        ms = sum(x.elapsed_time(y) for x, y in ev) / a.steps
-        errs = []
-        for o, r in zip(outs, refs):
-            g = o.cpu().numpy()[:, cols[0]:cols[1]].astype(np.complex128)
-            errs.append(float(np.linalg.norm(g - r) / np.linalg.norm(r)))
+        ms = sum(x.elapsed_time(y) for x, y in ev) / steps
+        return ms, [o.cpu().numpy() for o in outs]
+    finally:
         P.shifted_fresnel_destroy(h)
+
+
+def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm_peak, fp32_value):
+    """The 4-view step with the DFT stages on tensor cores, plus single 256^2 / 1024^2 / 2048^2 views
+    (the 256^2 view's FFT length 512 has no tensor-core pass and runs in FP32); per-view error vs the
+    FP64 oracle next to the FP32 path."""
+    import torch
+    import synth
+    import paper_1001_4309_gb300 as P
+    precs = (("fp32", P.binding.SF_PREC_FP32), ("fp16tc", P.binding.SF_PREC_FP16TC),
+             ("bf16tc", P.binding.SF_PREC_BF16TC))
+    res = {"fp32_value": round(fp32_value, 1)}
+    for name, prec in precs[1:]:
+        ms, fields = time_precision(views, holo, prec, dev, stream, flush, a.steps, a.warmup)
+        errs = view_errors(holo_np, views, fields)
         v = len(views) / (ms * 1e-3)
         res[name] = {"value": round(v, 1), "unit": UNIT, "ms_per_step": round(ms, 5),
                      "speedup_vs_fp32": round(v / fp32_value, 3),
                      "step_hbm_frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
-                     "rel_l2_vs_oracle_max": float(f"{max(errs):.3e}"),
-                     "rel_l2_sample": f"columns {cols[0]}-{cols[1] - 1} of each view"}
+                     "rel_l2_vs_oracle_max": max(e["rel_l2"] for e in errs), "per_view": errs}
+    singles = []
+    for h_np, vs in synth.config_c4():
+        h = torch.from_numpy(h_np).to(dev)
+        entry = {"view": f"{vs[0]['nx0']}^2 -> {vs[0]['nx1']}^2"}
+        for name, prec in precs:
+            ms, fields = time_precision(vs, h, prec, dev, stream, flush, 20, 3)
+            e = view_errors(h_np, vs, fields)[0]
+            entry[name] = {"views_per_s": round(1 / (ms * 1e-3), 1), "rel_l2": e["rel_l2"],
+                           "max_abs_rel": e["max_abs_rel"]}
+        singles.append(entry)
+    res["single_views"] = singles
     return res
 
 
