@@ -43,9 +43,9 @@ namespace tc {
 
 constexpr int kThreads = 256;  // 8 warps
 // unroll of the per-warp tile loop (measured best at 2048 within the
-// register budget of three CTAs per SM; 4096 spills when unrolled)
+// register budget of three CTAs per SM; 4096 spills beyond 2)
 template <int L>
-__host__ __device__ constexpr int unroll_of() { return L == 2048 ? 4 : 1; }
+__host__ __device__ constexpr int unroll_of() { return L == 2048 ? 4 : 2; }
 // rows per CTA: 64 KiB of half-precision buffers per CTA at either length
 template <int L>
 __host__ __device__ constexpr int rows_of() { return L == 4096 ? 2 : 4; }

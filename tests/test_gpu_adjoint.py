@@ -60,6 +60,9 @@ CASES = [
     (100, 64, 37, 100, -0.07, PITCH, 0.9e-6, (-2e-5, 1e-5), (5e-4, 3e-4), CPLX | NOPRE),
     (64, 65, 65, 64, 0.04, PITCH, 2.325e-6, (0, 0), (1e-4, -5e-5), 0),
     (256, 256, 256, 256, -0.05, PITCH, 2.325e-6, (0, 0), (100e-6, -50e-6), CPLX),
+    # FFT lengths with a factor 3: 1536 along x (1024 -> 400), 2304 along y (1500 -> 700)
+    (1024, 24, 400, 20, 0.03, PITCH, 3.1e-6, (0, 0), (1e-4, 1e-4), CPLX),
+    (16, 1500, 12, 700, -0.045, PITCH, 2.2e-6, (2e-5, 0), (-1e-4, 3e-4), CPLX | NOPRE),
 ]
 
 
