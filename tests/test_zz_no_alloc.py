@@ -37,6 +37,7 @@ def P():
 VIEW_A = view(WAVELENGTH, -0.05, PITCH, 2.325e-6, o1=(100e-6, -50e-6), n0=(256, 256), n1=(256, 256))
 VIEW_B = view(WAVELENGTH, 0.07, (PITCH, 3.1e-6), (1.0e-6, 2.2e-6), o0=(1e-5, 0), o1=(-3e-4, 2e-4),
               n0=(300, 200), n1=(500, 120), flags=8)
+VIEW_C = view(WAVELENGTH, 0.035, PITCH, 2.9e-6, o1=(1e-4, -2e-4), n0=(1024, 64), n1=(400, 64))  # FFT length 1536
 
 
 def inputs(v, seed):
@@ -85,13 +86,15 @@ def test_static_entry_matches_plan_on_consecutive_calls(P):
     compare(second, ref_b)
     third = static_path(P, VIEW_A, ha)  # after a larger view left its data in the array
     compare(third, ref_a)
+    hc = inputs(VIEW_C, 3)
+    compare(static_path(P, VIEW_C, hc), plan_path(P, VIEW_C, hc))  # a length with a factor 3
 
 
 def test_static_entry_rejects_sizes_beyond_its_scratch(P):
     import torch
     holo = torch.zeros((1, 1), dtype=torch.float32, device="cuda")
     out = torch.empty((1, 1), dtype=torch.complex64, device="cuda")
-    too_long = view(WAVELENGTH, 0.05, PITCH, PITCH, n0=(1500, 1), n1=(600, 1))  # needs FFT length 4096
+    too_long = view(WAVELENGTH, 0.05, PITCH, PITCH, n0=(1500, 1), n1=(600, 1))  # needs FFT length 2304
     assert P.shifted_fresnel_execute_static(too_long, holo.data_ptr(), out.data_ptr(), check=False) \
         == P.SF_ERR_UNSUPPORTED_SIZE
     too_big = view(WAVELENGTH, 0.05, PITCH, PITCH, n0=(8, 1100), n1=(1000, 8))  # nx1 * ny0 > 2^20
