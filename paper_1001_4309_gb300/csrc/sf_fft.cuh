@@ -134,14 +134,27 @@ __device__ __forceinline__ void dft8(float2* x) {
   x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
 }
 
-template <bool INV>
+// Radix 16 as 4 x 4.  ZIN: inputs 8..15 are known zero (the first forward
+// stage of a row with at most L/2 nonzeros), so the first-layer butterflies
+// see two inputs.  ZOUT: only outputs 0..7 are used (the last inverse stage of
+// a row with at most L/2 outputs), so the second layer forms half of them.
+template <bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void dft16(float2* x) {
   // 4 x 4: j = 4 j1 + j2, k = k1 + 4 k2
   float2 b[16];
 #pragma unroll
   for (int j2 = 0; j2 < 4; ++j2) {
-    float2 a0 = x[j2], a1 = x[4 + j2], a2 = x[8 + j2], a3 = x[12 + j2];
-    dft4<INV>(a0, a1, a2, a3);  // over j1 -> k1
+    float2 a0 = x[j2], a1 = x[4 + j2], a2, a3;
+    if constexpr (ZIN) {
+      a2 = csub(a0, a1);
+      a3 = sub_w4<INV>(a0, a1);
+      a1 = add_w4<INV>(a0, a1);
+      a0 = cadd(a0, x[4 + j2]);
+    } else {
+      a2 = x[8 + j2];
+      a3 = x[12 + j2];
+      dft4<INV>(a0, a1, a2, a3);  // over j1 -> k1
+    }
     b[4 * j2 + 0] = a0; b[4 * j2 + 1] = a1; b[4 * j2 + 2] = a2; b[4 * j2 + 3] = a3;
   }
   // twiddle W_16^{j2 k1}
@@ -157,17 +170,21 @@ __device__ __forceinline__ void dft16(float2* x) {
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
     float2 a0 = b[k1], a1 = b[4 + k1], a2 = b[8 + k1], a3 = b[12 + k1];
+    float2 s0, d0;
     if (k1 == 2) {
-      const float2 s0 = add_w4<INV>(a0, a2), d0 = sub_w4<INV>(a0, a2);
-      const float2 s1 = cadd(a1, a3), e1 = csub(a1, a3);
-      a0 = cadd(s0, s1);
-      a2 = csub(s0, s1);
-      a1 = add_w4<INV>(d0, e1);
-      a3 = sub_w4<INV>(d0, e1);
+      s0 = add_w4<INV>(a0, a2);
+      d0 = sub_w4<INV>(a0, a2);
     } else {
-      dft4<INV>(a0, a1, a2, a3);  // over j2 -> k2
+      s0 = cadd(a0, a2);
+      d0 = csub(a0, a2);
     }
-    x[k1 + 0] = a0; x[k1 + 4] = a1; x[k1 + 8] = a2; x[k1 + 12] = a3;
+    const float2 s1 = cadd(a1, a3), e1 = csub(a1, a3);
+    x[k1 + 0] = cadd(s0, s1);              // k2 = 0
+    x[k1 + 4] = add_w4<INV>(d0, e1);       // k2 = 1
+    if constexpr (!ZOUT) {
+      x[k1 + 8] = csub(s0, s1);            // k2 = 2
+      x[k1 + 12] = sub_w4<INV>(d0, e1);    // k2 = 3
+    }
   }
 }
 
@@ -207,7 +224,7 @@ __device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2) {
   a2 = csub(m, r);
 }
 
-template <int R, bool INV>
+template <int R, bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void dft(float2* x);
 
 // Twiddles W_R^{j2 k1} of a Cooley-Tukey split, element I = R1 j2 + k1.
@@ -244,8 +261,9 @@ __device__ __forceinline__ void dft_ct(float2* x) {
   }
 }
 
-template <int R, bool INV>
+template <int R, bool INV, bool ZIN, bool ZOUT>
 __device__ __forceinline__ void dft(float2* x) {
+  static_assert(R == 16 || !(ZIN || ZOUT), "pruned butterflies exist for radix 16");
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
     dft2<INV>(x[0], x[1]);
@@ -260,7 +278,7 @@ __device__ __forceinline__ void dft(float2* x) {
   } else if constexpr (R == 12) {
     dft_ct<3, 4, INV>(x);
   } else if constexpr (R == 16) {
-    dft16<INV>(x);
+    dft16<INV, ZIN, ZOUT>(x);
   } else if constexpr (R == 24) {
     dft_ct<3, 8, INV>(x);
   } else {
@@ -354,12 +372,12 @@ constexpr int tw_table_entries(int L, int E) { return stage_tw_offset(L, E, stag
 
 // Forward stage s on registers (values enter at the stage's read positions
 // and leave at the same positions with k in place of j).
-template <int L, int E, int S>
+template <int L, int E, int S, bool ZIN = false>
 __device__ __forceinline__ void stage_fwd(float2* v, int t, const float4* __restrict__ tw) {
   using St = Stage<L, E, S>;
 #pragma unroll
   for (int u = 0; u < St::NB; ++u) {
-    dft<St::R, false>(v + u * St::R);
+    dft<St::R, false, ZIN>(v + u * St::R);
     if constexpr (St::M > 1) {
       const float4* tp = tw + stage_tw_offset(L, E, S) + St::nidx(t, u);
 #pragma unroll
@@ -373,7 +391,7 @@ __device__ __forceinline__ void stage_fwd(float2* v, int t, const float4* __rest
 }
 
 // Adjoint of stage_fwd: conjugate twiddles, then the inverse radix-R DFT.
-template <int L, int E, int S>
+template <int L, int E, int S, bool ZOUT = false>
 __device__ __forceinline__ void stage_inv(float2* v, int t, const float4* __restrict__ tw) {
   using St = Stage<L, E, S>;
 #pragma unroll
@@ -387,7 +405,7 @@ __device__ __forceinline__ void stage_inv(float2* v, int t, const float4* __rest
         v[u * St::R + 2 * q + 1] = cmulc(v[u * St::R + 2 * q + 1], make_float2(w.z, w.w));
       }
     }
-    dft<St::R, true>(v + u * St::R);
+    dft<St::R, true, false, ZOUT>(v + u * St::R);
   }
 }
 
@@ -429,30 +447,32 @@ __device__ __forceinline__ void group_sync(int g) {
 
 // Full forward network.  Input: v[j] = x[t + T j] (stage 0 layout).
 // Output: the last stage's positions.  buf: this group's row buffer
-// (buf_elems(L) elements); g: the group's index in the CTA.
-template <int L, int E, int S = 0>
+// (buf_elems(L) elements); g: the group's index in the CTA.  PRUNE: v[j] is
+// zero for j >= E / 2 (a row of at most L / 2 nonzeros, E = 16 networks).
+template <int L, int E, int S = 0, bool PRUNE = false>
 __device__ __forceinline__ void fft_forward(float2* v, int t, int g, float2* buf, const float4* __restrict__ tw) {
   constexpr int NS = stage_count(L, E);
-  stage_fwd<L, E, S>(v, t, tw);
+  stage_fwd<L, E, S, PRUNE && S == 0>(v, t, tw);
   if constexpr (S + 1 < NS) {
     group_sync<L / E>(g);  // previous readers of buf are done
     stage_store<L, E, S>(v, t, buf);
     group_sync<L / E>(g);
     stage_load<L, E, S + 1>(v, t, buf);
-    fft_forward<L, E, S + 1>(v, t, g, buf, tw);
+    fft_forward<L, E, S + 1, PRUNE>(v, t, g, buf, tw);
   }
 }
 
 // Adjoint network: from the last stage's positions back to v[j] = x[t + T j].
-template <int L, int E, int S = stage_count(L, E) - 1>
+// PRUNE: only v[j], j < E / 2, are used afterwards (at most L / 2 outputs).
+template <int L, int E, int S = stage_count(L, E) - 1, bool PRUNE = false>
 __device__ __forceinline__ void fft_inverse(float2* v, int t, int g, float2* buf, const float4* __restrict__ tw) {
-  stage_inv<L, E, S>(v, t, tw);
+  stage_inv<L, E, S, PRUNE && S == 0>(v, t, tw);
   if constexpr (S > 0) {
     group_sync<L / E>(g);
     stage_store<L, E, S>(v, t, buf);
     group_sync<L / E>(g);
     stage_load<L, E, S - 1>(v, t, buf);
-    fft_inverse<L, E, S - 1>(v, t, g, buf, tw);
+    fft_inverse<L, E, S - 1, PRUNE>(v, t, g, buf, tw);
   }
 }
 

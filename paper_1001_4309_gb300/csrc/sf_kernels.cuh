@@ -115,11 +115,15 @@ struct StagedSrc {
 // of the tile leave as G-element contiguous runs.  With SPARE, the CTA may
 // have more threads than the tile's G T (a CTA sized for another length):
 // those only join the CTA barriers and the final store loop.
-template <int L, int KIND, typename Src, bool SPARE = false, int CTA = pass_cta_target(L)>
+template <int L, int KIND, typename Src, bool SPARE = false, int CTA = pass_cta_target(L), bool PRUNE = false>
 __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw,
                                              const Src& src) {
   using Sh = PassShape<L, CTA>;
   constexpr int T = Sh::T, G = Sh::G, E = fft_e(L);
+  // PRUNE (caller-checked: n0 <= L / 2 and n1 <= L / 2, E = 16): positions
+  // t + T j with j >= E / 2 are zero on input and unused on output
+  static_assert(!PRUNE || E == 16, "pruning is defined for the radix-16 network");
+  constexpr int J_IN = PRUNE ? E / 2 : E;
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   const int row = row0 + g;
   const bool active = !SPARE || threadIdx.x < Sh::THREADS;
@@ -132,18 +136,18 @@ __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int p = t + T * j;
-      v[j] = (valid && p < d.n0) ? src.in(g, row, p) : make_float2(0.f, 0.f);
+      v[j] = (j < J_IN && valid && p < d.n0) ? src.in(g, row, p) : make_float2(0.f, 0.f);
     }
 
-    fft_forward<L, E>(v, t, g, buf, tw);
+    fft_forward<L, E, 0, PRUNE>(v, t, g, buf, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = cmul(v[e], src.h(e * T + t));
-    fft_inverse<L, E>(v, t, g, buf, tw);
+    fft_inverse<L, E, stage_count(L, E) - 1, PRUNE>(v, t, g, buf, tw);
 
     // output chirp, then the transposed store through the tile [n1][G]
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
+    for (int j = 0; j < J_IN; ++j) {
       const int p = t + T * j;
       if (p < n1) smem[p * G + g] = cmul(v[j], src.co(p));
     }
@@ -176,20 +180,31 @@ __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2
   }
 }
 
-template <int L, int KIND, bool COHERENT, bool SPARE = false, int CTA = pass_cta_target(L)>
+template <int L, int KIND, bool COHERENT, bool SPARE = false, int CTA = pass_cta_target(L), bool PRUNE = false>
 __device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw) {
-  row_tile_src<L, KIND, GlobalSrc<KIND, COHERENT>, SPARE, CTA>(d, row0, smem, tw, GlobalSrc<KIND, COHERENT>{d});
+  row_tile_src<L, KIND, GlobalSrc<KIND, COHERENT>, SPARE, CTA, PRUNE>(d, row0, smem, tw,
+                                                                      GlobalSrc<KIND, COHERENT>{d});
 }
 
-// Row pass: tile blockIdx.x of pass blockIdx.y.
-template <int L, int KIND>
+// Row pass: tile blockIdx.x of pass blockIdx.y.  PRUNE: every pass of the
+// launch has n0 <= L / 2 and n1 <= L / 2 (the paper's 2N padding).
+template <int L, int KIND, bool PRUNE>
 __global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
 k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
   extern __shared__ float2 smem[];
   const PassDesc& d = b.d[blockIdx.y];
   const int row0 = blockIdx.x * PassShape<L>::G;
   if (row0 >= d.rows) return;  // whole CTA past this pass's rows
-  row_tile<L, KIND, false>(d, row0, smem, tw);
+  row_tile<L, KIND, false, false, pass_cta_target(L), PRUNE>(d, row0, smem, tw);
+}
+
+// The pruned network applies to the radix-16 (power-of-two) lengths.
+template <int L>
+bool pass_prunable(const PassBatch& b) {
+  if (!is_pow2(L) || fft_e(L) != 16) return false;
+  for (int k = 0; k < b.count; ++k)
+    if (2 * b.d[k].n0 > L || 2 * b.d[k].n1 > L) return false;
+  return true;
 }
 
 // Kernel spectrum of Eq. 4 (steps 5-6), one thread group per axis, run once
@@ -229,10 +244,19 @@ cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const f
     kern<<<grid, block, Sh::SMEM, s>>>(b, tw);
     return cudaGetLastError();
   };
+  if constexpr (is_pow2(L)) {
+    if (pass_prunable<L>(b)) {
+      switch (kind) {
+        case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL, true>);
+        case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX, true>);
+        case PASS_Y: return go(k_pass<L, PASS_Y, true>);
+      }
+    }
+  }
   switch (kind) {
-    case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL>);
-    case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX>);
-    case PASS_Y: return go(k_pass<L, PASS_Y>);
+    case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL, false>);
+    case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX, false>);
+    case PASS_Y: return go(k_pass<L, PASS_Y, false>);
   }
   return cudaErrorInvalidValue;
 }
