@@ -61,7 +61,7 @@ __device__ __forceinline__ void decode(const PersistArgs& pa, int tile, int& k, 
   row0 = (tile - pa.tile_off[k]) * PassShape<L>::G;
 }
 
-template <int L, int KIND>
+template <int L, int KIND, bool PRUNE>
 __global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
 k_pass_tma(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, const __grid_constant__ PersistArgs pa) {
   using Sh = PassShape<L>;
@@ -121,7 +121,7 @@ k_pass_tma(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, c
       atomicExch(pa.err, 1);
     }
     const StagedSrc<KIND> src{cin_s, h_s, cout_s, rows + (size_t)((i & 1) * G) * pa.row_bytes, pa.row_bytes};
-    row_tile_src<L, KIND>(d, row0, exch, tw, src);
+    row_tile_src<L, KIND, StagedSrc<KIND>, false, pass_cta_target(L), PRUNE>(d, row0, exch, tw, src);
     __syncthreads();  // stage (i & 1) is free for the copy issued in the next iteration
   }
   if (failed) {
@@ -137,7 +137,7 @@ k_pass_tma(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, c
 template <int L, int KIND>
 cudaError_t launch_tma_t(const PassBatch& b, const float4* tw, const PersistArgs& pa, int grid, size_t smem,
                          cudaStream_t s) {
-  auto kern = k_pass_tma<L, KIND>;
+  auto kern = pass_prunable<L>(b) ? k_pass_tma<L, KIND, true> : k_pass_tma<L, KIND, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, PassShape<L>::THREADS, smem, s>>>(b, tw, pa);
@@ -158,7 +158,7 @@ cudaError_t launch_tma_kind(PassKind kind, const PassBatch& b, const float4* tw,
 template <int L, int KIND>
 int occupancy_t(size_t smem) {
   int n = 0;
-  auto kern = k_pass_tma<L, KIND>;
+  auto kern = k_pass_tma<L, KIND, false>;  // the pruned variant has the same resources
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, PassShape<L>::THREADS, smem) != cudaSuccess) {
     cudaGetLastError();
