@@ -329,7 +329,10 @@ uint64_t shifted_fresnel_kernel_launches(void);
  *                         cheaper row-pass kernel, by the time per row of a
  *                         synthetic pass timed once per device and process.
  *   SF_AUTOTUNE_CACHE=path  file the measurements are read from and appended
- *                         to (one "device L kind kernel ns_per_row" line each).
+ *                         to (one "device L kind kernel prunable ns_per_row"
+ *                         line each; prunable: n0, n1 <= L/2, where the
+ *                         power-of-two network skips the dead half of its
+ *                         first and last stage).
  * All choices compute the same convolution; results differ by rounding only.
  */
 int32_t shifted_fresnel_fft_length(int32_t need, int32_t allow_mixed);

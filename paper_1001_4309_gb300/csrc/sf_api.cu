@@ -622,17 +622,22 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
   auto kind_of = [&](int axis) {
     return axis == 1 ? PASS_Y : (p->in_complex ? PASS_X_CPLX : PASS_X_REAL);
   };
-  // best measured cost of (L, kind) over the kernels, remembering the kernel
-  auto best = [&](int L, PassKind kind, int* impl) {
+  // best measured cost of (L, kind, prunable) over the kernels, remembering the kernel
+  auto best = [&](int L, PassKind kind, bool prune, int* impl) {
     double b = -1;
     for (int k = 0; k < 2; ++k) {
-      const double ns = row_cost_ns(p->device, L, kind, k, p->sms, s);
+      const double ns = row_cost_ns(p->device, L, kind, k, prune, p->sms, s);
       if (ns > 0 && (b < 0 || ns < b)) {
         b = ns;
         if (impl) *impl = k;
       }
     }
     return b;
+  };
+  // does axis a of view i run the pruned network at length L
+  auto prunable = [&](int i, int a, int L) {
+    const int n0 = a == 0 ? views[i].nx0 : views[i].ny0, n1 = a == 0 ? views[i].nx1 : views[i].ny1;
+    return (L & (L - 1)) == 0 && 2 * n0 <= L && 2 * n1 <= L;
   };
   for (int i = 0; i < n_views; ++i)
     for (int a = 0; a < 2; ++a) {
@@ -642,7 +647,8 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
       if (precision != SF_PREC_FP32 && tc_length_supported(P)) {
         L = P;
       } else if (tune && Q != P) {
-        const double cp = best(P, kind_of(a), nullptr), cq = best(Q, kind_of(a), nullptr);
+        const double cp = best(P, kind_of(a), prunable(i, a, P), nullptr);
+        const double cq = best(Q, kind_of(a), prunable(i, a, Q), nullptr);
         if (cp > 0 && cq > 0 && cp < cq) L = P;
       }
       c.L[2 * i + a] = L;
@@ -652,11 +658,14 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
       const int L = kFftLengths[slot];
       c.impl[slot][k] = tma_length_supported(L) ? impl_default(L) : 0;
       if (!tune || !tma_length_supported(L)) continue;
-      bool used = false;
-      for (int i = 0; i < n_views && !used; ++i)
+      bool used = false, all_prunable = true;
+      for (int i = 0; i < n_views; ++i)
         for (int a = 0; a < 2; ++a)
-          if (c.L[2 * i + a] == L && (kind_of(a) == k || (a == 0 && k == PASS_X_CPLX))) used = true;  // adjoint x: complex
-      if (used) best(L, (PassKind)k, &c.impl[slot][k]);
+          if (c.L[2 * i + a] == L && (kind_of(a) == k || (a == 0 && k == PASS_X_CPLX))) {  // adjoint x: complex
+            used = true;
+            all_prunable = all_prunable && prunable(i, a, L);
+          }
+      if (used) best(L, (PassKind)k, all_prunable, &c.impl[slot][k]);
     }
   return c;
 }

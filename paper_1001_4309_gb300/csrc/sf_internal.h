@@ -88,9 +88,9 @@ void adjoint_axis_coefficients(const sf_view& v, int axis, AxisCoef& a, int L = 
 
 // Autotuner (sf_tune.cu): SF_AUTOTUNE=1 selects measured choices; row_cost_ns
 // is the measured time per row (ns) of a pass of length L, kind and kernel
-// (0 one tile per CTA, 1 persistent), < 0 when not available.
+// (0 one tile per CTA, 1 persistent), prunable or not, < 0 when not available.
 int autotune_mode();
-double row_cost_ns(int device, int L, PassKind kind, int impl, int sms, cudaStream_t s);
+double row_cost_ns(int device, int L, PassKind kind, int impl, bool prune, int sms, cudaStream_t s);
 
 // Inner products for d(loss)/dz of one view (see shifted_fresnel_adjoint).
 struct ZGradArgs {

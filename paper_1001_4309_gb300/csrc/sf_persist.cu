@@ -209,6 +209,12 @@ int tma_occupancy(int L, PassKind kind, size_t smem) {
 
 cudaError_t launch_pass_persistent(int L, PassKind kind, const PassBatch& b, const float4* tw, int* err, int sms,
                                    cudaStream_t s) {
+  // bulk copies move whole rows: addresses, strides and row lengths must be multiples of 16 bytes
+  const size_t elem = kind == PASS_X_REAL ? sizeof(float) : sizeof(float2);
+  if (!tma_length_supported(L)) return cudaErrorInvalidValue;
+  for (int k = 0; k < b.count; ++k)
+    if (reinterpret_cast<uintptr_t>(b.d[k].src) % 16 || (b.d[k].src_ld * elem) % 16 || (b.d[k].n0 * elem) % 16)
+      return cudaErrorInvalidValue;
   PersistArgs pa;
   std::memset(&pa, 0, sizeof(pa));
   const int G = pass_rows_per_cta(L);

@@ -1,15 +1,18 @@
 // sf_tune.cu -- plan-time autotuner for the FP32 row passes.
 //
 // The cost of a row pass is (rows) x (time per row), and the time per row
-// depends only on the FFT length L, the pass kind (real x, complex x, y) and
-// the kernel (one tile per CTA, or the persistent kernel with bulk-copy
-// prefetch).  The tuner measures that time per row once per device and
-// process for each (L, kind, kernel) a plan asks about: one pass over a
-// synthetic batch of rows (zero data, n0 = n1 = L / 2, rows x L = 2^23),
-// two launches of warm-up, then the median of five launches timed with CUDA
-// events.  With SF_AUTOTUNE_CACHE naming a file, measurements are also read
-// from and appended to it (one line per measurement: device key, L, kind,
-// kernel, ns per row), so later processes skip the timing.
+// depends only on the FFT length L, the pass kind (real x, complex x, y), the
+// kernel (one tile per CTA, or the persistent kernel with bulk-copy prefetch)
+// and whether the pass is prunable (n0, n1 <= L / 2: the radix-16 network
+// skips the dead half of its first and last stage).  The tuner measures that
+// time per row once per device and process for each (L, kind, kernel,
+// prunable) a plan asks about: one pass over a synthetic batch of rows (zero
+// data; n0 = n1 = L / 2 when prunable, else n0 = L / 2 + 4, n1 = L / 2 - 4;
+// rows x L = 2^23), two launches of warm-up, then the median of five launches
+// timed with CUDA events.  With SF_AUTOTUNE_CACHE naming a file, measurements
+// are also read from and appended to it (one line per measurement: device
+// key, L, kind, kernel, prunable, ns per row), so later processes skip the
+// timing.
 //
 // The plan then picks, per axis, the cheaper of the two FFT lengths that can
 // hold the linear convolution (the next power of two, and the next length
@@ -30,7 +33,7 @@
 namespace sf {
 namespace {
 
-using Key = std::tuple<std::string, int, int, int>;  // device key, L, kind, kernel
+using Key = std::tuple<std::string, int, int, int, int>;  // device key, L, kind, kernel, prunable
 
 std::mutex g_mu;
 std::map<Key, double> g_cost;
@@ -56,10 +59,10 @@ void read_cache_file() {
   FILE* f = std::fopen(path, "r");
   if (!f) return;
   char dev[256];
-  int L, kind, impl;
+  int L, kind, impl, prune;
   double ns;
-  while (std::fscanf(f, "%255s %d %d %d %lf", dev, &L, &kind, &impl, &ns) == 5)
-    if (ns > 0) g_cost[Key(dev, L, kind, impl)] = ns;
+  while (std::fscanf(f, "%255s %d %d %d %d %lf", dev, &L, &kind, &impl, &prune, &ns) == 6)
+    if (ns > 0) g_cost[Key(dev, L, kind, impl, prune)] = ns;
   std::fclose(f);
 }
 
@@ -68,15 +71,18 @@ void append_cache_file(const Key& k, double ns) {
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %.6g\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k), ns);
+  std::fprintf(f, "%s %d %d %d %d %.6g\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+               std::get<4>(k), ns);
   std::fclose(f);
 }
 
 // Time per row (ns) of one synthetic pass; < 0 if it could not be measured.
-double measure(int L, PassKind kind, int impl, int sms, cudaStream_t s) {
+double measure(int L, PassKind kind, int impl, bool prune, int sms, cudaStream_t s) {
   const int G = pass_rows_per_cta(L);
   if (G < 1) return -1;
-  const int n0 = L / 2, n1 = L / 2;
+  // not prunable: n0 just above L / 2, keeping rows a multiple of 16 bytes
+  // (the persistent kernel's bulk copies need that)
+  const int n0 = prune ? L / 2 : L / 2 + 4, n1 = prune ? L / 2 : L / 2 - 4;
   int rows = std::max(256, (1 << 23) / L);
   rows = (rows + G - 1) / G * G;
   const size_t elem = kind == PASS_X_REAL ? sizeof(float) : sizeof(float2);
@@ -153,14 +159,14 @@ int autotune_mode() {
   return (m && std::strcmp(m, "1") == 0) ? 1 : 0;
 }
 
-double row_cost_ns(int device, int L, PassKind kind, int impl, int sms, cudaStream_t s) {
+double row_cost_ns(int device, int L, PassKind kind, int impl, bool prune, int sms, cudaStream_t s) {
   if (impl == 1 && !tma_length_supported(L)) return -1;
   std::lock_guard<std::mutex> lock(g_mu);
   read_cache_file();
-  const Key k(device_key(device), L, (int)kind, impl);
+  const Key k(device_key(device), L, (int)kind, impl, prune ? 1 : 0);
   auto it = g_cost.find(k);
   if (it != g_cost.end()) return it->second;
-  const double ns = measure(L, kind, impl, sms, s);
+  const double ns = measure(L, kind, impl, prune, sms, s);
   if (ns > 0) {
     g_cost[k] = ns;
     append_cache_file(k, ns);

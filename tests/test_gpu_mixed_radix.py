@@ -116,7 +116,7 @@ def test_autotuner_choices_cache_and_parity(P, monkeypatch, tmp_path):
     holo = random_field(n0[1], n0[0], seed=9).real
     lens, out = reconstruct(P, views, holo)
     lines = cache.read_text().split()
-    assert len(lines) > 0 and len(lines) % 5 == 0
+    assert len(lines) > 0 and len(lines) % 6 == 0  # device, L, kind, kernel, prunable, ns per row
     for (lx, ly), v in zip(lens, views):
         for L, need in ((lx, v["nx0"] + v["nx1"] - 1), (ly, v["ny0"] + v["ny1"] - 1)):
             assert L in (P.shifted_fresnel_fft_length(need, True), P.shifted_fresnel_fft_length(need, False))
