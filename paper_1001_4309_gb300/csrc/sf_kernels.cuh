@@ -14,9 +14,12 @@
 // The x pass reads hologram rows and writes the intermediate transposed,
 // [nx1][ny0]; the y pass then reads those rows (hologram columns) and writes
 // the view [ny1][nx1] transposed back.  Both passes load contiguous rows.
-// A CTA holds G = max(1, 256 / T) groups of T = L / E threads (E = 16 for
-// power-of-two lengths, 24 for the lengths with a factor 3); group g handles
-// row blockIdx.x * G + g of pass blockIdx.y.
+// A CTA holds G groups of T = L / E threads (E = 16 for power-of-two lengths,
+// 24 for the lengths with a factor 3; G from pass_cta_target); group g
+// handles row blockIdx.x * G + g of pass blockIdx.y.  When every pass of a
+// launch has n0, n1 <= L / 2 (the paper's 2N padding) the pruned variant
+// skips the zero half of the first forward stage and the cropped half of the
+// last inverse stage.
 #pragma once
 
 #include <climits>
