@@ -129,15 +129,19 @@ def measured_peaks():
 
 
 def source_hash():
-    """Hash of the sources the row-pass kernel k_pass is compiled from; ncu
-    traffic figures are only used while it matches the captured version."""
+    """Hash of the code (comments and blank lines stripped) of the sources the
+    row-pass kernel k_pass is compiled from; ncu traffic figures are only used
+    while it matches the captured version."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1001_4309_gb300", "csrc")
     files = [os.path.join(csrc, n) for n in ("sf_fft.cuh", "sf_kernels.cuh", "sf_pass.h")]
     for p in sorted(files + glob.glob(os.path.join(csrc, "sf_inst_*.cu"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
-            h.update(f.read())
+        with open(p) as f:
+            code = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+        code = "\n".join(line for line in (re.sub(r"//.*", "", x).rstrip() for x in code.splitlines()) if line)
+        h.update(os.path.basename(p).encode())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 
