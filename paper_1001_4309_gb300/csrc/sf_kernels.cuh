@@ -27,12 +27,9 @@
 #include "sf_fft.cuh"
 #include "sf_internal.h"
 
-#ifndef SF_PASS_CTA_THREADS
-#define SF_PASS_CTA_THREADS 256
-#endif
-#ifndef SF_PASS_MIN_WARPS
-#define SF_PASS_MIN_WARPS 16
-#endif
+// CTA size and resident warps per SM the power-of-two row passes are built for
+constexpr int kPassCtaThreads = 256;
+constexpr int kPassMinWarps = 16;
 
 namespace sf {
 
@@ -43,7 +40,7 @@ constexpr int fft_e(int L) { return is_pow2(L) ? kE : 24; }
 // where a 256-thread CTA holds a single row and two rows per CTA measured 9 %
 // faster per row), 192 for the lengths with a factor 3 (24 values per thread).
 constexpr int pass_cta_target(int L) {
-  return !is_pow2(L) ? 192 : (L == 4096 ? 2 * SF_PASS_CTA_THREADS : SF_PASS_CTA_THREADS);
+  return !is_pow2(L) ? 192 : (L == 4096 ? 2 * kPassCtaThreads : kPassCtaThreads);
 }
 
 // G rows of T = L / E threads per CTA.  Registers: powers of two for 16 warps
@@ -51,7 +48,7 @@ constexpr int pass_cta_target(int L) {
 template <int L, int CTA = pass_cta_target(L)>
 struct PassShape {
   static constexpr int T = L / fft_e(L);
-  static constexpr int MIN_WARPS = is_pow2(L) ? SF_PASS_MIN_WARPS : 12;
+  static constexpr int MIN_WARPS = is_pow2(L) ? kPassMinWarps : 12;
   static constexpr int G = (CTA / T) > 0 ? (CTA / T) : 1;
   static constexpr int THREADS = G * T;
   // CTAs per SM the register budget is set for

@@ -7,10 +7,7 @@
 namespace sf {
 
 constexpr int kMaxPassBatch = 16;  // (view, axis) passes per launch
-#ifndef SF_FFT_E
-#define SF_FFT_E 16
-#endif
-constexpr int kE = SF_FFT_E;       // complex values per thread in the FP32 FFT network
+constexpr int kE = 16;             // complex values per thread in the power-of-two FP32 FFT network
 constexpr int kTcE = 16;           // radix of the tensor-core network's stages
 
 enum PassKind : int { PASS_X_REAL = 0, PASS_X_CPLX = 1, PASS_Y = 2 };
