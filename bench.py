@@ -41,6 +41,7 @@ PAPER_CONTEXT = {  # the paper's own figures (Section 3), other hardware: contex
     "gpu": "four 1024^2 views (2048^2 padded) in about 60 ms (about 67 views/s) on four GT200 chips "
            "(2x GTX 295, CUDA 2.3, CUFFT), loop including host copies",
     "cpu": "the same four views in 9,542 ms (about 0.42 views/s) on a Core2Quad Q6600"}
+PAPER_GPU_VIEWS_PER_S = 4 / 0.060  # the paper's four views in about 60 ms, host copies included
 ERROR_COLS = 8  # columns per sampled block (first, middle, last block of every view)
 
 
@@ -386,7 +387,7 @@ def run_ours(a):
                                "what": "hologram read once + complex views written once"},
             "accuracy_fp32": accuracy,
             "plan_ms": round(plan_ms, 2),
-            "paper_context": PAPER_CONTEXT,
+            "paper_context": dict(PAPER_CONTEXT, e2e_over_paper_gpu=round(e2e["value"] / PAPER_GPU_VIEWS_PER_S, 1)),
             "plain_path": plain,
             "batched": batched,
             "mixed_precision": mixed,
