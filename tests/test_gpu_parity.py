@@ -246,3 +246,20 @@ def test_row_pass_kernels_agree(P, n0, n1, monkeypatch):
     for cols in sample_columns(n1):
         check_view({"field": [res["tma"][:, cols[0]:cols[1]]], "intensity": [None], "phase": [None]}, 0,
                    oracle.forward(holo, v, cols=cols))
+
+
+def test_many_views_one_plan(P):
+    """40 ragged views of one hologram: several launches per FFT length (16 passes each), both halves of
+    the two-stream split, every length family; sampled columns of every view against the oracle."""
+    rng = np.random.default_rng(21)
+    n0 = (300, 260)
+    sizes = [(int(a), int(b)) for a, b in rng.integers(1, 1300, size=(40, 2))]
+    views = [view(WAVELENGTH, float(rng.uniform(0.02, 0.12)) * (-1) ** k, PITCH,
+                  float(np.exp(rng.uniform(np.log(0.25e-6), np.log(9.3e-6)))),
+                  o1=tuple(rng.uniform(-1e-3, 1e-3, size=2)), n0=n0, n1=n1) for k, n1 in enumerate(sizes)]
+    holo = random_field(n0[1], n0[0], seed=99).real
+    res = run(P, views, holo, intensity=False, phase=False)
+    for i, v in enumerate(views):
+        c = (v["nx1"] // 2, min(v["nx1"], v["nx1"] // 2 + 3))
+        check_view({"field": [res["field"][i][:, c[0]:c[1]]], "intensity": [None], "phase": [None]}, 0,
+                   oracle.forward(holo, v, cols=c))
