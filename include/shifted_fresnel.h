@@ -155,7 +155,10 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
  *   streams     execute's per-length row-pass kernels, even holograms on one
  *               plan-owned stream and odd ones on another (one intermediate
  *               slot each), joined back into `stream`; consecutive holograms
- *               overlap.  Any FFT length.
+ *               overlap.  The launches are captured as a CUDA graph on a
+ *               plan-owned stream and the graph is replayed while calls pass
+ *               the same hologram count and buffers (other calls capture
+ *               anew).  Any FFT length.
  *
  * Choice: SF_BATCH_IMPL=persistent|streams forces one; with SF_AUTOTUNE=1 the
  * first call for each n_holos times both on its own buffers (blocking) and

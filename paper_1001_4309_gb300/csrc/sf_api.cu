@@ -62,6 +62,12 @@ struct BatchState {
   // the per-length kernels on two streams (even / odd holograms, one slot each)
   cudaStream_t st[2] = {nullptr, nullptr};
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+  // those launches captured as a CUDA graph, replayed while calls pass the same buffers
+  cudaGraphExec_t sgraph = nullptr;
+  std::vector<const void*> skey;         // hologram count and every buffer pointer of the captured call
+  uint64_t sgraph_kernels = 0;           // kernels in the graph
+  cudaStream_t cap = nullptr;            // the graph is captured and launched on this plan stream
+  cudaEvent_t pre = nullptr, post = nullptr;  // caller's stream -> cap -> caller's stream
   std::map<int, int> choice;             // hologram count -> BATCH_PERSISTENT / BATCH_STREAMS (autotuned)
 };
 enum { BATCH_PERSISTENT = 0, BATCH_STREAMS = 1 };
@@ -257,6 +263,10 @@ void free_plan(sf_plan p) {
     if (p->batch.st[k]) cudaStreamDestroy(p->batch.st[k]);
   }
   if (p->batch.fork) cudaEventDestroy(p->batch.fork);
+  if (p->batch.sgraph) cudaGraphExecDestroy(p->batch.sgraph);
+  if (p->batch.pre) cudaEventDestroy(p->batch.pre);
+  if (p->batch.post) cudaEventDestroy(p->batch.post);
+  if (p->batch.cap) cudaStreamDestroy(p->batch.cap);
   if (p->batch.d_fixed) cudaFree(p->batch.d_fixed);
   for (void* s : p->staging) cudaFree(s);
   if (p->arena) cudaFree(p->arena);
@@ -436,7 +446,11 @@ int batch_prepare(sf_plan p, int n_holos, bool persistent) {
           cudaEventCreateWithFlags(&b.join[k], cudaEventDisableTiming) != cudaSuccess ||
           cudaStreamCreateWithFlags(&b.st[k], cudaStreamNonBlocking) != cudaSuccess)
         return SF_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return SF_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.pre, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.post, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b.cap, cudaStreamNonBlocking) != cudaSuccess)
+      return SF_ERR_CUDA;
     b.init = true;
   }
   if (!persistent || b.n_holos == n_holos) return SF_OK;
@@ -717,10 +731,10 @@ int run_batch_persistent(sf_plan plan, const void* const* holos, int n_holos, vo
 
 // The per-length row-pass kernels, holograms alternating between two streams
 // (and two intermediate slots), so one hologram's passes overlap the next's.
-int run_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
-                      float* const* intensity, float* const* phase, cudaStream_t s) {
-  int rc = batch_prepare(plan, n_holos, false);
-  if (rc) return rc;
+// Enqueue the per-length launches of a batch on the plan's two streams,
+// forked from and joined back into s.
+cudaError_t enqueue_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
+                                  float* const* intensity, float* const* phase, cudaStream_t s) {
   BatchState& b = plan->batch;
   const int nv = (int)plan->views.size();
   cudaError_t e = cudaEventRecord(b.fork, s);
@@ -744,6 +758,62 @@ int run_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void*
     e = cudaEventRecord(b.join[k], b.st[k]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.join[k], 0);
   }
+  return e;
+}
+
+// The per-length row-pass kernels, holograms alternating between two streams
+// (and two intermediate slots), so one hologram's passes overlap the next's.
+// The launches are captured once as a CUDA graph and the graph is replayed
+// while calls pass the same hologram count and buffers (a frame loop over
+// fixed buffers pays one graph launch per call); other calls capture anew.
+int run_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
+                      float* const* intensity, float* const* phase, cudaStream_t s) {
+  int rc = batch_prepare(plan, n_holos, false);
+  if (rc) return rc;
+  BatchState& b = plan->batch;
+  const size_t n = (size_t)n_holos * plan->views.size();
+  std::vector<const void*> key;
+  key.reserve(1 + n_holos + 3 * n);
+  key.push_back(reinterpret_cast<const void*>((uintptr_t)n_holos));
+  for (int h = 0; h < n_holos; ++h) key.push_back(holos[h]);
+  for (size_t i = 0; i < n; ++i) {
+    key.push_back(view_out ? view_out[i] : nullptr);
+    key.push_back(intensity ? intensity[i] : nullptr);
+    key.push_back(phase ? phase[i] : nullptr);
+  }
+  cudaError_t e = cudaSuccess;
+  const bool replay = b.sgraph && key == b.skey;
+  if (!replay) {
+    if (b.sgraph) cudaGraphExecDestroy(b.sgraph);
+    b.sgraph = nullptr;
+    b.skey.clear();
+    const uint64_t before = g_launches.load();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t ee = enqueue_batch_streams(plan, holos, n_holos, view_out, intensity, phase, b.cap);
+      e = cudaStreamEndCapture(b.cap, &graph);
+      if (ee != cudaSuccess) e = ee;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      return SF_ERR_CUDA;
+    }
+    b.sgraph = exec;
+    b.skey = key;
+    b.sgraph_kernels = g_launches.load() - before;  // counted while capturing
+  }
+  // ordered after the caller's earlier work, and the caller's stream after the graph
+  e = cudaEventRecord(b.pre, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b.cap, b.pre, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b.sgraph, b.cap);
+  if (e == cudaSuccess) e = cudaEventRecord(b.post, b.cap);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.post, 0);
+  if (replay) g_launches += b.sgraph_kernels;
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SF_ERR_CUDA;
