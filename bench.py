@@ -371,6 +371,7 @@ def run_ours(a):
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 5),
+            "ms_per_step_median": round(statistics.median(step_ms), 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded in-line Gabor holograms; the paper's real holograms are not available)",
             "config": {"workload": WORKLOAD, "views_per_step": V, "fft_lengths": lengths[0],
