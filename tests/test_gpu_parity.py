@@ -81,6 +81,8 @@ SMALL = [
     (33, 17, 100, 3, 0.1, 2e-6, 9.3e-6, (0, 0), (-2e-3, 2e-3), 8 | 4),
     (64, 65, 65, 64, 0.04, PITCH, 2.325e-6, (0, 0), (1e-4, -5e-5), 4),
     (255, 129, 258, 127, 0.05, PITCH, 1.0e-6, (3e-5, -3e-5), (-4e-4, 6e-4), 0),
+    # exactly L / 2 in and out on both axes (L = 64 and 512): the pruned network at its limit
+    (32, 256, 32, 256, 0.045, PITCH, 3.3e-6, (1e-5, 2e-5), (1e-4, -1e-4), 8),
 ]
 
 
