@@ -348,6 +348,20 @@ def run_ours(a):
            "h2d_bytes_per_step": int(h_host.numel() * 4),
            "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in o_host)),
            "path": "shifted_fresnel_execute with pinned host buffers (library-staged copies), stream sync per step"}
+    # the paper's own loop returns intensity images (Section 2.2, steps 10-11): the same step with float32
+    # |u1|^2 outputs only, for comparison (the headline above returns the complex fields)
+    i_host = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.float32).pin_memory() for v in views]
+    n_i = max(1, min(a.steps, 500))
+    for _ in range(a.warmup):
+        P.shifted_fresnel_execute(sf.handle, h_host.data_ptr(), None, [o.data_ptr() for o in i_host], stream=sptr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_i):
+        P.shifted_fresnel_execute(sf.handle, h_host.data_ptr(), None, [o.data_ptr() for o in i_host], stream=sptr)
+        stream.synchronize()
+    ei_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e["intensity_outputs"] = {"value": round(job_value(V, n_i, world, ei_s * 1e3), 1), "unit": UNIT,
+                                "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in i_host)), "steps": n_i}
 
     plain = plain_path(holo, views, outs, flush, stream, a, step_bytes, float(peaks["hbm_gbs"]), value / world)
     batched = None if a.no_batch else batched_runs(holo_np, views, dev, stream, flush, float(peaks["hbm_gbs"]))
