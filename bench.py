@@ -325,6 +325,18 @@ def run_ours(a):
                 "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": round(dom_ms, 5)}
     step_bytes = alg["x"][0] + alg["y"][0]
     step_flops = alg["x"][1] + alg["y"][1]
+    # FP32 co-bound of the same kernel: nominal FFT flops against the FP32 CUDA
+    # cores' FMA peak from unit counts and clocks (128 FP32 lanes per SM, 2
+    # flops per FMA, the maximum SM clock read during the timed region)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = clk.get("sm_max_mhz") or 2070.0
+    fp32_peak = sm_count * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+    dom_tflops = dom_flops / (dom_ms * 1e-3) / 1e12
+    roofline["alu_co_bound"] = {
+        "bound": "alu", "achieved": round(dom_tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+        "frac": round(dom_tflops / fp32_peak, 4),
+        "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flops/FMA x {sm_max_mhz:.0f} MHz",
+        "flops": "nominal 2 x 5 L log2 L per row (forward + inverse FFT)"}
     passes = {p: {"ms": round(m, 5), "algorithmic_bytes": alg[p][0],
                   "gbs": round(alg[p][0] / (m * 1e-3) / 1e9, 1),
                   "nominal_tflops": round(alg[p][1] / (m * 1e-3) / 1e12, 2)}

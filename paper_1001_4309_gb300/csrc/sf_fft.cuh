@@ -337,6 +337,39 @@ constexpr bool stage_phys_additive(int L, int E, int s) {
   return true;
 }
 
+// Butterfly u (u < E / R) of thread t in stage s.  Power-of-two networks give
+// a thread consecutive butterflies (t NB + u), so a stage's butterflies stay
+// with the warp that produced their inputs whenever the previous stage's
+// stride is at most 32 (warp_local_exchange); the lengths with a factor 3
+// interleave them (t + T u).
+constexpr int stage_butterfly(int L, int E, int s, int t, int u) {
+  return is_pow2(L) ? t * (E / stage_radix(L, E, s)) + u : t + (L / E) * u;
+}
+
+// Thread that owns position p in stage s.
+constexpr int stage_owner(int L, int E, int s, int p) {
+  const int MP = stage_mprev(L, E, s), R = stage_radix(L, E, s), M = MP / R, NB = E / R, T = L / E;
+  const int b = (p / MP) * M + (p % MP) % M;
+  return is_pow2(L) ? b / NB : b % T;
+}
+
+// The exchange between stages s and s + 1 stays inside each warp: every
+// position a thread loads for stage s + 1 was stored by a thread of its own
+// warp.  Row groups must be whole warps (T a multiple of 32).
+constexpr bool warp_local_exchange(int L, int E, int s) {
+  const int T = L / E;
+  if (T % 32 != 0) return false;
+  for (int t = 0; t < T; ++t)
+    for (int u = 0; u < E / stage_radix(L, E, s + 1); ++u) {
+      const int b = stage_butterfly(L, E, s + 1, t, u);
+      const int MP = stage_mprev(L, E, s + 1), M = MP / stage_radix(L, E, s + 1);
+      const int base = (b / M) * MP + b % M;
+      for (int k = 0; k < stage_radix(L, E, s + 1); ++k)
+        if (stage_owner(L, E, s, base + k * M) / 32 != t / 32) return false;
+    }
+  return true;
+}
+
 // Position of element j of butterfly u (u < E / R) of thread t in stage s.
 template <int L, int E, int S>
 struct Stage {
@@ -348,10 +381,10 @@ struct Stage {
   static_assert(E % R == 0, "radix must divide the per-thread element count");
   static_assert(stage_phys_additive(L, E, S), "padded addresses must split into base + offset");
   __device__ __forceinline__ static int base(int t, int u) {
-    int b = t + T * u;
+    const int b = stage_butterfly(L, E, S, t, u);
     return (b / M) * MP + (b % M);
   }
-  __device__ __forceinline__ static int nidx(int t, int u) { return (t + T * u) % M; }
+  __device__ __forceinline__ static int nidx(int t, int u) { return stage_butterfly(L, E, S, t, u) % M; }
 };
 
 // Per-stage twiddle tables.  Stage s (with M > 1) owns M * R / 2 float4
@@ -445,18 +478,32 @@ __device__ __forceinline__ void group_sync(int g) {
   }
 }
 
+// Makes the stores of the exchange between stages s and s + 1 visible to
+// the loads of the other side: a warp barrier when the exchange stays inside
+// each warp, the row group's barrier otherwise.
+template <int L, int E, int S>
+__device__ __forceinline__ void exchange_sync(int g) {
+  if constexpr (warp_local_exchange(L, E, S)) __syncwarp();
+  else group_sync<L / E>(g);
+}
+
 // Full forward network.  Input: v[j] = x[t + T j] (stage 0 layout).
 // Output: the last stage's positions.  buf: this group's row buffer
 // (buf_elems(L) elements); g: the group's index in the CTA.  PRUNE: v[j] is
 // zero for j >= E / 2 (a row of at most L / 2 nonzeros, E = 16 networks).
+//
+// Only the first store needs a barrier in front (earlier users of buf may
+// still read any position): every later store of a stage's positions goes to
+// exactly the positions the same thread loaded for that stage, so no other
+// thread still needs their old contents.
 template <int L, int E, int S = 0, bool PRUNE = false>
 __device__ __forceinline__ void fft_forward(float2* v, int t, int g, float2* buf, const float4* __restrict__ tw) {
   constexpr int NS = stage_count(L, E);
   stage_fwd<L, E, S, PRUNE && S == 0>(v, t, tw);
   if constexpr (S + 1 < NS) {
-    group_sync<L / E>(g);  // previous readers of buf are done
+    if constexpr (S == 0) group_sync<L / E>(g);  // previous readers of buf are done
     stage_store<L, E, S>(v, t, buf);
-    group_sync<L / E>(g);
+    exchange_sync<L, E, S>(g);
     stage_load<L, E, S + 1>(v, t, buf);
     fft_forward<L, E, S + 1, PRUNE>(v, t, g, buf, tw);
   }
@@ -464,13 +511,14 @@ __device__ __forceinline__ void fft_forward(float2* v, int t, int g, float2* buf
 
 // Adjoint network: from the last stage's positions back to v[j] = x[t + T j].
 // PRUNE: only v[j], j < E / 2, are used afterwards (at most L / 2 outputs).
+// Runs on the buffer fft_forward left (each thread last accessed its own
+// last-stage positions there), so its stores need no barrier in front.
 template <int L, int E, int S = stage_count(L, E) - 1, bool PRUNE = false>
 __device__ __forceinline__ void fft_inverse(float2* v, int t, int g, float2* buf, const float4* __restrict__ tw) {
   stage_inv<L, E, S, PRUNE && S == 0>(v, t, tw);
   if constexpr (S > 0) {
-    group_sync<L / E>(g);
     stage_store<L, E, S>(v, t, buf);
-    group_sync<L / E>(g);
+    exchange_sync<L, E, S - 1>(g);
     stage_load<L, E, S - 1>(v, t, buf);
     fft_inverse<L, E, S - 1, PRUNE>(v, t, g, buf, tw);
   }
