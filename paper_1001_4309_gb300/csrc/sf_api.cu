@@ -99,10 +99,15 @@ struct sf_plan_s {
   double2* adj_part = nullptr;  // kZGradBlocks x 5 partial sums
   double* adj_z = nullptr;      // n_views dL/dz values
   BatchState batch;
-  // host-output overlap: a copy stream and one event per view, created on first use
+  // host-output overlap, created on first use: a copy stream, one event per
+  // view, and the pipeline's x-pass stream (lowest priority) and y-pass
+  // stream (highest), with their fork / join and per-view x-pass events
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> view_done;
   cudaEvent_t copies_done = nullptr;
+  cudaStream_t pipe_x = nullptr, pipe_y = nullptr;
+  std::vector<cudaEvent_t> x_done;
+  cudaEvent_t pipe_fork = nullptr, pipe_join = nullptr, holo_half = nullptr;
   // execute's second compute stream (half of the views), created on first use
   cudaStream_t split_stream = nullptr;
   cudaEvent_t split_fork = nullptr, split_join = nullptr;
@@ -253,6 +258,11 @@ void free_plan(sf_plan p) {
   for (cudaEvent_t e : p->view_done) cudaEventDestroy(e);
   if (p->copies_done) cudaEventDestroy(p->copies_done);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  for (cudaEvent_t e : p->x_done) cudaEventDestroy(e);
+  for (cudaEvent_t e : {p->pipe_fork, p->pipe_join, p->holo_half})
+    if (e) cudaEventDestroy(e);
+  if (p->pipe_x) cudaStreamDestroy(p->pipe_x);
+  if (p->pipe_y) cudaStreamDestroy(p->pipe_y);
   if (p->split_fork) cudaEventDestroy(p->split_fork);
   if (p->split_join) cudaEventDestroy(p->split_join);
   if (p->split_stream) cudaStreamDestroy(p->split_stream);
@@ -316,6 +326,43 @@ int ensure_copy_resources(sf_plan p) {
   p->copy_stream = cs;
   p->view_done = ev;
   p->copies_done = done;
+  return SF_OK;
+}
+
+// Copy stream and events, plus the two pipeline streams of the host-output
+// path: x passes at the lowest stream priority, y passes at the highest, so a
+// view's y pass takes the SMs ahead of the next views' x passes and the
+// x passes fill the y pass's launch tail.
+int ensure_pipeline_resources(sf_plan p) {
+  int rc = ensure_copy_resources(p);
+  if (rc || p->pipe_x) return rc;
+  int least = 0, greatest = 0;
+  cudaStream_t xs = nullptr, ys = nullptr;
+  std::vector<cudaEvent_t> ev(p->views.size(), nullptr);
+  cudaEvent_t f = nullptr, j = nullptr, h = nullptr;
+  bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&xs, cudaStreamNonBlocking, least) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&ys, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+            cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h, cudaEventDisableTiming) == cudaSuccess;
+  for (size_t i = 0; ok && i < ev.size(); ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    for (cudaEvent_t x : {f, j, h})
+      if (x) cudaEventDestroy(x);
+    if (xs) cudaStreamDestroy(xs);
+    if (ys) cudaStreamDestroy(ys);
+    return SF_ERR_CUDA;
+  }
+  p->pipe_x = xs;
+  p->pipe_y = ys;
+  p->x_done = ev;
+  p->pipe_fork = f;
+  p->pipe_join = j;
+  p->holo_half = h;
   return SF_OK;
 }
 
@@ -542,10 +589,11 @@ bool persistent_eligible(sf_plan p, int L, PassKind kind, const PassBatch& b) {
 // with equal FFT length (at most max_per_launch views per launch).  Pass
 // sources: x reads `src` (the hologram) into work[v]; y reads work[v] into the
 // view outputs dout/dint/dph[v].  after(views, n) runs after each launch.
+// x pass only: rows [row0, row1) of the hologram (row1 < 0: to the end).
 template <typename After>
 cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* work, float2* const* dout,
                         float* const* dint, float* const* dph, int max_per_launch, cudaStream_t s, After&& after,
-                        const std::vector<int>* subset = nullptr) {
+                        const std::vector<int>* subset = nullptr, int row0 = 0, int row1 = -1) {
   std::vector<int> order;
   if (subset) {
     order = *subset;
@@ -574,9 +622,11 @@ cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* 
       d.n0 = c.n0;
       d.n1 = c.n1;
       if (axis == 0) {
-        d.src = src;
-        d.dst = work[vi];
-        d.rows = vs.v.ny0;
+        const int r0 = std::min(row0, vs.v.ny0), r1 = row1 < 0 ? vs.v.ny0 : std::min(row1, vs.v.ny0);
+        const size_t elem = plan->in_complex ? sizeof(float2) : sizeof(float);
+        d.src = static_cast<const char*>(src) + elem * (size_t)r0 * vs.v.nx0;
+        d.dst = work[vi] + r0;
+        d.rows = std::max(r1 - r0, 0);
         d.src_ld = vs.v.nx0;
         d.dst_ld = vs.v.ny0;
       } else {
@@ -1030,17 +1080,19 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
 
-  // hologram: device pointer used in place, host memory staged
-  const size_t holo_bytes = (plan->in_complex ? sizeof(float2) : sizeof(float)) * (size_t)plan->nx0 * plan->ny0;
+  // hologram: device pointer used in place, host memory staged (the copy is
+  // issued below, once the output placement fixes the schedule)
+  const size_t holo_elem = plan->in_complex ? sizeof(float2) : sizeof(float);
+  const size_t holo_bytes = holo_elem * (size_t)plan->nx0 * plan->ny0;
   const void* src = holo;
+  bool holo_host = false;
   switch (classify(holo, plan->device)) {
     case PTR_OTHER_DEVICE: return SF_ERR_DEVICE_MISMATCH;
     case PTR_HOST: {
       int rc = stage_alloc(plan, &plan->st_holo, holo_bytes);
       if (rc) return rc;
-      e = cudaMemcpyAsync(plan->st_holo, holo, holo_bytes, cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) { cudaGetLastError(); return SF_ERR_CUDA; }
       src = plan->st_holo;
+      holo_host = true;
       break;
     }
     default: break;
@@ -1078,11 +1130,30 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   // two streams, see below).  Host outputs: one view at a time, with its
   // copies to the host overlapping the following views' passes.
   const bool overlap = !d2h.empty();
+  const bool pipeline = overlap && !env_is("SF_EXECUTE_SINGLE_STREAM", "1");
   std::vector<float2*> work(nv);
   for (int i = 0; i < nv; ++i) work[i] = plan->views[i].work;
   if (overlap) {
-    int rc = ensure_copy_resources(plan);
+    int rc = pipeline ? ensure_pipeline_resources(plan) : ensure_copy_resources(plan);
     if (rc) return rc;
+  }
+  // The staged hologram goes in two halves when the pipeline below can start
+  // the first view's x pass on the first half (FP32 passes; the split row
+  // keeps the second half's rows 16-byte aligned).
+  int split_row = 0;
+  if (holo_host && pipeline && !plan->tc_frags && plan->ny0 >= 256 && holo_bytes >= ((size_t)1 << 20))
+    split_row = (plan->ny0 / 2) & ~15;
+  if (holo_host) {
+    const size_t b0 = split_row ? holo_elem * (size_t)split_row * plan->nx0 : holo_bytes;
+    e = cudaMemcpyAsync(plan->st_holo, holo, b0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && split_row) e = cudaEventRecord(plan->holo_half, s);
+    if (e == cudaSuccess && split_row)
+      e = cudaMemcpyAsync(static_cast<char*>(plan->st_holo) + b0, static_cast<const char*>(holo) + b0,
+                          holo_bytes - b0, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return SF_ERR_CUDA;
+    }
   }
   // Device outputs, no profiling events, two or more views: the views are
   // split into two halves of about equal work, each run (x pass, then y pass)
@@ -1123,25 +1194,60 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   }
 
   if (overlap) {
-    // Host outputs: view by view (x pass, y pass), each view's copies to the
-    // host starting on the copy stream as soon as its y pass is done, so the
-    // copies (the bound of this path) start after the first view instead of
-    // after every view's x pass.
+    // Host outputs: view by view, each view's copies to the host starting on
+    // the copy stream as soon as its y pass is done, so the copies (the bound
+    // of this path) start after the first view instead of after every view's
+    // x pass.  Pipelined (default): the x passes run in view order on the
+    // low-priority stream, the first one split at the hologram's halves
+    // (its first half starts while the second half is still being copied);
+    // each y pass waits for its view's x pass on the high-priority stream.
+    // With SF_EXECUTE_SINGLE_STREAM=1 both passes of every view run in turn
+    // on the caller's stream.
     auto none = [](const int*, int) { return cudaSuccess; };
+    cudaStream_t ys = pipeline ? plan->pipe_y : s;
     auto copies = [&](const int* views, int) -> cudaError_t {
       const int vi = views[0];
-      cudaError_t r = cudaEventRecord(plan->view_done[vi], s);
+      cudaError_t r = cudaEventRecord(plan->view_done[vi], ys);
       if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, plan->view_done[vi], 0);
       for (const Copy& c : d2h)
         if (r == cudaSuccess && c.view == vi)
           r = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
       return r;
     };
-    for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
-      const std::vector<int> one{vi};
-      e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, none, &one);
-      if (e == cudaSuccess)
-        e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, copies, &one);
+    if (pipeline) {
+      cudaStream_t xs = plan->pipe_x;
+      e = cudaEventRecord(plan->pipe_fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, split_row ? plan->holo_half : plan->pipe_fork, 0);
+      for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+        const std::vector<int> one{vi};
+        if (vi == 0 && split_row) {
+          e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, xs, none, &one, 0,
+                          split_row);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, plan->pipe_fork, 0);
+          if (e == cudaSuccess)
+            e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, xs, none, &one,
+                            split_row);
+        } else {
+          e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, xs, none, &one);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(plan->x_done[vi], xs);
+      }
+      for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+        const std::vector<int> one{vi};
+        e = cudaStreamWaitEvent(ys, plan->x_done[vi], 0);
+        if (e == cudaSuccess)
+          e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, ys, copies, &one);
+      }
+      // every x pass precedes some y pass, so the y stream's end covers both
+      if (e == cudaSuccess) e = cudaEventRecord(plan->pipe_join, ys);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->pipe_join, 0);
+    } else {
+      for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+        const std::vector<int> one{vi};
+        e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, none, &one);
+        if (e == cudaSuccess)
+          e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, copies, &one);
+      }
     }
   } else {
     if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);

@@ -174,6 +174,42 @@ def test_host_buffers_match_device_buffers(P):
         sf.close()
 
 
+@pytest.mark.parametrize("single_stream", [False, True])
+def test_host_pipeline_matches_device_buffers(P, single_stream, monkeypatch):
+    """Host hologram >= 1 MiB and host outputs: the pipelined schedule (x passes
+    on one stream, y passes on another, the first x pass split at the
+    hologram's halves, one on the persistent 4096-point kernel) and the
+    single-stream schedule give the device-buffer results bit for bit, over
+    repeated calls with different holograms and a mix of host and device
+    outputs."""
+    import torch
+    if single_stream:
+        monkeypatch.setenv("SF_EXECUTE_SINGLE_STREAM", "1")
+    ny0, nx0 = 512, 2000
+    views = [view(WAVELENGTH, 0.05, PITCH, 2e-6, o1=(1e-4, -2e-4), n0=(nx0, ny0), n1=(2000, 64)),  # x: L 4096
+             view(WAVELENGTH, -0.04, PITCH, PITCH, n0=(nx0, ny0), n1=(300, 500)),
+             view(WAVELENGTH, 0.08, PITCH, 7e-6, o1=(-3e-4, 0.0), n0=(nx0, ny0), n1=(33, 17))]
+    holos = [random_field(ny0, nx0, seed=40 + k).real.astype(np.float32) for k in range(2)]
+    refs = [run(P, views, h, phase=False) for h in holos]
+    sf = P.ShiftedFresnel(views)
+    try:
+        assert sf.sizes(0)[0] == 4096
+        s = torch.cuda.current_stream().cuda_stream
+        for k in (0, 1, 0):
+            h = torch.from_numpy(holos[k].copy()).pin_memory()
+            f = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64).pin_memory() for v in views]
+            f[2] = f[2].cuda()  # one view's field stays on the device
+            I = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.float32) for v in views]  # pageable
+            P.shifted_fresnel_execute(sf.handle, h.data_ptr(), [x.data_ptr() for x in f], [x.data_ptr() for x in I],
+                                      None, stream=s)
+            torch.cuda.synchronize()
+            for i in range(len(views)):
+                assert np.array_equal(f[i].cpu().numpy(), refs[k]["field"][i]), (k, i)
+                assert np.array_equal(I[i].numpy(), refs[k]["intensity"][i]), (k, i)
+    finally:
+        sf.close()
+
+
 def test_repeat_execute_is_deterministic(P):
     import torch
     holo, views = synth.config_c1()
