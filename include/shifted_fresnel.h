@@ -116,17 +116,22 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
  * Each of holo and the output buffers may be device memory or host memory
  * (pinned or pageable).  Host buffers are staged through plan-owned device
  * buffers that the first call with a host buffer allocates.  With host
- * outputs the views run one at a time (x pass, then y pass) and each view's
- * copies to the host start on a plan-owned copy stream as soon as that view
- * is done, overlapping the following views; the caller's stream waits for
- * the last copy, so the caller synchronises its stream before reading host
- * outputs.  Every view needs at least one non-NULL output.
+ * outputs each view's copies to the host start on a plan-owned copy stream
+ * as soon as that view is done, overlapping the following views; the views'
+ * x passes run in order on a plan-owned stream of the lowest priority and
+ * each y pass, after its x pass, on one of the highest, and a host hologram
+ * of at least 1 MiB and 256 rows is copied in two halves, the first view's
+ * x pass starting on the first half (FP32 plans).  The caller's stream waits
+ * for the last copy, so the caller synchronises its stream before reading
+ * host outputs.  Every view needs at least one non-NULL output.
  * With device outputs and two or more views, the views are split into two
  * halves of about equal work run on `stream` and on a plan-owned second
  * stream (x pass then y pass each), so one half's y pass overlaps the other's
  * x pass; `stream` waits for both before the call's work is complete.
- * SF_EXECUTE_SINGLE_STREAM=1, or profiling events set with
- * shifted_fresnel_set_profile_events, keeps everything on `stream`.
+ * SF_EXECUTE_SINGLE_STREAM=1 keeps every pass on `stream` (with host
+ * outputs: both passes of each view in turn, copies still on the copy
+ * stream); so do profiling events set with shifted_fresnel_set_profile_events
+ * when every output is device memory.
  * Implementation: each pass runs a one-tile-per-CTA kernel, or, where the
  * plan chose it (by default at FFT length 4096; SF_PASS_IMPL or the
  * autotuner, see shifted_fresnel_fft_length) and the rows' address, stride
