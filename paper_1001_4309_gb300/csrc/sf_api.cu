@@ -107,7 +107,7 @@ struct sf_plan_s {
   cudaEvent_t copies_done = nullptr;
   cudaStream_t pipe_x = nullptr, pipe_y = nullptr;
   std::vector<cudaEvent_t> x_done;
-  cudaEvent_t pipe_fork = nullptr, pipe_join = nullptr, holo_half = nullptr;
+  cudaEvent_t pipe_fork = nullptr, pipe_join = nullptr, holo_half = nullptr, y_half = nullptr;
   // execute's second compute stream (half of the views), created on first use
   cudaStream_t split_stream = nullptr;
   cudaEvent_t split_fork = nullptr, split_join = nullptr;
@@ -259,7 +259,7 @@ void free_plan(sf_plan p) {
   if (p->copies_done) cudaEventDestroy(p->copies_done);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   for (cudaEvent_t e : p->x_done) cudaEventDestroy(e);
-  for (cudaEvent_t e : {p->pipe_fork, p->pipe_join, p->holo_half})
+  for (cudaEvent_t e : {p->pipe_fork, p->pipe_join, p->holo_half, p->y_half})
     if (e) cudaEventDestroy(e);
   if (p->pipe_x) cudaStreamDestroy(p->pipe_x);
   if (p->pipe_y) cudaStreamDestroy(p->pipe_y);
@@ -339,19 +339,20 @@ int ensure_pipeline_resources(sf_plan p) {
   int least = 0, greatest = 0;
   cudaStream_t xs = nullptr, ys = nullptr;
   std::vector<cudaEvent_t> ev(p->views.size(), nullptr);
-  cudaEvent_t f = nullptr, j = nullptr, h = nullptr;
+  cudaEvent_t f = nullptr, j = nullptr, h = nullptr, yh = nullptr;
   bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
             cudaStreamCreateWithPriority(&xs, cudaStreamNonBlocking, least) == cudaSuccess &&
             cudaStreamCreateWithPriority(&ys, cudaStreamNonBlocking, greatest) == cudaSuccess &&
             cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&h, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&h, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&yh, cudaEventDisableTiming) == cudaSuccess;
   for (size_t i = 0; ok && i < ev.size(); ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     for (cudaEvent_t x : ev)
       if (x) cudaEventDestroy(x);
-    for (cudaEvent_t x : {f, j, h})
+    for (cudaEvent_t x : {f, j, h, yh})
       if (x) cudaEventDestroy(x);
     if (xs) cudaStreamDestroy(xs);
     if (ys) cudaStreamDestroy(ys);
@@ -363,6 +364,7 @@ int ensure_pipeline_resources(sf_plan p) {
   p->pipe_fork = f;
   p->pipe_join = j;
   p->holo_half = h;
+  p->y_half = yh;
   return SF_OK;
 }
 
@@ -589,7 +591,8 @@ bool persistent_eligible(sf_plan p, int L, PassKind kind, const PassBatch& b) {
 // with equal FFT length (at most max_per_launch views per launch).  Pass
 // sources: x reads `src` (the hologram) into work[v]; y reads work[v] into the
 // view outputs dout/dint/dph[v].  after(views, n) runs after each launch.
-// x pass only: rows [row0, row1) of the hologram (row1 < 0: to the end).
+// Rows [row0, row1) of each pass only (row1 < 0: to the end): hologram rows
+// on the x pass, view columns on the y pass.
 template <typename After>
 cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* work, float2* const* dout,
                         float* const* dint, float* const* dph, int max_per_launch, cudaStream_t s, After&& after,
@@ -630,11 +633,13 @@ cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* 
         d.src_ld = vs.v.nx0;
         d.dst_ld = vs.v.ny0;
       } else {
-        d.src = work[vi];
-        d.dst = dout[vi];
-        d.inten = dint[vi];
-        d.phase = dph[vi];
-        d.rows = vs.v.nx1;
+        // y-pass row r is column r of the view
+        const int r0 = std::min(row0, vs.v.nx1), r1 = row1 < 0 ? vs.v.nx1 : std::min(row1, vs.v.nx1);
+        d.src = work[vi] + (size_t)r0 * vs.v.ny0;
+        d.dst = dout[vi] ? dout[vi] + r0 : nullptr;
+        d.inten = dint[vi] ? dint[vi] + r0 : nullptr;
+        d.phase = dph[vi] ? dph[vi] + r0 : nullptr;
+        d.rows = std::max(r1 - r0, 0);
         d.src_ld = vs.v.ny0;
         d.dst_ld = vs.v.nx1;
       }
@@ -1099,7 +1104,7 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   }
 
   // outputs: resolve staging for host buffers
-  struct Copy { void* dst; const void* src; size_t bytes; int view; };
+  struct Copy { void* dst; const void* src; size_t bytes; int view; size_t elem; };
   std::vector<Copy> d2h;
   std::vector<float2*> dout(nv, nullptr);
   std::vector<float*> dint(nv, nullptr), dph(nv, nullptr);
@@ -1113,7 +1118,7 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
         case PTR_HOST: {
           int rc = stage_alloc(plan, stage, bytes);
           if (rc) return rc;
-          d2h.push_back({user, *stage, bytes, i});
+          d2h.push_back({user, *stage, bytes, i, bytes / npx});
           *dev = *stage;
           return SF_OK;
         }
@@ -1214,6 +1219,19 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
           r = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
       return r;
     };
+    // Columns [c0, c1) of view vi's host outputs, once the y pass so far is
+    // done (one 2-D copy per output: ny1 rows of (c1 - c0) elements).
+    auto column_copies = [&](int vi, int c0, int c1, cudaEvent_t ev) -> cudaError_t {
+      const size_t ld = (size_t)plan->views[vi].v.nx1;
+      cudaError_t r = cudaEventRecord(ev, ys);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, ev, 0);
+      for (const Copy& c : d2h)
+        if (r == cudaSuccess && c.view == vi)
+          r = cudaMemcpy2DAsync(static_cast<char*>(c.dst) + c.elem * c0, c.elem * ld,
+                                static_cast<const char*>(c.src) + c.elem * c0, c.elem * ld, c.elem * (c1 - c0),
+                                (size_t)plan->views[vi].v.ny1, cudaMemcpyDeviceToHost, plan->copy_stream);
+      return r;
+    };
     if (pipeline) {
       cudaStream_t xs = plan->pipe_x;
       e = cudaEventRecord(plan->pipe_fork, s);
@@ -1232,11 +1250,27 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
         }
         if (e == cudaSuccess) e = cudaEventRecord(plan->x_done[vi], xs);
       }
+      // The first and the last view's y pass run in two column halves, each
+      // followed by its copies, so the copies start half a pass earlier and
+      // the last ones end half a pass sooner (FP32 plans, views of >= 256
+      // columns; the split column keeps rows of the intermediate 16-byte
+      // aligned).
       for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
         const std::vector<int> one{vi};
+        const int nx1 = plan->views[vi].v.nx1;
+        const int half = (vi == 0 || vi == nv - 1) && !plan->tc_frags && nx1 >= 256 ? (nx1 / 2) & ~15 : 0;
         e = cudaStreamWaitEvent(ys, plan->x_done[vi], 0);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && half) {
+          e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, ys, none, &one, 0,
+                          half);
+          if (e == cudaSuccess) e = column_copies(vi, 0, half, plan->y_half);
+          if (e == cudaSuccess)
+            e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, ys, none, &one,
+                            half);
+          if (e == cudaSuccess) e = column_copies(vi, half, nx1, plan->view_done[vi]);
+        } else if (e == cudaSuccess) {
           e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, ys, copies, &one);
+        }
       }
       // every x pass precedes some y pass, so the y stream's end covers both
       if (e == cudaSuccess) e = cudaEventRecord(plan->pipe_join, ys);

@@ -178,17 +178,18 @@ def test_host_buffers_match_device_buffers(P):
 def test_host_pipeline_matches_device_buffers(P, single_stream, monkeypatch):
     """Host hologram >= 1 MiB and host outputs: the pipelined schedule (x passes
     on one stream, y passes on another, the first x pass split at the
-    hologram's halves, one on the persistent 4096-point kernel) and the
+    hologram's halves, one on the persistent 4096-point kernel, the first and
+    last views' y passes in column halves with 2-D copies) and the
     single-stream schedule give the device-buffer results bit for bit, over
-    repeated calls with different holograms and a mix of host and device
-    outputs."""
+    repeated calls with different holograms and a mix of host (pinned and
+    pageable) and device outputs."""
     import torch
     if single_stream:
         monkeypatch.setenv("SF_EXECUTE_SINGLE_STREAM", "1")
     ny0, nx0 = 512, 2000
     views = [view(WAVELENGTH, 0.05, PITCH, 2e-6, o1=(1e-4, -2e-4), n0=(nx0, ny0), n1=(2000, 64)),  # x: L 4096
-             view(WAVELENGTH, -0.04, PITCH, PITCH, n0=(nx0, ny0), n1=(300, 500)),
-             view(WAVELENGTH, 0.08, PITCH, 7e-6, o1=(-3e-4, 0.0), n0=(nx0, ny0), n1=(33, 17))]
+             view(WAVELENGTH, 0.08, PITCH, 7e-6, o1=(-3e-4, 0.0), n0=(nx0, ny0), n1=(33, 17)),
+             view(WAVELENGTH, -0.04, PITCH, PITCH, n0=(nx0, ny0), n1=(300, 500))]
     holos = [random_field(ny0, nx0, seed=40 + k).real.astype(np.float32) for k in range(2)]
     refs = [run(P, views, h, phase=False) for h in holos]
     sf = P.ShiftedFresnel(views)
