@@ -47,6 +47,8 @@ struct BatchState {
   int n_holos = 0;                       // hologram count the graphs are built for
   std::vector<BatchGroup> groups;
   int items_per_holo = 0, grid = 0;
+  const void* kfunc = nullptr;           // persistent kernel: general, or specialised to one length
+  size_t ksmem = 0;                      // its dynamic shared memory
   std::vector<float2*> slot1;            // second intermediate slot per view
   BatchGroup* d_groups = nullptr;
   int* d_error = nullptr;
@@ -481,12 +483,20 @@ int batch_prepare(sf_plan p, int n_holos, bool persistent) {
     if (cudaMemcpy(b.d_groups, b.groups.data(), sizeof(BatchGroup) * b.groups.size(), cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return SF_ERR_CUDA;
+    // One power-of-two length on every pass of every view, all prunable: the
+    // specialised kernel (SF_BATCH_GENERAL=1 keeps the general one).
+    const PassKind kx = p->in_complex ? PASS_X_CPLX : PASS_X_REAL;
+    const int L1 = p->views[0].ax[0].L;
+    bool one = !env_is("SF_BATCH_GENERAL", "1") && batch_kernel_one(kx, L1) != nullptr;
+    for (const ViewState& vs : p->views)
+      for (int ph = 0; ph < 2 && one; ++ph)
+        one = vs.ax[ph].L == L1 && 2 * vs.ax[ph].n0 <= L1 && 2 * vs.ax[ph].n1 <= L1;
+    b.kfunc = one ? batch_kernel_one(kx, L1) : batch_kernel(kx);
+    b.ksmem = one ? batch_smem_bytes_one(L1) : batch_smem_bytes();
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    for (PassKind k : {PASS_X_REAL, PASS_X_CPLX})
-      cudaFuncSetAttribute(batch_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(p->in_complex ? PASS_X_CPLX : PASS_X_REAL),
-                                                      kBatchThreads, batch_smem_bytes()) != cudaSuccess ||
+    cudaFuncSetAttribute(b.kfunc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.ksmem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.kfunc, kBatchThreads, b.ksmem) != cudaSuccess ||
         per_sm < 1)
       return SF_ERR_CUDA;
     b.grid = sms * per_sm;
@@ -556,10 +566,10 @@ int batch_prepare(sf_plan p, int n_holos, bool persistent) {
     cudaKernelNodeParams kp;
     std::memset(&kp, 0, sizeof(kp));
     void* kargs[] = {&args};
-    kp.func = const_cast<void*>(batch_kernel(p->in_complex ? PASS_X_CPLX : PASS_X_REAL));
+    kp.func = const_cast<void*>(b.kfunc);
     kp.gridDim = dim3(b.grid);
     kp.blockDim = dim3(kBatchThreads);
-    kp.sharedMemBytes = (unsigned)batch_smem_bytes();
+    kp.sharedMemBytes = (unsigned)b.ksmem;
     kp.kernelParams = kargs;
     cudaGraphNode_t deps[2] = {cp, ms};
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&kn, b.graph[k], deps, 2, &kp);

@@ -49,6 +49,10 @@ int batch_tile_rows(int L);
 int batch_item_tiles(int L);
 size_t batch_smem_bytes();
 const void* batch_kernel(PassKind kind_x);
+// The batch kernel specialised to one power-of-two length (512 .. 4096) with
+// every pass prunable (sf_batch_one.cu); nullptr / 0 for other lengths.
+const void* batch_kernel_one(PassKind kind_x, int L);
+size_t batch_smem_bytes_one(int L);
 
 // Persistent row pass with TMA row prefetch (sf_persist.cu)
 struct PersistArgs {

@@ -131,6 +131,40 @@ def test_batch_paper_sized_ragged_views(P, impl, monkeypatch):
         sf.close()
 
 
+@pytest.mark.parametrize("general", [False, True])
+def test_batch_one_length_kernel(P, general, monkeypatch):
+    """Every pass at one power-of-two length with n0, n1 <= L / 2: the persistent
+    batch runs the kernel specialised to that length (pruned network), bit for
+    bit equal to per-hologram execute; SF_BATCH_GENERAL=1 keeps the general
+    kernel (unpruned network: equal up to rounding)."""
+    import torch
+    monkeypatch.setenv("SF_BATCH_IMPL", "persistent")
+    if general:
+        monkeypatch.setenv("SF_BATCH_GENERAL", "1")
+    n = 512
+    rng = np.random.default_rng(5)
+    vs = [view(WAVELENGTH, z, PITCH, p1, o1=tuple(rng.uniform(-5e-4, 5e-4, size=2)), n0=(n, n), n1=(n1x, n1y))
+          for z, p1, n1x, n1y in ((0.03, 4.65e-6, 512, 512), (0.05, 2e-6, 512, 400), (0.07, 1e-6, 300, 512),
+                                  (0.1, 0.5e-6, 512, 512))]
+    sf = P.ShiftedFresnel(vs)
+    try:
+        assert all(sf.sizes(i)[:2] == (1024, 1024) for i in range(len(vs)))
+        holos = holograms(5, shape=(n, n), seed=60)
+        ref = per_hologram(sf, holos)
+        outs = sf.alloc_batch_outputs(5, field=True, intensity=True)
+        for _ in range(2):
+            sf.execute_batch(holos, outs)
+            assert P.shifted_fresnel_batch_status(sf.handle, torch.cuda.current_stream().cuda_stream) == P.SF_OK
+            if general:
+                for h, (f_ref, _) in enumerate(ref):
+                    for v in range(len(vs)):
+                        assert rel_l2(outs["field"][h][v].cpu().numpy(), f_ref[v].cpu().numpy()) <= 1e-6
+            else:
+                check_equal(outs, ref)
+    finally:
+        sf.close()
+
+
 def test_batch_rejects_bad_arguments(P):
     import torch
     vs = ragged_views()[:2]
