@@ -156,7 +156,12 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
  *               for the y pass of hologram h - 2 (two intermediate slots per
  *               view).  The waits are bounded; if one expires the launch
  *               ends early and shifted_fresnel_batch_status reports
- *               SF_ERR_TIMEOUT.  FFT lengths up to 6144.
+ *               SF_ERR_TIMEOUT.  FFT lengths up to 6144.  When every pass of
+ *               every view has one power-of-two length 512 .. 4096 and
+ *               n0, n1 <= L / 2, a kernel specialised to that length (with
+ *               the pruned network) runs instead of the general one
+ *               (SF_BATCH_GENERAL=1, read when the plan's batch state is
+ *               first built, keeps the general kernel).
  *   streams     execute's per-length row-pass kernels, even holograms on one
  *               plan-owned stream and odd ones on another (one intermediate
  *               slot each), joined back into `stream`; consecutive holograms
