@@ -118,3 +118,16 @@ def test_fft_length_choice_without_gpu():
         assert p2 >= need and p2 & (p2 - 1) == 0 and p2 // 2 < max(need, 64)
     assert fl(0) == SF_ERR_INVALID_ARG
     assert fl(8193) == SF_ERR_UNSUPPORTED_SIZE
+
+
+def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library every entry point raises."""
+    from paper_1001_4309_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        binding.load()
+    with pytest.raises(RuntimeError, match="missing"):
+        binding.shifted_fresnel_plan([base_view()])
+    with pytest.raises(RuntimeError, match="missing"):
+        binding.shifted_fresnel_fft_length(2047)
