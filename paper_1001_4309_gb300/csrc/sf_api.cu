@@ -1082,6 +1082,19 @@ int shifted_fresnel_plan_query(sf_plan plan, int view, int32_t* lx, int32_t* ly,
   return SF_OK;
 }
 
+namespace sf {
+namespace {
+// After a failed enqueue: make `s` wait for whatever the call already put on
+// plan-owned stream `other`, so later work on `s` stays ordered after it
+// (best effort; errors here are cleared).
+void join_after_error(cudaStream_t s, cudaStream_t other, cudaEvent_t ev) {
+  cudaGetLastError();
+  if (other && ev && cudaEventRecord(ev, other) == cudaSuccess) cudaStreamWaitEvent(s, ev, 0);
+  cudaGetLastError();
+}
+}  // namespace
+}  // namespace sf
+
 int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out, float* const* intensity,
                             float* const* phase, void* stream) {
   if (!plan || !holo) return SF_ERR_INVALID_ARG;
@@ -1202,7 +1215,7 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
     if (e == cudaSuccess) e = cudaEventRecord(plan->split_join, plan->split_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->split_join, 0);
     if (e != cudaSuccess) {
-      cudaGetLastError();
+      join_after_error(s, plan->split_stream, plan->split_join);
       return SF_ERR_CUDA;
     }
     return SF_OK;
@@ -1309,7 +1322,11 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->copies_done, 0);
   }
   if (e != cudaSuccess) {
-    cudaGetLastError();
+    if (pipeline) {
+      join_after_error(s, plan->pipe_x, plan->pipe_fork);
+      join_after_error(s, plan->pipe_y, plan->pipe_join);
+    }
+    if (overlap) join_after_error(s, plan->copy_stream, plan->copies_done);
     return SF_ERR_CUDA;
   }
   return SF_OK;
