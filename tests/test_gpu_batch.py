@@ -131,25 +131,31 @@ def test_batch_paper_sized_ragged_views(P, impl, monkeypatch):
         sf.close()
 
 
-@pytest.mark.parametrize("general", [False, True])
-def test_batch_one_length_kernel(P, general, monkeypatch):
+@pytest.mark.parametrize("general,cplx", [(False, False), (True, False), (False, True)])
+def test_batch_one_length_kernel(P, general, cplx, monkeypatch):
     """Every pass at one power-of-two length with n0, n1 <= L / 2: the persistent
     batch runs the kernel specialised to that length (pruned network), bit for
-    bit equal to per-hologram execute; SF_BATCH_GENERAL=1 keeps the general
-    kernel (unpruned network: equal up to rounding)."""
+    bit equal to per-hologram execute, for real and complex holograms;
+    SF_BATCH_GENERAL=1 keeps the general kernel (unpruned network: equal up to
+    rounding)."""
     import torch
     monkeypatch.setenv("SF_BATCH_IMPL", "persistent")
     if general:
         monkeypatch.setenv("SF_BATCH_GENERAL", "1")
     n = 512
     rng = np.random.default_rng(5)
-    vs = [view(WAVELENGTH, z, PITCH, p1, o1=tuple(rng.uniform(-5e-4, 5e-4, size=2)), n0=(n, n), n1=(n1x, n1y))
+    flags = P.SF_IN_COMPLEX if cplx else 0
+    vs = [view(WAVELENGTH, z, PITCH, p1, o1=tuple(rng.uniform(-5e-4, 5e-4, size=2)), n0=(n, n), n1=(n1x, n1y),
+               flags=flags)
           for z, p1, n1x, n1y in ((0.03, 4.65e-6, 512, 512), (0.05, 2e-6, 512, 400), (0.07, 1e-6, 300, 512),
                                   (0.1, 0.5e-6, 512, 512))]
     sf = P.ShiftedFresnel(vs)
     try:
         assert all(sf.sizes(i)[:2] == (1024, 1024) for i in range(len(vs)))
-        holos = holograms(5, shape=(n, n), seed=60)
+        if cplx:
+            holos = [torch.from_numpy(random_field(n, n, seed=60 + h).astype(np.complex64)).cuda() for h in range(5)]
+        else:
+            holos = holograms(5, shape=(n, n), seed=60)
         ref = per_hologram(sf, holos)
         outs = sf.alloc_batch_outputs(5, field=True, intensity=True)
         for _ in range(2):
