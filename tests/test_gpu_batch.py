@@ -127,6 +127,15 @@ def test_batch_paper_sized_ragged_views(P, impl, monkeypatch):
         sf.execute_batch(holos, outs)
         torch.cuda.synchronize()
         check_equal(outs, ref)
+        # full-size parity against the oracle on sampled columns (first, middle, last block) of every size
+        h_np = holos[2].cpu().numpy()
+        for v_i, v in enumerate(vs):
+            got = outs["field"][2][v_i].cpu().numpy()
+            n = v["nx1"]
+            for c0 in (0, n // 2 - 2, n - 4):
+                cols = (c0, c0 + 4)
+                err = rel_l2(got[:, cols[0]:cols[1]], oracle.forward(h_np, v, cols=cols))
+                assert err <= 1e-5, (v["nx1"], cols, err)
     finally:
         sf.close()
 
