@@ -26,9 +26,9 @@ __device__ __forceinline__ double coord(int m, int n, double p, double o) { retu
 // xg = x1(m1) g, yg = y1(n1) g over the view grid.
 __global__ void k_weight_xy(const float2* __restrict__ g, float2* __restrict__ xg, float2* __restrict__ yg,
                             int nx1, int ny1, double px1, double py1, double ox1, double oy1) {
-  const size_t n = (size_t)nx1 * ny1;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int m1 = (int)(i % nx1), n1 = (int)(i / nx1);
+  const unsigned n = (unsigned)nx1 * (unsigned)ny1;  // < 2^31
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int n1 = (int)(i / (unsigned)nx1), m1 = (int)(i - (unsigned)n1 * (unsigned)nx1);
     const float x1 = (float)coord(m1, nx1, px1, ox1), y1 = (float)coord(n1, ny1, py1, oy1);
     const float2 v = g[i];
     xg[i] = make_float2(x1 * v.x, x1 * v.y);
@@ -51,19 +51,20 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(256) k_zgrad_partial(const ZGradArgs a, double2* __restrict__ partials) {
   double2 s[5];
   for (int k = 0; k < 5; ++k) s[k] = make_double2(0.0, 0.0);
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  const size_t n1 = (size_t)a.nx1 * a.ny1;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n1; i += stride) {
-    const int m = (int)(i % a.nx1), n = (int)(i / a.nx1);
+  // grids are at most 8192 x 8192 (< 2^31 elements): 32-bit index arithmetic
+  const unsigned stride = gridDim.x * blockDim.x;
+  const unsigned n1 = (unsigned)a.nx1 * (unsigned)a.ny1;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride) {
+    const int n = (int)(i / (unsigned)a.nx1), m = (int)(i - (unsigned)n * (unsigned)a.nx1);
     const double x1 = coord(m, a.nx1, a.px1, a.ox1), y1 = coord(n, a.ny1, a.py1, a.oy1);
     const float2 u = a.u1[i];
     const double2 ud = make_double2(u.x, u.y);
     cacc(s[0], a.g[i], ud, 1.0);
     cacc(s[1], a.g[i], ud, x1 * x1 + y1 * y1);
   }
-  const size_t n0 = (size_t)a.nx0 * a.ny0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n0; i += stride) {
-    const int m = (int)(i % a.nx0), n = (int)(i / a.nx0);
+  const unsigned n0 = (unsigned)a.nx0 * (unsigned)a.ny0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += stride) {
+    const int n = (int)(i / (unsigned)a.nx0), m = (int)(i - (unsigned)n * (unsigned)a.nx0);
     const double x0 = coord(m, a.nx0, a.px0, a.ox0), y0 = coord(n, a.ny0, a.py0, a.oy0);
     double2 u;
     if (a.u0_complex) {
@@ -94,20 +95,24 @@ __global__ void __launch_bounds__(256) k_zgrad_partial(const ZGradArgs a, double
   }
 }
 
-// Sum the partials in block order and form dL/dz.
+// Sum the partials in block order and form dL/dz: thread j < 10 sums the
+// real (even j) or imaginary (odd j) part of inner product j / 2.
 __global__ void k_zgrad_final(const double2* __restrict__ partials, int n_partials, double* out, double c_re,
                               double c_im, double q_re, double q_im) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double2 s[5];
-  for (int k = 0; k < 5; ++k) s[k] = make_double2(0.0, 0.0);
-  for (int b = 0; b < n_partials; ++b)
-    for (int k = 0; k < 5; ++k) {
-      s[k].x += partials[(size_t)b * 5 + k].x;
-      s[k].y += partials[(size_t)b * 5 + k].y;
-    }
-  const double tr = s[1].x - 2.0 * s[2].x - 2.0 * s[3].x + s[4].x;
-  const double ti = s[1].y - 2.0 * s[2].y - 2.0 * s[3].y + s[4].y;
-  *out = (c_re * s[0].x - c_im * s[0].y) + (q_re * tr - q_im * ti);
+  __shared__ double t[10];
+  const int j = threadIdx.x;
+  if (blockIdx.x != 0) return;
+  if (j < 10) {
+    const double* p = reinterpret_cast<const double*>(partials) + j;
+    double acc = 0.0;
+    for (int b = 0; b < n_partials; ++b) acc += p[(size_t)b * 10];
+    t[j] = acc;
+  }
+  __syncthreads();
+  if (j != 0) return;
+  const double tr = t[2] - 2.0 * t[4] - 2.0 * t[6] + t[8];
+  const double ti = t[3] - 2.0 * t[5] - 2.0 * t[7] + t[9];
+  *out = (c_re * t[0] - c_im * t[1]) + (q_re * tr - q_im * ti);
 }
 
 __global__ void k_axpy(float2* __restrict__ y, const float2* __restrict__ x, size_t n, int accumulate) {
