@@ -1095,6 +1095,170 @@ void join_after_error(cudaStream_t s, cudaStream_t other, cudaEvent_t ev) {
 }  // namespace
 }  // namespace sf
 
+namespace {
+
+// Buffers of one execute call once host memory is resolved to staging.
+struct ExecBuffers {
+  struct Copy { void* dst; const void* src; size_t bytes; int view; size_t elem; };
+  const void* src = nullptr;               // hologram on the device
+  std::vector<float2*> work, dout;         // per view: intermediate, complex output (or null)
+  std::vector<float*> dint, dph;           // per view: intensity, phase (or null)
+  std::vector<Copy> d2h;                   // staged host outputs, copied back per view
+};
+
+// Device outputs, two or more views: the views are split into two halves of
+// about equal work, each run (x pass, then y pass) on its own stream, so one
+// half's y pass overlaps the other's x pass.
+cudaError_t execute_split_halves(sf_plan plan, const ExecBuffers& io, cudaStream_t s) {
+  const int nv = (int)plan->views.size();
+  std::vector<int> order(nv), half[2];
+  double load[2] = {0, 0};
+  for (int i = 0; i < nv; ++i) order[i] = i;
+  auto cost = [&](int v) {
+    const ViewState& vs = plan->views[v];
+    return (double)vs.v.ny0 * vs.ax[0].L + (double)vs.v.nx1 * vs.ax[1].L;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  for (int v : order) {
+    const int k = load[1] < load[0] ? 1 : 0;
+    half[k].push_back(v);
+    load[k] += cost(v);
+  }
+  for (int k = 0; k < 2; ++k) std::sort(half[k].begin(), half[k].end());
+  auto none = [](const int*, int) { return cudaSuccess; };
+  cudaError_t e = cudaEventRecord(plan->split_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->split_stream, plan->split_fork, 0);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    cudaStream_t cs = k == 0 ? s : plan->split_stream;
+    for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis)
+      e = launch_axis(plan, axis, io.src, io.work.data(), io.dout.data(), io.dint.data(), io.dph.data(),
+                      kMaxPassBatch, cs, none, &half[k]);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(plan->split_join, plan->split_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->split_join, 0);
+  if (e != cudaSuccess) join_after_error(s, plan->split_stream, plan->split_join);
+  return e;
+}
+
+// Host outputs: view by view, each view's copies to the host starting on the
+// copy stream as soon as its y pass is done, so the copies (the bound of this
+// path) start after the first view instead of after every view's x pass.
+// Pipelined (default): the x passes run in view order on the low-priority
+// stream, the first one split at row split_row of the hologram when that is
+// nonzero (its first half starts while the second half is still being
+// copied); each y pass waits for its view's x pass on the high-priority
+// stream, the first and the last view's in two column halves.  Otherwise both
+// passes of every view run in turn on `s`.  `s` ends after the last copy.
+cudaError_t execute_host_outputs(sf_plan plan, const ExecBuffers& io, bool pipeline, int split_row,
+                                 cudaStream_t s) {
+  const int nv = (int)plan->views.size();
+  auto none = [](const int*, int) { return cudaSuccess; };
+  cudaStream_t ys = pipeline ? plan->pipe_y : s;
+  auto copies = [&](const int* views, int) -> cudaError_t {
+    const int vi = views[0];
+    cudaError_t r = cudaEventRecord(plan->view_done[vi], ys);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, plan->view_done[vi], 0);
+    for (const ExecBuffers::Copy& c : io.d2h)
+      if (r == cudaSuccess && c.view == vi)
+        r = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
+    return r;
+  };
+  // Columns [c0, c1) of view vi's host outputs, once the y pass so far is
+  // done (one 2-D copy per output: ny1 rows of (c1 - c0) elements).
+  auto column_copies = [&](int vi, int c0, int c1, cudaEvent_t ev) -> cudaError_t {
+    const size_t ld = (size_t)plan->views[vi].v.nx1;
+    cudaError_t r = cudaEventRecord(ev, ys);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, ev, 0);
+    for (const ExecBuffers::Copy& c : io.d2h)
+      if (r == cudaSuccess && c.view == vi)
+        r = cudaMemcpy2DAsync(static_cast<char*>(c.dst) + c.elem * c0, c.elem * ld,
+                              static_cast<const char*>(c.src) + c.elem * c0, c.elem * ld, c.elem * (c1 - c0),
+                              (size_t)plan->views[vi].v.ny1, cudaMemcpyDeviceToHost, plan->copy_stream);
+    return r;
+  };
+  auto x_pass = [&](int vi, cudaStream_t st, int r0, int r1) {
+    const std::vector<int> one{vi};
+    return launch_axis(plan, 0, io.src, io.work.data(), io.dout.data(), io.dint.data(), io.dph.data(), 1, st, none,
+                       &one, r0, r1);
+  };
+  auto y_pass = [&](int vi, int r0, int r1, bool with_copies) {
+    const std::vector<int> one{vi};
+    return with_copies ? launch_axis(plan, 1, io.src, io.work.data(), io.dout.data(), io.dint.data(),
+                                     io.dph.data(), 1, ys, copies, &one, r0, r1)
+                       : launch_axis(plan, 1, io.src, io.work.data(), io.dout.data(), io.dint.data(),
+                                     io.dph.data(), 1, ys, none, &one, r0, r1);
+  };
+  cudaError_t e = cudaSuccess;
+  if (pipeline) {
+    cudaStream_t xs = plan->pipe_x;
+    e = cudaEventRecord(plan->pipe_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, split_row ? plan->holo_half : plan->pipe_fork, 0);
+    for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+      if (vi == 0 && split_row) {
+        e = x_pass(vi, xs, 0, split_row);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, plan->pipe_fork, 0);
+        if (e == cudaSuccess) e = x_pass(vi, xs, split_row, -1);
+      } else {
+        e = x_pass(vi, xs, 0, -1);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(plan->x_done[vi], xs);
+    }
+    // The first and the last view's y pass run in two column halves, each
+    // followed by its copies (FP32 plans, views of >= 256 columns; the split
+    // column keeps rows of the intermediate 16-byte aligned).
+    for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+      const int nx1 = plan->views[vi].v.nx1;
+      const int half = (vi == 0 || vi == nv - 1) && !plan->tc_frags && nx1 >= 256 ? (nx1 / 2) & ~15 : 0;
+      e = cudaStreamWaitEvent(ys, plan->x_done[vi], 0);
+      if (e == cudaSuccess && half) {
+        e = y_pass(vi, 0, half, false);
+        if (e == cudaSuccess) e = column_copies(vi, 0, half, plan->y_half);
+        if (e == cudaSuccess) e = y_pass(vi, half, -1, false);
+        if (e == cudaSuccess) e = column_copies(vi, half, nx1, plan->view_done[vi]);
+      } else if (e == cudaSuccess) {
+        e = y_pass(vi, 0, -1, true);
+      }
+    }
+    // every x pass precedes some y pass, so the y stream's end covers both
+    if (e == cudaSuccess) e = cudaEventRecord(plan->pipe_join, ys);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->pipe_join, 0);
+  } else {
+    for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
+      e = x_pass(vi, s, 0, -1);
+      if (e == cudaSuccess) e = y_pass(vi, 0, -1, true);
+    }
+  }
+  // the caller's stream resumes after the last copy
+  if (e == cudaSuccess) e = cudaEventRecord(plan->copies_done, plan->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->copies_done, 0);
+  if (e != cudaSuccess) {
+    if (pipeline) {
+      join_after_error(s, plan->pipe_x, plan->pipe_fork);
+      join_after_error(s, plan->pipe_y, plan->pipe_join);
+    }
+    join_after_error(s, plan->copy_stream, plan->copies_done);
+  }
+  return e;
+}
+
+// Device outputs on `s` alone: every view's x pass, then every y pass, each
+// grouped by FFT length; profiling events (when attached) bracket the passes.
+cudaError_t execute_single_stream(sf_plan plan, const ExecBuffers& io, cudaStream_t s) {
+  auto none = [](const int*, int) { return cudaSuccess; };
+  cudaError_t e = cudaSuccess;
+  if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);
+  for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
+    if (axis == 1 && plan->prof[1]) e = cudaEventRecord(plan->prof[1], s);
+    if (e == cudaSuccess)
+      e = launch_axis(plan, axis, io.src, io.work.data(), io.dout.data(), io.dint.data(), io.dph.data(),
+                      kMaxPassBatch, s, none);
+  }
+  if (e == cudaSuccess && plan->prof[2]) e = cudaEventRecord(plan->prof[2], s);
+  return e;
+}
+
+}  // namespace
+
 int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out, float* const* intensity,
                             float* const* phase, void* stream) {
   if (!plan || !holo) return SF_ERR_INVALID_ARG;
@@ -1106,20 +1270,20 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   DeviceGuard guard(plan->device);
   if (!guard.ok) return SF_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaSuccess;
+  ExecBuffers io;
 
   // hologram: device pointer used in place, host memory staged (the copy is
   // issued below, once the output placement fixes the schedule)
   const size_t holo_elem = plan->in_complex ? sizeof(float2) : sizeof(float);
   const size_t holo_bytes = holo_elem * (size_t)plan->nx0 * plan->ny0;
-  const void* src = holo;
+  io.src = holo;
   bool holo_host = false;
   switch (classify(holo, plan->device)) {
     case PTR_OTHER_DEVICE: return SF_ERR_DEVICE_MISMATCH;
     case PTR_HOST: {
       int rc = stage_alloc(plan, &plan->st_holo, holo_bytes);
       if (rc) return rc;
-      src = plan->st_holo;
+      io.src = plan->st_holo;
       holo_host = true;
       break;
     }
@@ -1127,12 +1291,13 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   }
 
   // outputs: resolve staging for host buffers
-  struct Copy { void* dst; const void* src; size_t bytes; int view; size_t elem; };
-  std::vector<Copy> d2h;
-  std::vector<float2*> dout(nv, nullptr);
-  std::vector<float*> dint(nv, nullptr), dph(nv, nullptr);
+  io.dout.assign(nv, nullptr);
+  io.dint.assign(nv, nullptr);
+  io.dph.assign(nv, nullptr);
+  io.work.resize(nv);
   for (int i = 0; i < nv; ++i) {
     ViewState& vs = plan->views[i];
+    io.work[i] = vs.work;
     const size_t npx = (size_t)vs.v.nx1 * vs.v.ny1;
     auto resolve = [&](void* user, void** stage, size_t bytes, void** dev) -> int {
       if (!user) return SF_OK;
@@ -1141,36 +1306,44 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
         case PTR_HOST: {
           int rc = stage_alloc(plan, stage, bytes);
           if (rc) return rc;
-          d2h.push_back({user, *stage, bytes, i, bytes / npx});
+          io.d2h.push_back({user, *stage, bytes, i, bytes / npx});
           *dev = *stage;
           return SF_OK;
         }
         default: *dev = user; return SF_OK;
       }
     };
-    int rc = resolve(view_out ? view_out[i] : nullptr, (void**)&vs.st_out, sizeof(float2) * npx, (void**)&dout[i]);
-    if (!rc) rc = resolve(intensity ? (void*)intensity[i] : nullptr, (void**)&vs.st_int, sizeof(float) * npx, (void**)&dint[i]);
-    if (!rc) rc = resolve(phase ? (void*)phase[i] : nullptr, (void**)&vs.st_ph, sizeof(float) * npx, (void**)&dph[i]);
+    int rc = resolve(view_out ? view_out[i] : nullptr, (void**)&vs.st_out, sizeof(float2) * npx,
+                     (void**)&io.dout[i]);
+    if (!rc)
+      rc = resolve(intensity ? (void*)intensity[i] : nullptr, (void**)&vs.st_int, sizeof(float) * npx,
+                   (void**)&io.dint[i]);
+    if (!rc)
+      rc = resolve(phase ? (void*)phase[i] : nullptr, (void**)&vs.st_ph, sizeof(float) * npx, (void**)&io.dph[i]);
     if (rc) return rc;
   }
 
-  // Device outputs: x passes then y passes, each grouped by FFT length (on
-  // two streams, see below).  Host outputs: one view at a time, with its
-  // copies to the host overlapping the following views' passes.
-  const bool overlap = !d2h.empty();
-  const bool pipeline = overlap && !env_is("SF_EXECUTE_SINGLE_STREAM", "1");
-  std::vector<float2*> work(nv);
-  for (int i = 0; i < nv; ++i) work[i] = plan->views[i].work;
-  if (overlap) {
-    int rc = pipeline ? ensure_pipeline_resources(plan) : ensure_copy_resources(plan);
+  // Schedule: host outputs -> execute_host_outputs (pipelined unless
+  // SF_EXECUTE_SINGLE_STREAM=1); device outputs of two or more views without
+  // profiling events -> execute_split_halves (unless SF_EXECUTE_SINGLE_STREAM=1);
+  // otherwise execute_single_stream.
+  const bool host_out = !io.d2h.empty();
+  const bool single = env_is("SF_EXECUTE_SINGLE_STREAM", "1");
+  const bool pipeline = host_out && !single;
+  const bool split = !host_out && !plan->prof[0] && nv >= 2 && !single;
+  if (host_out || split) {
+    int rc = pipeline ? ensure_pipeline_resources(plan)
+             : host_out ? ensure_copy_resources(plan)
+                        : ensure_split_resources(plan);
     if (rc) return rc;
   }
-  // The staged hologram goes in two halves when the pipeline below can start
-  // the first view's x pass on the first half (FP32 passes; the split row
-  // keeps the second half's rows 16-byte aligned).
+  // The staged hologram goes in two halves when the pipeline can start the
+  // first view's x pass on the first half (FP32 passes; the split row keeps
+  // the second half's rows 16-byte aligned).
   int split_row = 0;
   if (holo_host && pipeline && !plan->tc_frags && plan->ny0 >= 256 && holo_bytes >= ((size_t)1 << 20))
     split_row = (plan->ny0 / 2) & ~15;
+  cudaError_t e = cudaSuccess;
   if (holo_host) {
     const size_t b0 = split_row ? holo_elem * (size_t)split_row * plan->nx0 : holo_bytes;
     e = cudaMemcpyAsync(plan->st_holo, holo, b0, cudaMemcpyHostToDevice, s);
@@ -1178,155 +1351,14 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
     if (e == cudaSuccess && split_row)
       e = cudaMemcpyAsync(static_cast<char*>(plan->st_holo) + b0, static_cast<const char*>(holo) + b0,
                           holo_bytes - b0, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return SF_ERR_CUDA;
-    }
   }
-  // Device outputs, no profiling events, two or more views: the views are
-  // split into two halves of about equal work, each run (x pass, then y pass)
-  // on its own stream, so one half's y pass overlaps the other's x pass.
-  if (!overlap && !plan->prof[0] && nv >= 2 && !env_is("SF_EXECUTE_SINGLE_STREAM", "1")) {
-    int rc = ensure_split_resources(plan);
-    if (rc) return rc;
-    std::vector<int> order(nv), half[2];
-    double load[2] = {0, 0};
-    for (int i = 0; i < nv; ++i) order[i] = i;
-    auto cost = [&](int v) {
-      const ViewState& vs = plan->views[v];
-      return (double)vs.v.ny0 * vs.ax[0].L + (double)vs.v.nx1 * vs.ax[1].L;
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    for (int v : order) {
-      const int k = load[1] < load[0] ? 1 : 0;
-      half[k].push_back(v);
-      load[k] += cost(v);
-    }
-    for (int k = 0; k < 2; ++k) std::sort(half[k].begin(), half[k].end());
-    auto none = [](const int*, int) { return cudaSuccess; };
-    e = cudaEventRecord(plan->split_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->split_stream, plan->split_fork, 0);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-      cudaStream_t cs = k == 0 ? s : plan->split_stream;
-      for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis)
-        e = launch_axis(plan, axis, src, work.data(), dout.data(), dint.data(), dph.data(), kMaxPassBatch, cs, none,
-                        &half[k]);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(plan->split_join, plan->split_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->split_join, 0);
-    if (e != cudaSuccess) {
-      join_after_error(s, plan->split_stream, plan->split_join);
-      return SF_ERR_CUDA;
-    }
-    return SF_OK;
-  }
-
-  if (overlap) {
-    // Host outputs: view by view, each view's copies to the host starting on
-    // the copy stream as soon as its y pass is done, so the copies (the bound
-    // of this path) start after the first view instead of after every view's
-    // x pass.  Pipelined (default): the x passes run in view order on the
-    // low-priority stream, the first one split at the hologram's halves
-    // (its first half starts while the second half is still being copied);
-    // each y pass waits for its view's x pass on the high-priority stream.
-    // With SF_EXECUTE_SINGLE_STREAM=1 both passes of every view run in turn
-    // on the caller's stream.
-    auto none = [](const int*, int) { return cudaSuccess; };
-    cudaStream_t ys = pipeline ? plan->pipe_y : s;
-    auto copies = [&](const int* views, int) -> cudaError_t {
-      const int vi = views[0];
-      cudaError_t r = cudaEventRecord(plan->view_done[vi], ys);
-      if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, plan->view_done[vi], 0);
-      for (const Copy& c : d2h)
-        if (r == cudaSuccess && c.view == vi)
-          r = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, plan->copy_stream);
-      return r;
-    };
-    // Columns [c0, c1) of view vi's host outputs, once the y pass so far is
-    // done (one 2-D copy per output: ny1 rows of (c1 - c0) elements).
-    auto column_copies = [&](int vi, int c0, int c1, cudaEvent_t ev) -> cudaError_t {
-      const size_t ld = (size_t)plan->views[vi].v.nx1;
-      cudaError_t r = cudaEventRecord(ev, ys);
-      if (r == cudaSuccess) r = cudaStreamWaitEvent(plan->copy_stream, ev, 0);
-      for (const Copy& c : d2h)
-        if (r == cudaSuccess && c.view == vi)
-          r = cudaMemcpy2DAsync(static_cast<char*>(c.dst) + c.elem * c0, c.elem * ld,
-                                static_cast<const char*>(c.src) + c.elem * c0, c.elem * ld, c.elem * (c1 - c0),
-                                (size_t)plan->views[vi].v.ny1, cudaMemcpyDeviceToHost, plan->copy_stream);
-      return r;
-    };
-    if (pipeline) {
-      cudaStream_t xs = plan->pipe_x;
-      e = cudaEventRecord(plan->pipe_fork, s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, split_row ? plan->holo_half : plan->pipe_fork, 0);
-      for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
-        const std::vector<int> one{vi};
-        if (vi == 0 && split_row) {
-          e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, xs, none, &one, 0,
-                          split_row);
-          if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, plan->pipe_fork, 0);
-          if (e == cudaSuccess)
-            e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, xs, none, &one,
-                            split_row);
-        } else {
-          e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, xs, none, &one);
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(plan->x_done[vi], xs);
-      }
-      // The first and the last view's y pass run in two column halves, each
-      // followed by its copies, so the copies start half a pass earlier and
-      // the last ones end half a pass sooner (FP32 plans, views of >= 256
-      // columns; the split column keeps rows of the intermediate 16-byte
-      // aligned).
-      for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
-        const std::vector<int> one{vi};
-        const int nx1 = plan->views[vi].v.nx1;
-        const int half = (vi == 0 || vi == nv - 1) && !plan->tc_frags && nx1 >= 256 ? (nx1 / 2) & ~15 : 0;
-        e = cudaStreamWaitEvent(ys, plan->x_done[vi], 0);
-        if (e == cudaSuccess && half) {
-          e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, ys, none, &one, 0,
-                          half);
-          if (e == cudaSuccess) e = column_copies(vi, 0, half, plan->y_half);
-          if (e == cudaSuccess)
-            e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, ys, none, &one,
-                            half);
-          if (e == cudaSuccess) e = column_copies(vi, half, nx1, plan->view_done[vi]);
-        } else if (e == cudaSuccess) {
-          e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, ys, copies, &one);
-        }
-      }
-      // every x pass precedes some y pass, so the y stream's end covers both
-      if (e == cudaSuccess) e = cudaEventRecord(plan->pipe_join, ys);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->pipe_join, 0);
-    } else {
-      for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
-        const std::vector<int> one{vi};
-        e = launch_axis(plan, 0, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, none, &one);
-        if (e == cudaSuccess)
-          e = launch_axis(plan, 1, src, work.data(), dout.data(), dint.data(), dph.data(), 1, s, copies, &one);
-      }
-    }
-  } else {
-    if (plan->prof[0]) e = cudaEventRecord(plan->prof[0], s);
-    auto none = [](const int*, int) { return cudaSuccess; };
-    for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
-      if (axis == 1 && plan->prof[1]) e = cudaEventRecord(plan->prof[1], s);
-      if (e == cudaSuccess)
-        e = launch_axis(plan, axis, src, work.data(), dout.data(), dint.data(), dph.data(), kMaxPassBatch, s, none);
-    }
-  }
-  if (e == cudaSuccess && plan->prof[2]) e = cudaEventRecord(plan->prof[2], s);
-  if (overlap && e == cudaSuccess) {
-    // the caller's stream resumes after the last copy
-    e = cudaEventRecord(plan->copies_done, plan->copy_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->copies_done, 0);
+  if (e == cudaSuccess) {
+    e = host_out ? execute_host_outputs(plan, io, pipeline, split_row, s)
+        : split  ? execute_split_halves(plan, io, s)
+                 : execute_single_stream(plan, io, s);
   }
   if (e != cudaSuccess) {
-    if (pipeline) {
-      join_after_error(s, plan->pipe_x, plan->pipe_fork);
-      join_after_error(s, plan->pipe_y, plan->pipe_join);
-    }
-    if (overlap) join_after_error(s, plan->copy_stream, plan->copies_done);
+    cudaGetLastError();
     return SF_ERR_CUDA;
   }
   return SF_OK;
