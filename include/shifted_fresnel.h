@@ -101,6 +101,28 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
                          int device, void* stream);
 
 /*
+ * shifted_fresnel_plan_update -- give the plan's views new depths, pitches,
+ * offsets, wavelength or SF_NO_PREFACTOR (the paper's interactive change of
+ * view, Section 3; or a z step of an optimisation) without a new plan: the
+ * chirps of Eqs. 2-3 and the kernel spectra of Eq. 4 (steps 5-6) are rebuilt
+ * in place on `stream`, asynchronously (no allocation, no synchronisation).
+ *
+ *   views      host array of n_views descriptions (copied); view i must keep
+ *              view i's nx0, ny0, nx1, ny1 and SF_IN_COMPLEX, so every FFT
+ *              length and buffer stays as planned.
+ *   n_views    the plan's view count.
+ *   stream     stream to run on.  Work on `stream` after the call sees the
+ *              new views; calls of this plan still in flight on other
+ *              streams must be finished (or ordered before it) by the caller.
+ *
+ * Results equal those of a new plan with the same views.  On SF_ERR_CUDA the
+ * plan's views are undefined until an update succeeds.
+ * Errors: SF_ERR_INVALID_ARG (NULL plan or views, other view count or sizes),
+ * SF_ERR_UNSUPPORTED_SIZE, SF_ERR_CUDA.
+ */
+int shifted_fresnel_plan_update(sf_plan plan, const sf_view* views, int n_views, void* stream);
+
+/*
  * shifted_fresnel_execute -- reconstruct every view of the plan from one
  * hologram (Section 2.2, steps 2-10, and Eq. 5).
  *

@@ -74,6 +74,8 @@ def load():
     lib.shifted_fresnel_plan.argtypes = [pp, ctypes.POINTER(sf_view), ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
     lib.shifted_fresnel_execute.argtypes = [vp, vp, pp, pp, pp, vp]
     lib.shifted_fresnel_destroy.argtypes = [vp]
+    lib.shifted_fresnel_plan_update.argtypes = [vp, ctypes.POINTER(sf_view), ctypes.c_int, vp]
+    lib.shifted_fresnel_plan_update.restype = ctypes.c_int
     lib.shifted_fresnel_strerror.argtypes = [ctypes.c_int]
     lib.shifted_fresnel_strerror.restype = ctypes.c_char_p
     lib.shifted_fresnel_plan_query.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
@@ -191,6 +193,15 @@ def shifted_fresnel_destroy(plan, check=True):
     return rc
 
 
+def shifted_fresnel_plan_update(plan, views, stream=0, check=True):
+    """New depths / pitches / offsets / wavelength for the plan's views (same sizes), in place."""
+    arr = (sf_view * len(views))(*[make_view(v) for v in views])
+    rc = load().shifted_fresnel_plan_update(plan, arr, len(views), ctypes.c_void_p(stream) if stream else None)
+    if check and rc != SF_OK:
+        raise SFError(rc, "shifted_fresnel_plan_update")
+    return rc
+
+
 def shifted_fresnel_plan_query(plan, view):
     lx, ly, ws = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
     rc = load().shifted_fresnel_plan_query(plan, view, ctypes.byref(lx), ctypes.byref(ly), ctypes.byref(ws))
@@ -228,17 +239,24 @@ class ShiftedFresnel:
     intensity / phase images.
     """
 
-    def __init__(self, views, device=None):
+    def __init__(self, views, device=None, precision=SF_PREC_FP32):
         import torch
         self.torch = torch
         self.views = [dict(v) for v in views]
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
-            self.handle = shifted_fresnel_plan(self.views, device=self.device.index, stream=stream)
+            self.handle = shifted_fresnel_plan(self.views, precision=precision, device=self.device.index,
+                                               stream=stream)
 
     def sizes(self, i):
         return shifted_fresnel_plan_query(self.handle, i)
+
+    def update(self, views, stream=None):
+        """Re-target the plan's views (same sizes) in place, ordered on the current stream."""
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
+        shifted_fresnel_plan_update(self.handle, views, stream=s)
+        self.views = [dict(v) for v in views]
 
     def alloc_outputs(self, field=True, intensity=False, phase=False):
         t = self.torch

@@ -85,6 +85,7 @@ struct sf_plan_s {
   int precision = SF_PREC_FP32;
   uint32_t* tc_frags = nullptr;  // per-lane DFT fragments and twiddle tables of the tensor-core pass
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
+  AxisCoef* axes_dev = nullptr;  // coefficient table read by the chirp and spectrum kernels
   int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA
   int sms = 0;
   void* arena = nullptr;
@@ -934,6 +935,50 @@ const char* shifted_fresnel_strerror(int status) {
 
 uint64_t shifted_fresnel_kernel_launches(void) { return g_launches.load(); }
 
+namespace {
+
+// Input / output chirps and kernel spectra of every view and axis (forward
+// and adjoint) from the coefficients in p->views, on stream s: the
+// coefficient table goes to the device, then one chirp launch and one
+// spectrum launch per FFT length, then (tensor-core plans) the spectra in
+// position order.  The device pointers in the coefficients are the plan's.
+cudaError_t build_view_vectors(sf_plan p, cudaStream_t s) {
+  std::vector<AxisCoef> axes;
+  axes.reserve(4 * p->views.size());
+  int max_n = 1;
+  for (const ViewState& vs : p->views)
+    for (int a = 0; a < 2; ++a) {
+      axes.push_back(vs.ax[a]);
+      axes.push_back(vs.adj[a]);
+      max_n = std::max(max_n, std::max(vs.ax[a].n0, vs.ax[a].n1));
+    }
+  // sorted by FFT length so each length's spectra are built by one launch
+  std::stable_sort(axes.begin(), axes.end(), [](const AxisCoef& x, const AxisCoef& y) { return x.L < y.L; });
+  // pageable source: the call returns once the table is staged
+  cudaError_t e =
+      cudaMemcpyAsync(p->axes_dev, axes.data(), sizeof(AxisCoef) * axes.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    e = launch_chirps(p->axes_dev, (int)axes.size(), max_n, s);
+    ++g_launches;
+  }
+  for (size_t i = 0; i < axes.size() && e == cudaSuccess;) {
+    size_t j = i;
+    while (j < axes.size() && axes[j].L == axes[i].L) ++j;
+    e = launch_hspec(axes[i].L, p->axes_dev + i, (int)(j - i), p->tw[axes[i].L], s);
+    ++g_launches;
+    i = j;
+  }
+  for (ViewState& vs : p->views)
+    for (int a = 0; a < 2 && e == cudaSuccess; ++a)
+      if (vs.hpos[a]) {
+        e = launch_hpos(vs.ax[a].L, vs.ax[a].H, vs.hpos[a], s);
+        ++g_launches;
+      }
+  return e;
+}
+
+}  // namespace
+
 int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int precision, int device,
                          void* stream) {
   if (!out) return SF_ERR_INVALID_ARG;
@@ -1007,10 +1052,6 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   char* base = static_cast<char*>(p->arena);
   for (auto& kv : tw_off) p->tw[kv.first] = reinterpret_cast<float4*>(base + kv.second);
 
-  // axes sorted by FFT length so each length's spectra are built by one launch
-  std::vector<AxisCoef> axes;
-  axes.reserve(4 * n_views);
-  int max_n = 1;
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.work = reinterpret_cast<float2*>(base + off_work[i]);
@@ -1021,19 +1062,15 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       c.cin = reinterpret_cast<float2*>(base + off_cin[2 * i + a]);
       c.cout = reinterpret_cast<float2*>(base + off_cout[2 * i + a]);
       c.H = reinterpret_cast<float2*>(base + off_H[2 * i + a]);
-      axes.push_back(c);
-      max_n = std::max(max_n, std::max(c.n0, c.n1));
       AxisCoef& ca = vs.adj[a];
       ca.cin = reinterpret_cast<float2*>(base + off_cin[2 * n_views + 2 * i + a]);
       ca.cout = reinterpret_cast<float2*>(base + off_cout[2 * n_views + 2 * i + a]);
       ca.H = reinterpret_cast<float2*>(base + off_H[2 * n_views + 2 * i + a]);
-      axes.push_back(ca);
     }
   }
-  std::stable_sort(axes.begin(), axes.end(), [](const AxisCoef& x, const AxisCoef& y) { return x.L < y.L; });
-  AxisCoef* axes_dev = reinterpret_cast<AxisCoef*>(base + off_axes);
+  p->axes_dev = reinterpret_cast<AxisCoef*>(base + off_axes);
 
-  cudaError_t e = cudaMemcpyAsync(axes_dev, axes.data(), sizeof(AxisCoef) * axes.size(), cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaSuccess;
   std::vector<std::vector<float4>> tw_host;  // kept alive until the stream is synchronised below
   for (auto& kv : p->tw) {
     tw_host.emplace_back(twiddle_entries(kv.first));
@@ -1042,26 +1079,13 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       e = cudaMemcpyAsync(kv.second, tw_host.back().data(), sizeof(float4) * tw_host.back().size(),
                           cudaMemcpyHostToDevice, s);
   }
-  if (e == cudaSuccess) { e = launch_chirps(axes_dev, (int)axes.size(), max_n, s); ++g_launches; }
-  for (size_t i = 0; i < axes.size() && e == cudaSuccess;) {
-    size_t j = i;
-    while (j < axes.size() && axes[j].L == axes[i].L) ++j;
-    e = launch_hspec(axes[i].L, axes_dev + i, (int)(j - i), p->tw[axes[i].L], s);
-    ++g_launches;
-    i = j;
-  }
+  if (e == cudaSuccess) e = build_view_vectors(p, s);
   p->dev_err = reinterpret_cast<int*>(base + off_err);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
   if (off_frags != SIZE_MAX && e == cudaSuccess) {
     p->tc_frags = reinterpret_cast<uint32_t*>(base + off_frags);
     e = launch_tc_tables(p->tc_frags, precision, s);
     g_launches += 3;  // fragments and the twiddle tables of both lengths
-    for (ViewState& vs : p->views)
-      for (int a = 0; a < 2 && e == cudaSuccess; ++a)
-        if (vs.hpos[a]) {
-          e = launch_hpos(vs.ax[a].L, vs.ax[a].H, vs.hpos[a], s);
-          ++g_launches;
-        }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -1070,6 +1094,41 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     return e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA;
   }
   *out = p;
+  return SF_OK;
+}
+
+int shifted_fresnel_plan_update(sf_plan plan, const sf_view* views, int n_views, void* stream) {
+  if (!plan || !views || n_views != (int)plan->views.size()) return SF_ERR_INVALID_ARG;
+  for (int i = 0; i < n_views; ++i) {
+    int rc = validate_view(views[i]);
+    if (rc) return rc;
+    const sf_view& o = plan->views[i].v;
+    if (views[i].nx0 != o.nx0 || views[i].ny0 != o.ny0 || views[i].nx1 != o.nx1 || views[i].ny1 != o.ny1 ||
+        (views[i].flags & SF_IN_COMPLEX) != (o.flags & SF_IN_COMPLEX))
+      return SF_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return SF_ERR_CUDA;
+  // new coefficients on the same FFT lengths and device vectors
+  for (int i = 0; i < n_views; ++i) {
+    ViewState& vs = plan->views[i];
+    vs.v = views[i];
+    for (int a = 0; a < 2; ++a) {
+      const AxisCoef f = vs.ax[a], g = vs.adj[a];
+      axis_coefficients(vs.v, a, vs.ax[a], f.L);
+      adjoint_axis_coefficients(vs.v, a, vs.adj[a], g.L);
+      vs.ax[a].cin = f.cin;
+      vs.ax[a].cout = f.cout;
+      vs.ax[a].H = f.H;
+      vs.adj[a].cin = g.cin;
+      vs.adj[a].cout = g.cout;
+      vs.adj[a].H = g.H;
+    }
+  }
+  if (build_view_vectors(plan, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
   return SF_OK;
 }
 

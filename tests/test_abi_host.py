@@ -131,3 +131,10 @@ def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
         binding.shifted_fresnel_plan([base_view()])
     with pytest.raises(RuntimeError, match="missing"):
         binding.shifted_fresnel_fft_length(2047)
+
+
+def test_plan_update_rejects_null_arguments(lib):
+    """shifted_fresnel_plan_update checks its arguments before touching a device."""
+    assert lib.shifted_fresnel_plan_update(None, [base_view()], check=False) == lib.SF_ERR_INVALID_ARG
+    raw = lib.load().shifted_fresnel_plan_update
+    assert raw(None, None, 1, None) == lib.SF_ERR_INVALID_ARG
