@@ -5,12 +5,14 @@ the forward pass is ``shifted_fresnel_execute`` and the backward pass is
 ``shifted_fresnel_adjoint``, which returns the gradient with respect to the
 complex object field (sum over views of A_v^H g_v) and, when asked, with
 respect to each view's z.  The z values are part of the plan (the chirps and
-kernel spectra depend on them); the ``z`` tensor passed in is the plan's z,
-used only as the handle that receives dL/dz.
+kernel spectra depend on them): a ``z`` tensor that differs from the plan's
+depths re-targets the plan first (``shifted_fresnel_plan_update``), so z can
+be a trained parameter.
 
 ``phase_retrieval`` fits a complex object to measured view intensities
 (twin-image-free in-line holography from several depths) by minimising
-sum_v || |A_v u|^2 - I_v ||^2 with Adam.
+sum_v || |A_v u|^2 - I_v ||^2 with Adam; ``fit_depths`` fits the views' z to
+measured intensities of a known object with the same loss.
 """
 
 from __future__ import annotations
@@ -27,10 +29,12 @@ class ShiftedFresnelFunction(torch.autograd.Function):
     def forward(ctx, u0, z, sf):
         if not (sf.views[0].get("flags", 0) & SF_IN_COMPLEX):
             raise ValueError("the plan must take a complex object (SF_IN_COMPLEX)")
-        zs = [v["z"] for v in sf.views]
-        if z is not None and (z.numel() != len(zs) or
-                              any(abs(float(a) - b) > 1e-12 * abs(b) for a, b in zip(z.detach().cpu(), zs))):
-            raise ValueError("z must hold the plan's per-view distances")
+        if z is not None:
+            zv = [float(a) for a in z.detach().cpu()]
+            if len(zv) != len(sf.views):
+                raise ValueError("z must hold one distance per view")
+            if any(a != v["z"] for a, v in zip(zv, sf.views)):
+                sf.update([dict(v, z=a) for v, a in zip(sf.views, zv)])
         u0c = u0.contiguous()
         outs = sf.reconstruct(u0c, field=True)
         ctx.sf = sf
@@ -94,4 +98,24 @@ def phase_retrieval(sf, intensities, n_iter=200, u_init=None, lr=0.05, recompute
     return u.detach(), [float(x) for x in torch.stack(losses).cpu()]
 
 
-__all__ = ["ShiftedFresnelFunction", "views", "intensity_loss", "phase_retrieval", "ShiftedFresnel"]
+def fit_depths(sf, u0, intensities, n_iter=100, lr=5e-5):
+    """Fit each view's z to measured intensities of a known object u0 (Adam on dL/dz).
+
+    The plan follows z through every step and holds the fitted depths on
+    return.  Returns (z, losses).
+    """
+    z = torch.tensor([v["z"] for v in sf.views], dtype=torch.float64, device=u0.device, requires_grad=True)
+    opt = torch.optim.Adam([z], lr=lr)
+    u = u0.detach()
+    losses = []
+    for _ in range(n_iter):
+        opt.zero_grad(set_to_none=True)
+        loss = intensity_loss(u, sf, intensities, z=z)
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+    sf.update([dict(v, z=float(a)) for v, a in zip(sf.views, z.detach().cpu())])
+    return z.detach(), [float(x) for x in torch.stack(losses).cpu()]
+
+
+__all__ = ["ShiftedFresnelFunction", "views", "intensity_loss", "phase_retrieval", "fit_depths", "ShiftedFresnel"]

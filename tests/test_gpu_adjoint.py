@@ -189,3 +189,26 @@ def test_phase_retrieval_200_iterations_paper_scale(P):
         sf.close()
     assert np.all(np.isfinite(losses))
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def test_fit_depths_recovers_z(P):
+    """z as a trained parameter: the plan follows it (plan update) and Adam on the
+    adjoint's dL/dz recovers both views' depths from a 3 % start."""
+    import torch
+    from paper_1001_4309_gb300.autograd import fit_depths
+    n = 128
+    rng = np.random.default_rng(1)
+    u = to_dev(synth.gabor.bars_disks_object(n, rng) * np.exp(1j * 0.3))
+    z_true, pitches = (0.03, 0.045), (PITCH, 2e-6)
+    mk = lambda z, p1: view(WAVELENGTH, z, PITCH, p1, n0=(n, n), n1=(n, n), flags=CPLX | NOPRE)  # noqa: E731
+    truth = P.ShiftedFresnel([mk(z, p) for z, p in zip(z_true, pitches)])
+    I = [o.abs() ** 2 for o in truth.reconstruct(u)["field"]]
+    truth.close()
+    sf = P.ShiftedFresnel([mk(1.03 * z, p) for z, p in zip(z_true, pitches)])
+    try:
+        z, losses = fit_depths(sf, u, I, n_iter=100, lr=5e-5)
+        assert np.all(np.abs(z.cpu().numpy() - np.array(z_true)) < 3e-5), z
+        assert losses[-1] < 1e-3 * losses[0], (losses[0], losses[-1])
+        assert [v["z"] for v in sf.views] == [float(a) for a in z.cpu()]  # the plan holds the fitted depths
+    finally:
+        sf.close()
