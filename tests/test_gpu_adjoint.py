@@ -198,12 +198,13 @@ def test_fit_depths_recovers_z(P):
     from paper_1001_4309_gb300.autograd import fit_depths
     n = 128
     rng = np.random.default_rng(1)
-    u = to_dev(synth.gabor.bars_disks_object(n, rng) * np.exp(1j * 0.3))
+    u_np = (synth.gabor.bars_disks_object(n, rng) * np.exp(1j * 0.3)).astype(np.complex64)
+    u = to_dev(u_np)
     z_true, pitches = (0.03, 0.045), (PITCH, 2e-6)
     mk = lambda z, p1: view(WAVELENGTH, z, PITCH, p1, n0=(n, n), n1=(n, n), flags=CPLX | NOPRE)  # noqa: E731
-    truth = P.ShiftedFresnel([mk(z, p) for z, p in zip(z_true, pitches)])
-    I = [o.abs() ** 2 for o in truth.reconstruct(u)["field"]]
-    truth.close()
+    # measured intensities from the FP64 oracle at the true depths
+    I = [torch.from_numpy((np.abs(oracle.forward(u_np, mk(z, p))) ** 2).astype(np.float32)).cuda()
+         for z, p in zip(z_true, pitches)]
     sf = P.ShiftedFresnel([mk(1.03 * z, p) for z, p in zip(z_true, pitches)])
     try:
         z, losses = fit_depths(sf, u, I, n_iter=100, lr=5e-5)
