@@ -265,6 +265,31 @@ int shifted_fresnel_batch_status(sf_plan plan, void* stream);
 int shifted_fresnel_adjoint(sf_plan plan, const void* holo, const void* const* grad_view, void* grad_holo,
                             double* grad_z, void* stream);
 
+/*
+ * shifted_fresnel_intensity_loss -- the multi-depth intensity loss of phase
+ * retrieval and the view gradients that shifted_fresnel_adjoint takes back
+ * to the object: with u_v the complex views (for instance from execute) and
+ * I_v measured intensities,
+ *
+ *   L = sum_v sum_pixels (|u_v|^2 - I_v)^2          (|u_v|^2 as in Eq. 5)
+ *   g_v = 4 (|u_v|^2 - I_v) u_v  = 2 dL/d(conj u_v)
+ *
+ * (the conjugate-Wirtinger gradient PyTorch's complex autograd uses).
+ *
+ *   fields     n_views device pointers to complex64 [ny1][nx1] views.
+ *   measured   n_views device pointers to float32 [ny1][nx1] intensities.
+ *   grads      n_views device pointers receiving complex64 [ny1][nx1]
+ *              gradients, or NULL for the loss alone.
+ *   loss       device pointer to one double: the loss, written on `stream`
+ *              (per view, residuals in FP32 and their squares summed in
+ *              double precision in a fixed order: deterministic).
+ *   stream     stream to run on.
+ * Errors: SF_ERR_INVALID_ARG (NULL or host pointers), SF_ERR_OOM (first call
+ * allocates a small partial-sum buffer), SF_ERR_CUDA.
+ */
+int shifted_fresnel_intensity_loss(sf_plan plan, void* const* fields, const float* const* measured,
+                                   void* const* grads, double* loss, void* stream);
+
 /* shifted_fresnel_destroy -- synchronise the plan's device and free everything it owns. */
 int shifted_fresnel_destroy(sf_plan plan);
 

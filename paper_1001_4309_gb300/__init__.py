@@ -20,6 +20,7 @@ from .binding import (  # noqa: F401
     shifted_fresnel_strerror,
     shifted_fresnel_plan_query,
     shifted_fresnel_plan_update,
+    shifted_fresnel_intensity_loss,
     shifted_fresnel_kernel_launches,
     shifted_fresnel_set_profile_events,
     shifted_fresnel_fft_length,

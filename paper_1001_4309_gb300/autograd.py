@@ -19,7 +19,18 @@ from __future__ import annotations
 
 import torch
 
-from .binding import ShiftedFresnel, shifted_fresnel_adjoint, SF_IN_COMPLEX
+from .binding import ShiftedFresnel, shifted_fresnel_adjoint, shifted_fresnel_intensity_loss, SF_IN_COMPLEX
+
+
+def _follow_z(sf, z):
+    """Re-target the plan when the z tensor differs from its depths."""
+    if z is None:
+        return
+    zv = [float(a) for a in z.detach().cpu()]
+    if len(zv) != len(sf.views):
+        raise ValueError("z must hold one distance per view")
+    if any(a != v["z"] for a, v in zip(zv, sf.views)):
+        sf.update([dict(v, z=a) for v, a in zip(sf.views, zv)])
 
 
 class ShiftedFresnelFunction(torch.autograd.Function):
@@ -29,12 +40,7 @@ class ShiftedFresnelFunction(torch.autograd.Function):
     def forward(ctx, u0, z, sf):
         if not (sf.views[0].get("flags", 0) & SF_IN_COMPLEX):
             raise ValueError("the plan must take a complex object (SF_IN_COMPLEX)")
-        if z is not None:
-            zv = [float(a) for a in z.detach().cpu()]
-            if len(zv) != len(sf.views):
-                raise ValueError("z must hold one distance per view")
-            if any(a != v["z"] for a, v in zip(zv, sf.views)):
-                sf.update([dict(v, z=a) for v, a in zip(sf.views, zv)])
+        _follow_z(sf, z)
         u0c = u0.contiguous()
         outs = sf.reconstruct(u0c, field=True)
         ctx.sf = sf
@@ -64,10 +70,56 @@ def views(u0, sf, z=None):
     return ShiftedFresnelFunction.apply(u0, z, sf)
 
 
+class IntensityLossFunction(torch.autograd.Function):
+    """loss = IntensityLossFunction.apply(u0, z, sf, intensities): the fused multi-depth intensity loss.
+
+    Forward: execute, then shifted_fresnel_intensity_loss (loss in double
+    precision and the view gradients 4 (|u|^2 - I) u in one kernel per view).
+    Backward: shifted_fresnel_adjoint of those view gradients (and dL/dz when
+    z requires it), scaled by the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, u0, z, sf, intensities):
+        if not (sf.views[0].get("flags", 0) & SF_IN_COMPLEX):
+            raise ValueError("the plan must take a complex object (SF_IN_COMPLEX)")
+        _follow_z(sf, z)
+        u0c = u0.contiguous()
+        fields = sf.reconstruct(u0c, field=True)["field"]
+        meas = [I.contiguous() for I in intensities]
+        need = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
+        grads = [torch.empty_like(f) for f in fields] if need else None
+        loss = torch.empty((), dtype=torch.float64, device=u0c.device)
+        shifted_fresnel_intensity_loss(sf.handle, [f.data_ptr() for f in fields], [I.data_ptr() for I in meas],
+                                       [g.data_ptr() for g in grads] if grads else None, loss.data_ptr(),
+                                       stream=torch.cuda.current_stream(u0c.device).cuda_stream)
+        ctx.sf = sf
+        ctx.grads = grads
+        ctx.save_for_backward(u0c)
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        (u0,) = ctx.saved_tensors
+        sf = ctx.sf
+        need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_u or need_z):
+            return None, None, None, None
+        grad_u = torch.empty_like(u0) if need_u else None
+        grad_z = torch.zeros(len(sf.views), dtype=torch.float64, device=u0.device) if need_z else None
+        shifted_fresnel_adjoint(sf.handle, u0.data_ptr() if need_z else None, [g.data_ptr() for g in ctx.grads],
+                                grad_u.data_ptr() if need_u else None, grad_z.data_ptr() if need_z else None,
+                                stream=torch.cuda.current_stream(u0.device).cuda_stream)
+        if need_u:
+            grad_u.mul_(grad_loss.to(grad_u.real.dtype))
+        if need_z:
+            grad_z.mul_(grad_loss)
+        return grad_u, grad_z, None, None
+
+
 def intensity_loss(u0, sf, intensities, z=None):
-    """sum_v || |A_v u0|^2 - I_v ||^2 (the loss of the multi-depth phase retrieval)."""
-    outs = views(u0, sf, z)
-    return sum(((o.real ** 2 + o.imag ** 2 - I) ** 2).sum() for o, I in zip(outs, intensities))
+    """sum_v || |A_v u0|^2 - I_v ||^2 (the loss of the multi-depth phase retrieval), float64 scalar."""
+    return IntensityLossFunction.apply(u0, z, sf, intensities)
 
 
 def phase_retrieval(sf, intensities, n_iter=200, u_init=None, lr=0.05, recompute=False, callback=None):
@@ -118,4 +170,5 @@ def fit_depths(sf, u0, intensities, n_iter=100, lr=5e-5):
     return z.detach(), [float(x) for x in torch.stack(losses).cpu()]
 
 
-__all__ = ["ShiftedFresnelFunction", "views", "intensity_loss", "phase_retrieval", "fit_depths", "ShiftedFresnel"]
+__all__ = ["ShiftedFresnelFunction", "IntensityLossFunction", "views", "intensity_loss", "phase_retrieval",
+           "fit_depths", "ShiftedFresnel"]

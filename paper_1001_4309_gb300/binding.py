@@ -75,6 +75,8 @@ def load():
     lib.shifted_fresnel_execute.argtypes = [vp, vp, pp, pp, pp, vp]
     lib.shifted_fresnel_destroy.argtypes = [vp]
     lib.shifted_fresnel_plan_update.argtypes = [vp, ctypes.POINTER(sf_view), ctypes.c_int, vp]
+    lib.shifted_fresnel_intensity_loss.argtypes = [vp, pp, pp, pp, vp, vp]
+    lib.shifted_fresnel_intensity_loss.restype = ctypes.c_int
     lib.shifted_fresnel_plan_update.restype = ctypes.c_int
     lib.shifted_fresnel_strerror.argtypes = [ctypes.c_int]
     lib.shifted_fresnel_strerror.restype = ctypes.c_char_p
@@ -169,6 +171,16 @@ def shifted_fresnel_execute_batch(plan, holo_ptrs, view_out=None, intensity=None
                                               ctypes.c_void_p(stream) if stream else None)
     if check and rc != SF_OK:
         raise SFError(rc, "shifted_fresnel_execute_batch")
+    return rc
+
+
+def shifted_fresnel_intensity_loss(plan, fields, measured, grads, loss_ptr, stream=0, check=True):
+    """loss (device double) = sum_v ||(|u_v|^2 - I_v)||^2; grads[v] = 4 (|u_v|^2 - I_v) u_v (or grads None)."""
+    rc = load().shifted_fresnel_intensity_loss(plan, _ptr_array(fields), _ptr_array(measured), _ptr_array(grads),
+                                               ctypes.c_void_p(loss_ptr) if loss_ptr else None,
+                                               ctypes.c_void_p(stream) if stream else None)
+    if check and rc != SF_OK:
+        raise SFError(rc, "shifted_fresnel_intensity_loss")
     return rc
 
 

@@ -115,6 +115,39 @@ __global__ void k_zgrad_final(const double2* __restrict__ partials, int n_partia
   *out = (c_re * t[0] - c_im * t[1]) + (q_re * tr - q_im * ti);
 }
 
+// Intensity loss of one view (Eq. 5): r = |u|^2 - I per pixel, block partials
+// of sum r^2 in double precision, and (when g is given) the loss gradient
+// g = 4 r u, i.e. 2 dL/d(conj u) (the conjugate-Wirtinger convention of
+// PyTorch's complex autograd).
+__global__ void __launch_bounds__(256) k_intensity_partial(const float2* __restrict__ u, const float* __restrict__ I,
+                                                           float2* __restrict__ g, unsigned n,
+                                                           double* __restrict__ partials) {
+  double acc = 0.0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 v = u[i];
+    const float r = fmaf(v.x, v.x, v.y * v.y) - I[i];
+    acc += (double)r * (double)r;
+    if (g) g[i] = make_float2(4.f * r * v.x, 4.f * r * v.y);
+  }
+  __shared__ double red[8];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// out (+)= the partials summed in block order.
+__global__ void k_sum_partials(const double* __restrict__ partials, int n_partials, double* out, int accumulate) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int b = 0; b < n_partials; ++b) t += partials[b];
+  *out = accumulate ? *out + t : t;
+}
+
 __global__ void k_axpy(float2* __restrict__ y, const float2* __restrict__ x, size_t n, int accumulate) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float2 v = x[i];
@@ -146,6 +179,15 @@ cudaError_t launch_zgrad(const ZGradArgs& a, double2* partials, int n_partials, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_zgrad_final<<<1, 32, 0, s>>>(partials, n_partials, out, c_re, c_im, q_re, q_im);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_loss(const float2* u, const float* I, float2* g, size_t n, double* partials,
+                                  int n_partials, double* loss, int accumulate, cudaStream_t s) {
+  k_intensity_partial<<<n_partials, 256, 0, s>>>(u, I, g, (unsigned)n, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials<<<1, 32, 0, s>>>(partials, n_partials, loss, accumulate);
   return cudaGetLastError();
 }
 

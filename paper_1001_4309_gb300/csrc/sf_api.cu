@@ -101,6 +101,7 @@ struct sf_plan_s {
   float2* adj_out = nullptr;    // nx0 * ny0: staging of a host grad_holo
   double2* adj_part = nullptr;  // kZGradBlocks x 5 partial sums
   double* adj_z = nullptr;      // n_views dL/dz values
+  double* loss_part = nullptr;  // kZGradBlocks block partials of shifted_fresnel_intensity_loss
   BatchState batch;
   // host-output overlap, created on first use: a copy stream, one event per
   // view, and the pipeline's x-pass stream (lowest priority) and y-pass
@@ -1557,6 +1558,43 @@ int shifted_fresnel_adjoint(sf_plan plan, const void* holo, const void* const* g
     e = cudaMemcpyAsync(grad_holo, gout, sizeof(float2) * h0, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && grad_z)
     e = cudaMemcpyAsync(grad_z, plan->adj_z, sizeof(double) * nv, cudaMemcpyDefault, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  return SF_OK;
+}
+
+int shifted_fresnel_intensity_loss(sf_plan plan, void* const* fields, const float* const* measured,
+                                   void* const* grads, double* loss, void* stream) {
+  if (!plan || !fields || !measured || !loss) return SF_ERR_INVALID_ARG;
+  const int nv = (int)plan->views.size();
+  for (int v = 0; v < nv; ++v) {
+    if (!fields[v] || !measured[v]) return SF_ERR_INVALID_ARG;
+    for (const void* q : {(const void*)fields[v], (const void*)measured[v], grads ? (const void*)grads[v] : nullptr})
+      if (q && classify(q, plan->device) != PTR_DEVICE) return SF_ERR_INVALID_ARG;
+  }
+  if (classify(loss, plan->device) != PTR_DEVICE) return SF_ERR_INVALID_ARG;
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return SF_ERR_CUDA;
+  if (!plan->loss_part) {
+    void* b = nullptr;
+    if (cudaMalloc(&b, sizeof(double) * kZGradBlocks) != cudaSuccess) {
+      cudaGetLastError();
+      return SF_ERR_OOM;
+    }
+    plan->staging.push_back(b);
+    plan->loss_part = static_cast<double*>(b);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+    const sf_view& w = plan->views[v].v;
+    e = launch_intensity_loss(static_cast<const float2*>(fields[v]), measured[v],
+                              grads ? static_cast<float2*>(grads[v]) : nullptr, (size_t)w.nx1 * w.ny1,
+                              plan->loss_part, kZGradBlocks, loss, v > 0 ? 1 : 0, s);
+    g_launches += 2;
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SF_ERR_CUDA;

@@ -113,6 +113,9 @@ cudaError_t launch_weight_xy(const float2* g, float2* xg, float2* yg, int nx1, i
 cudaError_t launch_zgrad(const ZGradArgs& a, double2* partials, int n_partials, double* out, double c_re,
                          double c_im, double q_re, double q_im, cudaStream_t s);
 cudaError_t launch_axpy(float2* y, const float2* x, size_t n, int accumulate, cudaStream_t s);
+// loss (+)= sum over pixels of (|u|^2 - I)^2, g = 4 (|u|^2 - I) u (g may be null); two launches
+cudaError_t launch_intensity_loss(const float2* u, const float* I, float2* g, size_t n, double* partials,
+                                  int n_partials, double* loss, int accumulate, cudaStream_t s);
 constexpr int kZGradBlocks = 304;
 void count_launches(uint64_t n);
 

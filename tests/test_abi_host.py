@@ -138,3 +138,8 @@ def test_plan_update_rejects_null_arguments(lib):
     assert lib.shifted_fresnel_plan_update(None, [base_view()], check=False) == lib.SF_ERR_INVALID_ARG
     raw = lib.load().shifted_fresnel_plan_update
     assert raw(None, None, 1, None) == lib.SF_ERR_INVALID_ARG
+
+
+def test_intensity_loss_rejects_null_arguments(lib):
+    raw = lib.load().shifted_fresnel_intensity_loss
+    assert raw(None, None, None, None, None, None) == lib.SF_ERR_INVALID_ARG

@@ -213,3 +213,40 @@ def test_fit_depths_recovers_z(P):
         assert [v["z"] for v in sf.views] == [float(a) for a in z.cpu()]  # the plan holds the fitted depths
     finally:
         sf.close()
+
+
+def test_fused_intensity_loss_matches_composed(P):
+    """shifted_fresnel_intensity_loss (one kernel per view) against the same loss
+    composed from torch operations on the differentiable views: loss, object
+    gradient and dL/dz agree to rounding."""
+    import torch
+    from paper_1001_4309_gb300.autograd import intensity_loss, views
+    n = 96
+    vs = [view(WAVELENGTH, z, PITCH, p1, o1=(3e-5, -2e-5), n0=(n, n), n1=(n, 80), flags=CPLX | NOPRE)
+          for z, p1 in ((0.02, PITCH), (0.04, 2e-6), (-0.03, 3e-6))]
+    rng = np.random.default_rng(8)
+    u0 = to_dev(np.exp(1j * rng.uniform(-1, 1, (n, n))) * (1 + 0.2 * rng.standard_normal((n, n))))
+    sf = P.ShiftedFresnel(vs)
+    try:
+        meas = [o.abs() ** 2 * 0.9 for o in sf.reconstruct(u0 * 1.1)["field"]]
+        zs = [v["z"] for v in vs]
+        res = []
+        for fused in (True, False):
+            u = u0.clone().requires_grad_(True)
+            z = torch.tensor(zs, dtype=torch.float64, device="cuda", requires_grad=True)
+            if fused:
+                loss = intensity_loss(u, sf, meas, z)
+            else:
+                loss = sum(((o.real ** 2 + o.imag ** 2 - I).double() ** 2).sum()
+                           for o, I in zip(views(u, sf, z), meas))
+            (2.0 * loss).backward()  # a non-unit incoming gradient
+            res.append((float(loss.detach()), u.grad.cpu().numpy(), z.grad.cpu().numpy()))
+        (lf, gf, zf), (lc, gc, zc) = res
+        assert abs(lf - lc) <= 1e-5 * abs(lc), (lf, lc)
+        assert rel_l2(gf, gc) <= 1e-5
+        assert np.allclose(zf, zc, rtol=1e-4, atol=0), (zf, zc)
+        # the loss alone (no gradients requested)
+        with torch.no_grad():
+            assert abs(float(intensity_loss(u0, sf, meas)) - lc) <= 1e-5 * abs(lc)
+    finally:
+        sf.close()
