@@ -211,6 +211,34 @@ def test_host_pipeline_matches_device_buffers(P, single_stream, monkeypatch):
         sf.close()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_pipeline_single_complex_view(P, pinned):
+    """One view (first and last at once: both y-pass column halves) from a complex host
+    hologram split in halves, pinned or pageable: equal to the device-buffer result."""
+    import torch
+    ny0, nx0 = 384, 400
+    v = view(WAVELENGTH, 0.04, PITCH, 3e-6, o1=(2e-4, -1e-4), n0=(nx0, ny0), n1=(512, 300), flags=P.SF_IN_COMPLEX)
+    holo = random_field(ny0, nx0, seed=77).astype(np.complex64)
+    ref = run(P, [v], holo, phase=True)
+    sf = P.ShiftedFresnel([v])
+    try:
+        h = torch.from_numpy(holo.copy())
+        f = torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64)
+        I = torch.empty((v["ny1"], v["nx1"]), dtype=torch.float32)
+        ph = torch.empty((v["ny1"], v["nx1"]), dtype=torch.float32)
+        if pinned:
+            h, f, I, ph = h.pin_memory(), f.pin_memory(), I.pin_memory(), ph.pin_memory()
+        for _ in range(2):
+            P.shifted_fresnel_execute(sf.handle, h.data_ptr(), [f.data_ptr()], [I.data_ptr()], [ph.data_ptr()],
+                                      stream=torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            assert np.array_equal(f.numpy(), ref["field"][0])
+            assert np.array_equal(I.numpy(), ref["intensity"][0])
+            assert np.array_equal(ph.numpy(), ref["phase"][0])
+    finally:
+        sf.close()
+
+
 def test_repeat_execute_is_deterministic(P):
     import torch
     holo, views = synth.config_c1()
