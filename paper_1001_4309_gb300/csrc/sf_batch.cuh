@@ -43,6 +43,10 @@ __device__ __forceinline__ int batch_ld_acquire(const int* p) {
 template <typename Run>
 __device__ __forceinline__ void batch_loop(const BatchArgs& a, Run&& run) {
   __shared__ int s_item, s_group, s_stop;
+  // the item's pass descriptor, staged once per item: the row tile reads its
+  // fields after every barrier, and shared memory answers those re-reads
+  // faster than the global table would
+  __shared__ PassDesc s_desc;
   if (threadIdx.x == 0) s_item = atomicAdd(a.next, 1);
   for (;;) {
     __syncthreads();
@@ -87,13 +91,14 @@ __device__ __forceinline__ void batch_loop(const BatchArgs& a, Run&& run) {
       }
       s_group = g;
       s_stop = stop;
+      if (!stop) s_desc = a.descs[(size_t)(item / a.items_per_holo) * a.n_groups + g];
     }
     __syncthreads();
     if (s_stop) return;
     const int item = s_item, g = s_group;
     const int h = item / a.items_per_holo;
     const BatchGroup gi = a.groups[g];
-    const PassDesc& d = a.descs[(size_t)h * a.n_groups + g];
+    const PassDesc& d = s_desc;
     const int t0 = (item - h * a.items_per_holo - gi.first_item) * gi.chunk;
     const int t1 = min(t0 + gi.chunk, gi.tiles);
     for (int tile = t0; tile < t1; ++tile) {
