@@ -51,6 +51,7 @@ struct BatchState {
   size_t ksmem = 0;                      // its dynamic shared memory
   std::vector<float2*> slot1;            // second intermediate slot per view
   BatchGroup* d_groups = nullptr;
+  int* d_item_group = nullptr;           // group of each item within a hologram
   int* d_error = nullptr;
   void* d_fixed = nullptr;               // slot1 workspaces + groups + error word
   void* d_sized = nullptr;               // descriptors + counters for n_holos
@@ -473,6 +474,7 @@ int batch_prepare(sf_plan p, int n_holos, bool persistent) {
     std::vector<size_t> off(nv);
     for (int v = 0; v < nv; ++v) off[v] = ar.take(sizeof(float2) * (size_t)p->views[v].v.ny0 * p->views[v].v.nx1);
     const size_t o_groups = ar.take(sizeof(BatchGroup) * b.groups.size());
+    const size_t o_item_group = ar.take(sizeof(int) * b.items_per_holo);
     if (cudaMalloc(&b.d_fixed, ar.off) != cudaSuccess) {
       cudaGetLastError();
       return SF_ERR_OOM;
@@ -483,6 +485,13 @@ int batch_prepare(sf_plan p, int n_holos, bool persistent) {
     b.d_groups = reinterpret_cast<BatchGroup*>(base + o_groups);
     b.d_error = p->dev_err;
     if (cudaMemcpy(b.d_groups, b.groups.data(), sizeof(BatchGroup) * b.groups.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return SF_ERR_CUDA;
+    std::vector<int> item_group(b.items_per_holo);
+    for (int g = 0; g < (int)b.groups.size(); ++g)
+      for (int i = 0; i < b.groups[g].items; ++i) item_group[b.groups[g].first_item + i] = g;
+    b.d_item_group = reinterpret_cast<int*>(base + o_item_group);
+    if (cudaMemcpy(b.d_item_group, item_group.data(), sizeof(int) * item_group.size(), cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return SF_ERR_CUDA;
     // One power-of-two length on every pass of every view, all prunable: the
@@ -530,6 +539,7 @@ int batch_prepare(sf_plan p, int n_holos, bool persistent) {
   std::memset(&args, 0, sizeof(args));
   args.descs = b.d_descs;
   args.groups = b.d_groups;
+  args.item_group = b.d_item_group;
   args.done = b.d_done;
   args.next = b.d_done + n_desc;
   args.error = b.d_error;

@@ -60,12 +60,7 @@ __device__ __forceinline__ void batch_loop(const BatchArgs& a, Run&& run) {
       int g = 0;
       if (!stop) {
         const int h = item / a.items_per_holo, r = item - h * a.items_per_holo;
-        int lo = 0, hi = a.n_groups - 1;  // last group with first_item <= r
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.groups[mid].first_item <= r) lo = mid; else hi = mid - 1;
-        }
-        g = lo;
+        g = a.item_group[r];
         // dependency of this item, if any
         const int* cnt = nullptr;
         int target = 0;
@@ -88,21 +83,20 @@ __device__ __forceinline__ void batch_loop(const BatchArgs& a, Run&& run) {
             __nanosleep(256);
           }
         }
+        if (!stop) s_desc = a.descs[(size_t)h * a.n_groups + g];
       }
       s_group = g;
       s_stop = stop;
-      if (!stop) s_desc = a.descs[(size_t)(item / a.items_per_holo) * a.n_groups + g];
     }
     __syncthreads();
     if (s_stop) return;
     const int item = s_item, g = s_group;
     const int h = item / a.items_per_holo;
     const BatchGroup gi = a.groups[g];
-    const PassDesc& d = s_desc;
     const int t0 = (item - h * a.items_per_holo - gi.first_item) * gi.chunk;
     const int t1 = min(t0 + gi.chunk, gi.tiles);
     for (int tile = t0; tile < t1; ++tile) {
-      run(d, gi.phase, gi.L, tile);
+      run(s_desc, gi.phase, gi.L, tile);
       __syncthreads();  // the next tile reuses the shared tile buffer
     }
     // The barrier orders every thread's stores before thread 0's device-scope

@@ -36,6 +36,7 @@ struct BatchGroup {
 struct BatchArgs {
   const PassDesc* descs;     // [n_holos][n_groups]
   const BatchGroup* groups;  // [n_groups] (x groups of views 0..V-1, then y groups)
+  const int* item_group;     // [items_per_holo] group of each item within a hologram
   int* done;                 // [n_holos][n_groups] completed items
   int* next;                 // item counter
   int* error;                // set to 1 when a bounded wait expires
