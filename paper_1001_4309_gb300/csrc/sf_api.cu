@@ -50,6 +50,11 @@ struct BatchState {
   const void* kfunc = nullptr;           // persistent kernel: general, or specialised to one length
   size_t ksmem = 0;                      // its dynamic shared memory
   std::vector<float2*> slot1;            // second intermediate slot per view
+  // two-stream batch: holograms per row-pass launch (sk) and their
+  // intermediate slots sslot[(group * sk + j) * n_views + v], group = chunk parity
+  int sk = 0;
+  std::vector<float2*> sslot;
+  void* d_sslot = nullptr;
   BatchGroup* d_groups = nullptr;
   int* d_item_group = nullptr;           // group of each item within a hologram
   int* d_error = nullptr;
@@ -283,6 +288,7 @@ void free_plan(sf_plan p) {
   if (p->batch.post) cudaEventDestroy(p->batch.post);
   if (p->batch.cap) cudaStreamDestroy(p->batch.cap);
   if (p->batch.d_fixed) cudaFree(p->batch.d_fixed);
+  if (p->batch.d_sslot) cudaFree(p->batch.d_sslot);
   for (void* s : p->staging) cudaFree(s);
   if (p->arena) cudaFree(p->arena);
   delete p;
@@ -609,6 +615,29 @@ bool persistent_eligible(sf_plan p, int L, PassKind kind, const PassBatch& b) {
   return true;
 }
 
+// One launch of the row pass over the descriptors of b (all FFT length L;
+// view_of[k] is descriptor k's view): the tensor-core pass on tensor-core
+// plans, the persistent bulk-copy pass where the plan chose it and the rows
+// allow it, else the one-tile-per-CTA pass.  max_rows: the most rows of any
+// descriptor.
+cudaError_t launch_row_pass(sf_plan plan, int axis, int L, PassBatch& b, const int* view_of, int max_rows,
+                            cudaStream_t s) {
+  const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
+  cudaError_t e;
+  if (plan->tc_frags && tc_length_supported(L)) {
+    for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[view_of[k]].hpos[axis];
+    const int G = tc_rows_per_cta(L);
+    e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tc_frags, s);
+  } else if (persistent_eligible(plan, L, kind, b)) {
+    e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);
+  } else {
+    const int G = pass_rows_per_cta(L);
+    e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
+  }
+  ++g_launches;
+  return e;
+}
+
 // Every view's pass along one axis (0: x, 1: y), launched in groups of views
 // with equal FFT length (at most max_per_launch views per launch).  Pass
 // sources: x reads `src` (the hologram) into work[v]; y reads work[v] into the
@@ -667,18 +696,7 @@ cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* 
       }
       max_rows = std::max(max_rows, d.rows);
     }
-    const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
-    if (plan->tc_frags && tc_length_supported(L)) {
-      for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[batch_view[k]].hpos[axis];
-      const int G = tc_rows_per_cta(L);
-      e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tc_frags, s);
-    } else if (persistent_eligible(plan, L, kind, b)) {
-      e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);
-    } else {
-      const int G = pass_rows_per_cta(L);
-      e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
-    }
-    ++g_launches;
+    e = launch_row_pass(plan, axis, L, b, batch_view, max_rows, s);
     if (e == cudaSuccess) e = after(batch_view, b.count);
   }
   return e;
@@ -810,12 +828,127 @@ int run_batch_persistent(sf_plan plan, const void* const* holos, int n_holos, vo
 // (and two intermediate slots), so one hologram's passes overlap the next's.
 // Enqueue the per-length launches of a batch on the plan's two streams,
 // forked from and joined back into s.
+// Holograms per row-pass launch of the two-stream batch.  When one
+// hologram's x pass is too small to fill the GPU (fewer CTAs than two waves
+// of two per SM), K holograms share each launch (K x n_views <= kMaxPassBatch
+// descriptors), each with its own intermediate slot; the two streams then
+// alternate chunks of K holograms, so 2 K slots per view are needed, the
+// extra ones within 512 MiB.  Sets b.sk and b.sslot.
+int ensure_stream_slots(sf_plan p) {
+  BatchState& b = p->batch;
+  if (b.sk) return SF_OK;
+  const int nv = (int)p->views.size();
+  long long ctas = 0;
+  size_t ws = 0;
+  for (const ViewState& vs : p->views) {
+    ctas += (vs.v.ny0 + pass_rows_per_cta(vs.ax[0].L) - 1) / std::max(1, pass_rows_per_cta(vs.ax[0].L));
+    ws += sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1;
+  }
+  const long long target = 2LL * 2 * std::max(1, p->sms);
+  int K = (int)std::min<long long>(kMaxPassBatch / nv, (target + ctas - 1) / std::max(1LL, ctas));
+  K = std::max(K, 1);
+  while (K > 1 && (size_t)(2 * K - 2) * ws > ((size_t)512 << 20)) --K;
+  std::vector<float2*> slots((size_t)2 * K * nv, nullptr);
+  for (int v = 0; v < nv; ++v) {
+    slots[(size_t)0 * nv + v] = p->views[v].work;
+    slots[(size_t)K * nv + v] = b.slot1[v];
+  }
+  if (K > 1) {
+    Arena ar;
+    std::vector<size_t> off(slots.size(), SIZE_MAX);
+    for (int grp = 0; grp < 2; ++grp)
+      for (int j = 1; j < K; ++j)
+        for (int v = 0; v < nv; ++v)
+          off[(size_t)(grp * K + j) * nv + v] = ar.take(sizeof(float2) * (size_t)p->views[v].v.ny0 * p->views[v].v.nx1);
+    if (cudaMalloc(&b.d_sslot, ar.off) != cudaSuccess) {
+      cudaGetLastError();
+      b.d_sslot = nullptr;
+      K = 1;  // fall back to one hologram per launch
+    } else {
+      for (size_t i = 0; i < slots.size(); ++i)
+        if (off[i] != SIZE_MAX) slots[i] = reinterpret_cast<float2*>(static_cast<char*>(b.d_sslot) + off[i]);
+    }
+  }
+  if (K == 1) {
+    slots.resize((size_t)2 * nv);
+    for (int v = 0; v < nv; ++v) {
+      slots[v] = p->views[v].work;
+      slots[(size_t)nv + v] = b.slot1[v];
+    }
+  }
+  b.sslot = slots;
+  b.sk = K;
+  return SF_OK;
+}
+
 cudaError_t enqueue_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
                                   float* const* intensity, float* const* phase, cudaStream_t s) {
   BatchState& b = plan->batch;
   const int nv = (int)plan->views.size();
   cudaError_t e = cudaEventRecord(b.fork, s);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b.st[k], b.fork, 0);
+  if (b.sk > 1) {
+    // chunks of K holograms, alternating streams; every (hologram, view) pass
+    // of a chunk and axis in launches of up to kMaxPassBatch descriptors of
+    // one FFT length
+    const int K = b.sk;
+    for (int c = 0; c * K < n_holos && e == cudaSuccess; ++c) {
+      const int h0 = c * K, h1 = std::min(n_holos, h0 + K), grp = c & 1;
+      for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis) {
+        std::vector<int> order(nv);
+        for (int v = 0; v < nv; ++v) order[v] = v;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return plan->views[x].ax[axis].L < plan->views[y].ax[axis].L; });
+        std::vector<std::pair<int, int>> items;  // (hologram, view), grouped by FFT length
+        for (int v : order)
+          for (int h = h0; h < h1; ++h) items.emplace_back(h, v);
+        for (size_t i = 0; i < items.size() && e == cudaSuccess;) {
+          const int L = plan->views[items[i].second].ax[axis].L;
+          PassBatch pb;
+          std::memset(&pb, 0, sizeof(pb));
+          int view_of[kMaxPassBatch];
+          int max_rows = 0;
+          while (i < items.size() && pb.count < kMaxPassBatch && plan->views[items[i].second].ax[axis].L == L) {
+            const int h = items[i].first, v = items[i].second;
+            const ViewState& vs = plan->views[v];
+            const AxisCoef& co = vs.ax[axis];
+            float2* slot = b.sslot[(size_t)(grp * K + (h - h0)) * nv + v];
+            PassDesc& d = pb.d[pb.count];
+            view_of[pb.count++] = v;
+            d.cin = co.cin;
+            d.cout = co.cout;
+            d.H = co.H;
+            d.n0 = co.n0;
+            d.n1 = co.n1;
+            if (axis == 0) {
+              d.src = holos[h];
+              d.dst = slot;
+              d.rows = vs.v.ny0;
+              d.src_ld = vs.v.nx0;
+              d.dst_ld = vs.v.ny0;
+            } else {
+              const size_t o = (size_t)h * nv + v;
+              d.src = slot;
+              d.dst = view_out ? static_cast<float2*>(view_out[o]) : nullptr;
+              d.inten = intensity ? intensity[o] : nullptr;
+              d.phase = phase ? phase[o] : nullptr;
+              d.rows = vs.v.nx1;
+              d.src_ld = vs.v.ny0;
+              d.dst_ld = vs.v.nx1;
+            }
+            max_rows = std::max(max_rows, d.rows);
+            ++i;
+          }
+          e = launch_row_pass(plan, axis, L, pb, view_of, max_rows, b.st[grp]);
+        }
+      }
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(b.join[k], b.st[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.join[k], 0);
+    }
+    return e;
+  }
   std::vector<float2*> work(nv), dout(nv);
   std::vector<float*> dint(nv), dph(nv);
   auto none = [](const int*, int) { return cudaSuccess; };
@@ -847,6 +980,7 @@ int run_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void*
                       float* const* intensity, float* const* phase, cudaStream_t s) {
   int rc = batch_prepare(plan, n_holos, false);
   if (rc) return rc;
+  if ((rc = ensure_stream_slots(plan))) return rc;
   BatchState& b = plan->batch;
   const size_t n = (size_t)n_holos * plan->views.size();
   std::vector<const void*> key;

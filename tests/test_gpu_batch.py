@@ -180,6 +180,28 @@ def test_batch_one_length_kernel(P, general, cplx, monkeypatch):
         sf.close()
 
 
+@pytest.mark.parametrize("n_holos", [1, 20, 37])
+def test_batch_streams_many_small_holograms(P, n_holos, monkeypatch):
+    """Small views: the two-stream batch puts up to 16 holograms in each row-pass
+    launch (each with its own intermediate slot; chunks alternate streams).
+    Equal to per-hologram execute for a partial last chunk and over replays."""
+    import torch
+    monkeypatch.setenv("SF_BATCH_IMPL", "streams")
+    n = 256
+    vs = [view(WAVELENGTH, -0.05, PITCH, 2.325e-6, o1=(1e-4, -5e-5), n0=(n, n), n1=(n, n))]
+    sf = P.ShiftedFresnel(vs)
+    try:
+        holos = holograms(n_holos, shape=(n, n), seed=90)
+        ref = per_hologram(sf, holos)
+        outs = sf.alloc_batch_outputs(n_holos, field=True, intensity=True)
+        for _ in range(3):  # capture, then replays
+            sf.execute_batch(holos, outs)
+            torch.cuda.synchronize()
+            check_equal(outs, ref)
+    finally:
+        sf.close()
+
+
 def test_batch_rejects_bad_arguments(P):
     import torch
     vs = ragged_views()[:2]
