@@ -187,7 +187,10 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
  *   streams     execute's per-length row-pass kernels, even holograms on one
  *               plan-owned stream and odd ones on another (one intermediate
  *               slot each), joined back into `stream`; consecutive holograms
- *               overlap.  The launches are captured as a CUDA graph on a
+ *               overlap.  When one hologram's passes are too small to fill
+ *               the GPU, chunks of up to 16 / n_views holograms share each
+ *               launch (one slot per hologram of a chunk; the first call
+ *               allocates the extra slots, at most 512 MiB).  The launches are captured as a CUDA graph on a
  *               plan-owned stream and the graph is replayed while calls pass
  *               the same hologram count and buffers (other calls capture
  *               anew).  Any FFT length.
