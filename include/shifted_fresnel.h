@@ -178,7 +178,8 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
  *               for the y pass of hologram h - 2 (two intermediate slots per
  *               view).  The waits are bounded; if one expires the launch
  *               ends early and shifted_fresnel_batch_status reports
- *               SF_ERR_TIMEOUT.  FFT lengths up to 6144.  When every pass of
+ *               SF_ERR_TIMEOUT.  FFT lengths up to 6144, FP32 plans only
+ *               (tensor-core plans run the streams implementation).  When every pass of
  *               every view has one power-of-two length 512 .. 4096 and
  *               n0, n1 <= L / 2, a kernel specialised to that length (with
  *               the pruned network) runs instead of the general one
@@ -210,7 +211,8 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
  * Every (hologram, view) needs at least one non-NULL output.  All buffers
  * must be device memory of the plan's device (SF_ERR_INVALID_ARG otherwise).
  * Views may have different sizes (ragged).  The persistent kernel forced on
- * a plan with an FFT length above 6144 returns SF_ERR_UNSUPPORTED_SIZE.
+ * a plan with an FFT length above 6144, or on a tensor-core plan, returns
+ * SF_ERR_UNSUPPORTED_SIZE.
  *
  * The first call allocates per-view second intermediate slots and two
  * streams; the persistent kernel also allocates, per n_holos, descriptor

@@ -452,6 +452,7 @@ long long env_ll(const char* name, long long dflt) {
 // memcpy(descriptors <- pinned table), memset(counters), persistent kernel.
 // Every FFT length of the plan fits the persistent batch kernel.
 bool batch_persistent_supported(sf_plan p) {
+  if (p->tc_frags) return false;  // its tiles are the FP32 network only
   for (const ViewState& vs : p->views)
     for (int ph = 0; ph < 2; ++ph)
       if (!batch_length_supported(vs.ax[ph].L)) return false;

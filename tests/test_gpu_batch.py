@@ -202,6 +202,28 @@ def test_batch_streams_many_small_holograms(P, n_holos, monkeypatch):
         sf.close()
 
 
+def test_batch_tensor_core_plan(P, monkeypatch):
+    """A tensor-core plan batches through the streams implementation (bit-identical
+    to its per-hologram execute); the persistent kernel, FP32 only, refuses it."""
+    import torch
+    n = 1024
+    vs = [view(WAVELENGTH, z, PITCH, p1, n0=(n, n), n1=(n, n)) for z, p1 in ((0.03, 4.65e-6), (0.07, 1e-6))]
+    sf = P.ShiftedFresnel(vs, precision=P.SF_PREC_FP16TC)
+    try:
+        holos = holograms(3, shape=(n, n), seed=30)
+        ref = per_hologram(sf, holos)
+        outs = sf.alloc_batch_outputs(3, field=True, intensity=True)
+        sf.execute_batch(holos, outs)
+        torch.cuda.synchronize()
+        check_equal(outs, ref)
+        monkeypatch.setenv("SF_BATCH_IMPL", "persistent")
+        rc = P.shifted_fresnel_execute_batch(sf.handle, [h.data_ptr() for h in holos],
+                                             [o.data_ptr() for row in outs["field"] for o in row], check=False)
+        assert rc == P.SF_ERR_UNSUPPORTED_SIZE
+    finally:
+        sf.close()
+
+
 def test_batch_rejects_bad_arguments(P):
     import torch
     vs = ragged_views()[:2]
