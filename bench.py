@@ -42,32 +42,34 @@ PAPER_CONTEXT = {  # the paper's own figures (Section 3), other hardware: contex
            "(2x GTX 295, CUDA 2.3, CUFFT), loop including host copies",
     "cpu": "the same four views in 9,542 ms (about 0.42 views/s) on a Core2Quad Q6600"}
 PAPER_GPU_VIEWS_PER_S = 4 / 0.060  # the paper's four views in about 60 ms, host copies included
-ERROR_COLS = 8  # columns per sampled block (first, middle, last block of every view)
+
+
+_ORACLE_VIEWS = {}  # (id of hologram, view) -> (hologram, oracle view): each whole view computed once
+
+
+def oracle_view(holo_np, v):
+    """The FP64 oracle's whole complex view of hologram holo_np (cached per hologram object and view)."""
+    import oracle
+    oracle.build()
+    key = (id(holo_np), tuple(sorted(v.items())))
+    hit = _ORACLE_VIEWS.get(key)
+    if hit is None or hit[0] is not holo_np:
+        hit = (holo_np, oracle.forward(holo_np, v))
+        _ORACLE_VIEWS[key] = hit
+    return hit[1]
 
 
 def view_errors(holo_np, views, fields):
     """Per view: relative L2 and max-abs error (relative to the largest reference magnitude) of the
-    complex field against the FP64 oracle, on three blocks of output columns (first, middle, last)."""
+    complex field against the FP64 oracle, over every pixel of the view."""
     import numpy as np
-    import oracle
-    oracle.build()
     out = []
     for v, f in zip(views, fields):
-        n = v["nx1"]
-        w = min(ERROR_COLS, n)
-        blocks = sorted({(0, w), (n // 2 - w // 2, n // 2 - w // 2 + w), (n - w, n)})
-        num = den = 0.0
-        mx_err = mx_ref = 0.0
-        for c0, c1 in blocks:
-            r = oracle.forward(holo_np, v, cols=(c0, c1))
-            g = f[:, c0:c1].astype(np.complex128)
-            num += float(np.sum(np.abs(g - r) ** 2))
-            den += float(np.sum(np.abs(r) ** 2))
-            mx_err = max(mx_err, float(np.max(np.abs(g - r))))
-            mx_ref = max(mx_ref, float(np.max(np.abs(r))))
-        out.append({"view": f"{v['nx1']}x{v['ny1']} z={v['z']:g}", "rel_l2": float(f"{(num / den) ** 0.5:.3e}"),
-                    "max_abs_rel": float(f"{mx_err / mx_ref:.3e}"),
-                    "sample": f"columns {', '.join(f'{c0}-{c1 - 1}' for c0, c1 in blocks)}"})
+        r = oracle_view(holo_np, v)
+        d = np.abs(f.astype(np.complex128) - r)
+        out.append({"view": f"{v['nx1']}x{v['ny1']} z={v['z']:g}",
+                    "rel_l2": float(f"{np.linalg.norm(d) / np.linalg.norm(r):.3e}"),
+                    "max_abs_rel": float(f"{d.max() / np.abs(r).max():.3e}"), "sample": "whole view"})
     return out
 
 
@@ -634,6 +636,7 @@ def differentiable(dev, stream):
         z_err = max(abs(float(a) - b) for a, b in zip(zf.cpu(), z_true))
     finally:
         sf.close()
+    retrieval = inline_retrieval(dev)
     return {"workload": "complex 1024^2 object, 4 views (z = 3/5/7/10 cm, 1 um pitch)",
             "forward_plus_adjoint_with_dz_ms": round(ms, 4),
             "phase_retrieval": {"iterations": 200, "seconds": round(secs, 3), "ms_per_iteration": round(secs * 5, 3),
@@ -641,7 +644,58 @@ def differentiable(dev, stream):
                                 "loss_first": float(f"{losses[0]:.4e}"), "loss_last": float(f"{losses[-1]:.4e}")},
             "depth_fit": {"iterations": 100, "ms_per_iteration": round(zsecs * 10, 3), "start": "z x 1.02",
                           "max_abs_z_error_m": float(f"{z_err:.3e}"),
-                          "what": "Adam on dL/dz from the adjoint, plan re-targeted each step"}}
+                          "what": "Adam on dL/dz from the adjoint, plan re-targeted each step"},
+            "retrieval_error": retrieval}
+
+
+def aligned_error(u, ref):
+    """Relative L2 error of u against ref after the best global complex scale."""
+    import numpy as np
+    u = u.ravel().astype(np.complex128)
+    ref = ref.ravel().astype(np.complex128)
+    alpha = np.vdot(u, ref) / np.vdot(u, u)
+    return float(np.linalg.norm(alpha * u - ref) / np.linalg.norm(ref))
+
+
+def inline_retrieval(dev):
+    """Twin-image suppression on the multi-depth in-line set (1024^2 object, views at the hologram pitch,
+    z = 3/5/7/10 cm): object error of 200 retrieval iterations from a flat start against back-propagating
+    the 5 cm hologram alone.  The measured intensities here are this library's FP32 forward of the known
+    object with 2000-photon noise (the GPU test makes them with the FP64 oracle instead)."""
+    import time as _t
+    import numpy as np
+    import torch
+    import synth
+    import paper_1001_4309_gb300 as P
+    from paper_1001_4309_gb300.autograd import phase_retrieval
+    obj, vs = synth.config_c5_inline(1024)
+    vs = [dict(v, flags=P.SF_IN_COMPLEX | P.SF_NO_PREFACTOR) for v in vs]
+    sf = P.ShiftedFresnel(vs, device=dev.index)
+    bp_sf = P.ShiftedFresnel([dict(vs[1], z=-vs[1]["z"])], device=dev.index)
+    try:
+        fields = sf.reconstruct(torch.from_numpy(obj.astype(np.complex64)).to(dev))["field"]
+        meas = [synth.poisson_intensity((f.abs() ** 2).double().cpu().numpy(), 2000, seed=40 + k)
+                for k, f in enumerate(fields)]
+        scale = float(np.mean([m.mean() for m in meas]))
+        I = [torch.from_numpy((m / scale).astype(np.float32)).to(dev) for m in meas]
+        bp = bp_sf.reconstruct(torch.from_numpy(np.sqrt(meas[1] / scale).astype(np.complex64)).to(dev))["field"][0]
+        e_bp = aligned_error(bp.cpu().numpy(), obj)
+        u0 = torch.ones((1024, 1024), dtype=torch.complex64, device=dev)
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        u, losses = phase_retrieval(sf, I, n_iter=200, u_init=u0, lr=0.1)
+        torch.cuda.synchronize()
+        secs = _t.perf_counter() - t0
+        e_pr = aligned_error(u.cpu().numpy(), obj)
+    finally:
+        sf.close()
+        bp_sf.close()
+    return {"workload": "in-line holograms of a known 1024^2 amplitude-and-phase object at z = 3/5/7/10 cm, "
+                        "views at the hologram pitch, 2000-photon noise",
+            "object_rel_l2_backpropagation_5cm": round(e_bp, 4), "object_rel_l2_retrieval_200": round(e_pr, 4),
+            "retrieval_over_backpropagation": round(e_pr / e_bp, 3), "ms_per_iteration": round(secs * 5, 3),
+            "measure": "relative L2 against the known object after the best global complex scale",
+            "loss_first": float(f"{losses[0]:.4e}"), "loss_last": float(f"{losses[-1]:.4e}")}
 
 
 def plain_path(holo, views, outs, flush, stream, a, step_bytes, hbm_peak, ours_per_gpu):
@@ -682,7 +736,10 @@ def cpu_baseline(holo_np, views, min_seconds):
     t0 = time.perf_counter()
     n_views = 0
     while True:
-        oracle.forward(holo_np, views[n_views % len(views)])
+        v = views[n_views % len(views)]
+        r = oracle.forward(holo_np, v)
+        if n_views < len(views):  # keep the first pass for the accuracy figures
+            _ORACLE_VIEWS[(id(holo_np), tuple(sorted(v.items())))] = (holo_np, r)
         n_views += 1
         if time.perf_counter() - t0 >= min_seconds or n_views >= 400:
             break

@@ -33,6 +33,31 @@ def _follow_z(sf, z):
         sf.update([dict(v, z=a) for v, a in zip(sf.views, zv)])
 
 
+def _save_plan_state(ctx, sf, z):
+    """Record the views the forward pass ran with, and z's device and dtype."""
+    ctx.sf = sf
+    ctx.views = [dict(v) for v in sf.views]
+    ctx.z_meta = (z.device, z.dtype) if isinstance(z, torch.Tensor) else None
+
+
+def _restore_plan_state(ctx):
+    """Put the plan back on the forward pass's views when another forward
+    re-targeted it in between (two losses at different z before one backward):
+    the adjoint and dL/dz must use the depths the views were computed at."""
+    sf = ctx.sf
+    if sf.views != ctx.views:
+        sf.update([dict(v) for v in ctx.views])
+    return sf
+
+
+def _grad_z_out(ctx, grad_z):
+    """dL/dz on z's own device and dtype (z may live on the host)."""
+    if grad_z is None or ctx.z_meta is None:
+        return grad_z
+    device, dtype = ctx.z_meta
+    return grad_z.to(device=device, dtype=dtype)
+
+
 class ShiftedFresnelFunction(torch.autograd.Function):
     """views = ShiftedFresnelFunction.apply(u0, z, sf) -> tuple of complex64 view fields."""
 
@@ -43,17 +68,17 @@ class ShiftedFresnelFunction(torch.autograd.Function):
         _follow_z(sf, z)
         u0c = u0.contiguous()
         outs = sf.reconstruct(u0c, field=True)
-        ctx.sf = sf
+        _save_plan_state(ctx, sf, z)
         ctx.save_for_backward(u0c)
         return tuple(outs["field"])
 
     @staticmethod
     def backward(ctx, *grads):
         (u0,) = ctx.saved_tensors
-        sf = ctx.sf
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         if not (need_u or need_z):
             return None, None, None
+        sf = _restore_plan_state(ctx)
         gs = [g.contiguous() if g is not None else None for g in grads]
         grad_u = torch.empty_like(u0) if need_u else None
         grad_z = torch.zeros(len(sf.views), dtype=torch.float64, device=u0.device) if need_z else None
@@ -62,7 +87,7 @@ class ShiftedFresnelFunction(torch.autograd.Function):
                                 grad_u.data_ptr() if need_u else None,
                                 grad_z.data_ptr() if need_z else None,
                                 stream=torch.cuda.current_stream(u0.device).cuda_stream)
-        return grad_u, grad_z, None
+        return grad_u, _grad_z_out(ctx, grad_z), None
 
 
 def views(u0, sf, z=None):
@@ -71,63 +96,82 @@ def views(u0, sf, z=None):
 
 
 class IntensityLossFunction(torch.autograd.Function):
-    """loss = IntensityLossFunction.apply(u0, z, sf, intensities): the fused multi-depth intensity loss.
+    """loss = IntensityLossFunction.apply(u0, z, sf, intensities, recompute): the fused multi-depth intensity loss.
 
     Forward: execute, then shifted_fresnel_intensity_loss (loss in double
     precision and the view gradients 4 (|u|^2 - I) u in one kernel per view).
     Backward: shifted_fresnel_adjoint of those view gradients (and dL/dz when
-    z requires it), scaled by the incoming gradient.
+    z requires it), scaled by the incoming gradient.  With ``recompute`` the
+    forward pass keeps nothing of view size (it computes the loss alone) and
+    the backward pass recomputes the view fields and their gradients first:
+    one more execute per step for V fewer view-sized buffers held between the
+    passes.
     """
 
     @staticmethod
-    def forward(ctx, u0, z, sf, intensities):
+    def forward(ctx, u0, z, sf, intensities, recompute=False):
         if not (sf.views[0].get("flags", 0) & SF_IN_COMPLEX):
             raise ValueError("the plan must take a complex object (SF_IN_COMPLEX)")
         _follow_z(sf, z)
         u0c = u0.contiguous()
-        fields = sf.reconstruct(u0c, field=True)["field"]
         meas = [I.contiguous() for I in intensities]
-        need = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
-        grads = [torch.empty_like(f) for f in fields] if need else None
-        loss = torch.empty((), dtype=torch.float64, device=u0c.device)
-        shifted_fresnel_intensity_loss(sf.handle, [f.data_ptr() for f in fields], [I.data_ptr() for I in meas],
-                                       [g.data_ptr() for g in grads] if grads else None, loss.data_ptr(),
-                                       stream=torch.cuda.current_stream(u0c.device).cuda_stream)
-        ctx.sf = sf
+        need = (ctx.needs_input_grad[0] or ctx.needs_input_grad[1]) and not recompute
+        grads, loss = _loss_and_view_grads(sf, u0c, meas, need)
+        _save_plan_state(ctx, sf, z)
         ctx.grads = grads
+        ctx.meas = meas if recompute else None
         ctx.save_for_backward(u0c)
         return loss
 
     @staticmethod
     def backward(ctx, grad_loss):
         (u0,) = ctx.saved_tensors
-        sf = ctx.sf
         need_u, need_z = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         if not (need_u or need_z):
-            return None, None, None, None
+            return None, None, None, None, None
+        sf = _restore_plan_state(ctx)
+        grads = ctx.grads
+        if grads is None:  # recompute: the views and their gradients at the forward pass's depths
+            grads, _ = _loss_and_view_grads(sf, u0, ctx.meas, True)
         grad_u = torch.empty_like(u0) if need_u else None
         grad_z = torch.zeros(len(sf.views), dtype=torch.float64, device=u0.device) if need_z else None
-        shifted_fresnel_adjoint(sf.handle, u0.data_ptr() if need_z else None, [g.data_ptr() for g in ctx.grads],
+        shifted_fresnel_adjoint(sf.handle, u0.data_ptr() if need_z else None, [g.data_ptr() for g in grads],
                                 grad_u.data_ptr() if need_u else None, grad_z.data_ptr() if need_z else None,
                                 stream=torch.cuda.current_stream(u0.device).cuda_stream)
+        ctx.grads = None
         if need_u:
             grad_u.mul_(grad_loss.to(grad_u.real.dtype))
         if need_z:
-            grad_z.mul_(grad_loss)
-        return grad_u, grad_z, None, None
+            grad_z.mul_(grad_loss.to(grad_z.device))
+        return grad_u, _grad_z_out(ctx, grad_z), None, None, None
 
 
-def intensity_loss(u0, sf, intensities, z=None):
-    """sum_v || |A_v u0|^2 - I_v ||^2 (the loss of the multi-depth phase retrieval), float64 scalar."""
-    return IntensityLossFunction.apply(u0, z, sf, intensities)
+def _loss_and_view_grads(sf, u0, meas, want_grads):
+    """Execute the plan on u0, then the fused loss kernel: (view gradients or None, float64 loss)."""
+    fields = sf.reconstruct(u0, field=True)["field"]
+    grads = [torch.empty_like(f) for f in fields] if want_grads else None
+    loss = torch.empty((), dtype=torch.float64, device=u0.device)
+    shifted_fresnel_intensity_loss(sf.handle, [f.data_ptr() for f in fields], [I.data_ptr() for I in meas],
+                                   [g.data_ptr() for g in grads] if grads else None, loss.data_ptr(),
+                                   stream=torch.cuda.current_stream(u0.device).cuda_stream)
+    return grads, loss
+
+
+def intensity_loss(u0, sf, intensities, z=None, recompute=False):
+    """sum_v || |A_v u0|^2 - I_v ||^2 (the loss of the multi-depth phase retrieval), float64 scalar.
+
+    ``recompute=True`` holds no view-sized buffer between forward and backward
+    (the backward pass recomputes the views)."""
+    return IntensityLossFunction.apply(u0, z, sf, intensities, recompute)
 
 
 def phase_retrieval(sf, intensities, n_iter=200, u_init=None, lr=0.05, recompute=False, callback=None):
     """Fit a complex object to measured view intensities by gradient descent (Adam).
 
-    ``recompute=True`` keeps no view fields between forward and backward
-    (they are recomputed in backward through torch.utils.checkpoint), for
-    memory-bound view sets.  Returns (u, losses).
+    ``recompute=True`` keeps no view fields or view gradients between
+    forward and backward (the backward pass recomputes them: one more execute
+    per iteration), for view sets whose buffers do not fit beside the object.
+    Returns (u, losses).
     """
     v0 = sf.views[0]
     if u_init is None:
@@ -137,11 +181,7 @@ def phase_retrieval(sf, intensities, n_iter=200, u_init=None, lr=0.05, recompute
     losses = []
     for it in range(n_iter):
         opt.zero_grad(set_to_none=True)
-        if recompute:
-            from torch.utils.checkpoint import checkpoint
-            loss = checkpoint(lambda x: intensity_loss(x, sf, intensities), u, use_reentrant=False)
-        else:
-            loss = intensity_loss(u, sf, intensities)
+        loss = intensity_loss(u, sf, intensities, recompute=recompute)
         loss.backward()
         opt.step()
         losses.append(loss.detach())

@@ -21,4 +21,7 @@ from .gabor import (  # noqa: F401
     config_c3,
     config_c4,
     config_c5,
+    config_c5_inline,
+    retrieval_object,
+    poisson_intensity,
 )

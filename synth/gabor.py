@@ -232,3 +232,36 @@ def config_c5(n=1024):
     t = bars_disks_object(n, rng) * np.exp(1j * 0.5 * rng.standard_normal() )
     views = [view(WAVELENGTH, z, PITCH, 1.0e-6, n0=(n, n), n1=(n, n)) for z in (0.03, 0.05, 0.07, 0.10)]
     return t, views
+
+
+def retrieval_object(n, seed):
+    """Mixed amplitude and phase object for multi-depth retrieval, complex128 [n, n].
+
+    Amplitude 1 on the background and 0.3 inside random bars and disks
+    (``bars_disks_object``); phase from the smooth random-phase blobs of
+    ``target_blobs_object`` (peak phase within +-pi/2).
+    """
+    rng = np.random.default_rng(seed)
+    t = bars_disks_object(n, rng)
+    phase = np.angle(target_blobs_object(n, rng))
+    return np.where(np.abs(t) > 0, 1.0, 0.3) * np.exp(1j * phase)
+
+
+def poisson_intensity(I, photons, seed):
+    """Photon noise at a mean count of ``photons`` per pixel: Poisson(photons I / mean I) mean I / photons."""
+    rng = np.random.default_rng(seed)
+    s = float(np.mean(I))
+    return rng.poisson(photons * I / s) * (s / photons)
+
+
+def config_c5_inline(n=1024):
+    """Multi-depth in-line (Gabor) retrieval set: the object of ``retrieval_object``
+    and four views at z = 3, 5, 7, 10 cm with the hologram's own pitch and no
+    offset (the in-line recording geometry; every view covers the whole object).
+
+    Returns (object complex128, views).  Callers add the measured intensities
+    (with ``poisson_intensity`` at 2000 photons) from a model of their choice.
+    """
+    obj = retrieval_object(n, seed=4 * 1000 + 1)
+    views = [view(WAVELENGTH, z, PITCH, PITCH, n0=(n, n), n1=(n, n)) for z in (0.03, 0.05, 0.07, 0.10)]
+    return obj, views

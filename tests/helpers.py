@@ -27,3 +27,12 @@ def header_functions(path):
     src = open(path).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(shifted_fresnel_\w+)\s*\(", src, flags=re.M)))
+
+
+def aligned_rel_l2(u, ref):
+    """Relative L2 error of u against ref after the best global complex scale
+    (least squares: alpha = <u, ref> / <u, u>), i.e. up to global phase and amplitude."""
+    u = np.asarray(u, dtype=np.complex128).ravel()
+    ref = np.asarray(ref, dtype=np.complex128).ravel()
+    alpha = np.vdot(u, ref) / np.vdot(u, u)
+    return float(np.linalg.norm(alpha * u - ref) / np.linalg.norm(ref))

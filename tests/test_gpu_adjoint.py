@@ -8,7 +8,11 @@
   vs central finite differences of the loss in z (relative step 1e-3 per
   side, plans rebuilt at z +- h).
 * torch.autograd gradient of the intensity loss vs finite differences.
-* 200 iterations of multi-depth phase retrieval on the 1024^2 object.
+* The same object gradient and dL/dz at the full 1024^2, four-depth size
+  against the oracle, and its autograd gradients against finite differences.
+* 200 iterations of multi-depth phase retrieval on the 1024^2 object, and
+  the twin-image test: multi-depth retrieval against single-hologram
+  back-propagation on in-line holograms made by the oracle.
 """
 
 import numpy as np
@@ -17,7 +21,7 @@ import pytest
 import oracle
 import synth
 from synth import view, random_field, WAVELENGTH, PITCH
-from helpers import rel_l2
+from helpers import rel_l2, aligned_rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -170,25 +174,197 @@ def test_autograd_matches_finite_differences(P):
     sf.close()
 
 
+@pytest.fixture(scope="module")
+def c5():
+    """The 1024^2 four-depth workload (3, 5, 7, 10 cm at 1 um view pitch): its
+    views, intensities of the known object from the FP64 oracle, a trial
+    object u (the known one perturbed, rounded to complex64) and the view
+    gradients g_v = 4 (|A_v u|^2 - I_v) A_v u of the intensity loss at u,
+    also from the oracle."""
+    t, vs = synth.config_c5()
+    vs = [dict(v, flags=CPLX | NOPRE) for v in vs]
+    meas = [np.abs(oracle.forward(t, v)) ** 2 for v in vs]
+    rng = np.random.default_rng(55)
+    u = (t * (1 + 0.1 * rng.standard_normal(t.shape)) + 0.05 * random_field(*t.shape, seed=56)).astype(np.complex64)
+    gs = []
+    for v, I in zip(vs, meas):
+        u1 = oracle.forward(u, v)
+        gs.append(4 * (np.abs(u1) ** 2 - I) * u1)
+    return t, vs, meas, u, gs
+
+
+def test_adjoint_and_grad_z_paper_scale(P, c5):
+    """Object gradient sum_v A_v^H g_v and dL/dz of all four depths at the full
+    1024^2 size against the FP64 oracle's adjoint and z-derivative."""
+    _, vs, _, u, gs = c5
+    got, gz = gpu_adjoint(P, vs, gs, holo=to_dev(u), want_z=True)
+    ref = sum(oracle.adjoint(g.astype(np.complex64), v) for g, v in zip(gs, vs))
+    err = rel_l2(got, ref)
+    print(f"object gradient rel-L2 {err:.3e}")
+    assert err <= TOL
+    for i, v in enumerate(vs):
+        r = oracle_dldz(u, gs[i].astype(np.complex64), v)
+        print(f"z = {v['z']}: dL/dz {gz[i]:.6e} oracle {r:.6e} rel {abs(gz[i] - r) / abs(r):.2e}")
+        assert abs(gz[i] - r) <= 1e-3 * abs(r), (i, gz[i], r)
+
+
+def test_autograd_paper_scale_vs_finite_differences(P, c5):
+    """torch.autograd gradients of the intensity loss at 1024^2 and four depths
+    against central finite differences of the GPU loss: a random direction in
+    u (step 1e-3 of the object's RMS) and each z (relative step 1e-3)."""
+    import torch
+    from paper_1001_4309_gb300.autograd import intensity_loss
+    _, vs, meas, u_np, _ = c5
+    I = [to_dev(m, complex_=False) for m in meas]
+    sf = P.ShiftedFresnel(vs)
+    try:
+        zs = [v["z"] for v in vs]
+        z = torch.tensor(zs, dtype=torch.float64, device="cuda", requires_grad=True)
+        u = to_dev(u_np).requires_grad_(True)
+        intensity_loss(u, sf, I, z).backward()
+        u0 = u.detach()
+        d = to_dev(random_field(*u_np.shape, seed=57)) * (1e-3 * float(np.sqrt(np.mean(np.abs(u_np) ** 2))))
+        with torch.no_grad():
+            lp = float(intensity_loss(u0 + d, sf, I))
+            lm = float(intensity_loss(u0 - d, sf, I))
+        fd = (lp - lm) / 2
+        an = float(torch.real(torch.vdot(u.grad.flatten(), d.flatten())))
+        print(f"direction: fd {fd:.6e} autograd {an:.6e}")
+        assert abs(fd - an) <= 1e-2 * abs(an), (fd, an)
+        for i, z0 in enumerate(zs):
+            h = 1e-3 * z0
+            vals = []
+            for sgn in (1, -1):
+                zz = torch.tensor(zs, dtype=torch.float64)
+                zz[i] = z0 + sgn * h
+                with torch.no_grad():
+                    vals.append(float(intensity_loss(u0, sf, I, zz)))
+            fdz = (vals[0] - vals[1]) / (2 * h)
+            print(f"z = {z0}: fd {fdz:.6e} autograd {float(z.grad[i]):.6e}")
+            assert abs(fdz - float(z.grad[i])) <= 1e-2 * abs(fdz), (i, fdz, float(z.grad[i]))
+    finally:
+        sf.close()
+
+
 def test_phase_retrieval_200_iterations_paper_scale(P):
-    """Four depths (3, 5, 7, 10 cm) at 1 um view pitch from a known 1024^2 object."""
+    """Config-5 geometry: the 1024^2 object seen at four depths (3, 5, 7, 10 cm)
+    at 1 um view pitch, intensities of the known object from the FP64 oracle;
+    200 Adam iterations from a flat start lower the loss tenfold."""
     import torch
     from paper_1001_4309_gb300.autograd import phase_retrieval
     t, vs = synth.config_c5()
     vs = [dict(v, flags=CPLX | NOPRE) for v in vs]
+    meas = [np.abs(oracle.forward(t, v)) ** 2 for v in vs]
+    scale = float(np.mean([m.mean() for m in meas]))
+    I = [to_dev(m / scale, complex_=False) for m in meas]
     sf = P.ShiftedFresnel(vs)
     try:
-        truth = to_dev(t)
-        I = [o.abs() ** 2 for o in sf.reconstruct(truth)["field"]]
-        scale = float(sum(x.mean() for x in I) / len(I))
-        I = [x / scale for x in I]
-        u_init = torch.ones_like(truth) / scale ** 0.5
+        u_init = torch.ones((t.shape[0], t.shape[1]), dtype=torch.complex64, device="cuda") / scale ** 0.5
         u, losses = phase_retrieval(sf, I, n_iter=200, u_init=u_init, lr=0.05 / scale ** 0.5)
         torch.cuda.synchronize()
     finally:
         sf.close()
     assert np.all(np.isfinite(losses))
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def inline_measurements(P):
+    """The multi-depth in-line set at 1024^2: views at the hologram pitch, and
+    intensities of the known object from the FP64 oracle with photon noise at
+    a mean of 2000 photons per pixel, scaled to unit mean."""
+    obj, vs = synth.config_c5_inline(1024)
+    vs = [dict(v, flags=CPLX | NOPRE) for v in vs]
+    meas = [synth.poisson_intensity(np.abs(oracle.forward(obj, v)) ** 2, 2000, seed=40 + k)
+            for k, v in enumerate(vs)]
+    scale = float(np.mean([m.mean() for m in meas]))
+    return obj, vs, [m / scale for m in meas], scale
+
+
+def test_multi_depth_retrieval_suppresses_twin_image(P):
+    """In-line holograms of a known amplitude-and-phase object at 3, 5, 7 and
+    10 cm (FP64 oracle, 2000-photon noise).  Back-propagating the 5 cm hologram
+    alone (its amplitude, by z = -5 cm) leaves the twin image in the object;
+    200 iterations of the multi-depth intensity retrieval from a flat start
+    must reach at most half of that object error (both measured after the
+    best global complex scale)."""
+    import torch
+    from paper_1001_4309_gb300.autograd import phase_retrieval
+    obj, vs, meas, scale = inline_measurements(P)
+    n = obj.shape[0]
+    bp_view = dict(vs[1], z=-vs[1]["z"])
+    bp_sf = P.ShiftedFresnel([bp_view])
+    try:
+        bp = bp_sf.reconstruct(to_dev(np.sqrt(meas[1]).astype(np.complex64)))["field"][0].cpu().numpy()
+    finally:
+        bp_sf.close()
+    e_bp = aligned_rel_l2(bp, obj)
+    sf = P.ShiftedFresnel(vs)
+    try:
+        I = [to_dev(m, complex_=False) for m in meas]
+        u_init = torch.ones((n, n), dtype=torch.complex64, device="cuda")
+        u, losses = phase_retrieval(sf, I, n_iter=200, u_init=u_init, lr=0.1)
+        torch.cuda.synchronize()
+    finally:
+        sf.close()
+    e_pr = aligned_rel_l2(u.cpu().numpy(), obj)
+    print(f"object error: back-propagation {e_bp:.4f}, retrieval {e_pr:.4f}; loss {losses[0]:.4e} -> {losses[-1]:.4e}")
+    assert np.all(np.isfinite(losses))
+    assert e_pr <= 0.5 * e_bp, (e_pr, e_bp)
+
+
+def test_phase_retrieval_recompute_matches_stored_views(P):
+    """recompute=True (no view-sized buffers kept between forward and backward)
+    follows the same trajectory as keeping the view gradients."""
+    import torch
+    from paper_1001_4309_gb300.autograd import phase_retrieval
+    obj, vs = synth.config_c5_inline(256)
+    vs = [dict(v, flags=CPLX | NOPRE) for v in vs]
+    meas = [np.abs(oracle.forward(obj, v)) ** 2 for v in vs]
+    scale = float(np.mean([m.mean() for m in meas]))
+    I = [to_dev(m / scale, complex_=False) for m in meas]
+    sf = P.ShiftedFresnel(vs)
+    try:
+        runs = []
+        for recompute in (False, True):
+            u_init = torch.ones((256, 256), dtype=torch.complex64, device="cuda")
+            u, losses = phase_retrieval(sf, I, n_iter=20, u_init=u_init, lr=0.1, recompute=recompute)
+            runs.append((u.cpu().numpy(), losses))
+    finally:
+        sf.close()
+    (u0, l0), (u1, l1) = runs
+    assert np.allclose(l0, l1, rtol=1e-9, atol=0), (l0[-1], l1[-1])
+    assert rel_l2(u1, u0) <= 1e-6
+
+
+def test_backward_uses_the_forward_depths(P):
+    """Two losses at different depths through one plan, one backward: each
+    gradient is taken at its own forward pass's z (the plan is re-targeted
+    back), and a host z tensor receives its gradient on the host."""
+    import torch
+    from paper_1001_4309_gb300.autograd import intensity_loss
+    n = 64
+    vs = [view(WAVELENGTH, 0.04, PITCH, 2e-6, n0=(n, n), n1=(n, n), flags=CPLX | NOPRE)]
+    u0 = to_dev(random_field(n, n, seed=31))
+    sf = P.ShiftedFresnel(vs)
+    try:
+        meas = [o.abs() ** 2 * 1.1 for o in sf.reconstruct(u0 * 0.8)["field"]]
+        za = torch.tensor([0.04], dtype=torch.float64, requires_grad=True)  # host tensors
+        zb = torch.tensor([0.05], dtype=torch.float64, requires_grad=True)
+        u = u0.clone().requires_grad_(True)
+        (intensity_loss(u, sf, meas, za) + intensity_loss(u, sf, meas, zb)).backward()
+        assert za.grad.device.type == "cpu" and zb.grad.device.type == "cpu"
+        both = (u.grad.clone(), float(za.grad), float(zb.grad))
+        ref = []
+        for z in (0.04, 0.05):
+            zz = torch.tensor([z], dtype=torch.float64, device="cuda", requires_grad=True)
+            uu = u0.clone().requires_grad_(True)
+            intensity_loss(uu, sf, meas, zz).backward()
+            ref.append((uu.grad.clone(), float(zz.grad)))
+    finally:
+        sf.close()
+    assert rel_l2(both[0].cpu().numpy(), (ref[0][0] + ref[1][0]).cpu().numpy()) <= 1e-6
+    assert abs(both[1] - ref[0][1]) <= 1e-9 * abs(ref[0][1])
+    assert abs(both[2] - ref[1][1]) <= 1e-9 * abs(ref[1][1])
 
 
 def test_fit_depths_recovers_z(P):

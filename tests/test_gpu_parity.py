@@ -2,9 +2,10 @@
 
 Tolerance: relative L2 error <= 1e-5 per view for the FP32 path, measured
 against the oracle's complex field; intensities and phases are checked from
-the same outputs.  Small cases compare every pixel; the paper-scale and
-maximum-size cases compare sampled output columns, which the oracle
-computes on their own.
+the same outputs.  Every case up to the paper-scale four-view workload
+compares every pixel; the longest FFT lengths (4096, 8192) on thin
+holograms compare sampled output columns along x, which the oracle computes
+on their own, and every pixel along y.
 """
 
 import numpy as np
@@ -46,18 +47,18 @@ def run(P, views, holo, field=True, intensity=True, phase=True):
     return res
 
 
-def check_view(res, i, ref, cols=None, tol=TOL):
-    f = res["field"][i] if cols is None else res["field"][i][:, cols[0]:cols[1]]
+def check_view(res, i, ref, tol=TOL):
+    f = res["field"][i]
     err = rel_l2(f, ref)
     assert err <= tol, f"view {i}: field rel-L2 {err:.3e} > {tol}"
     if res["intensity"][i] is not None:
-        I = res["intensity"][i] if cols is None else res["intensity"][i][:, cols[0]:cols[1]]
+        I = res["intensity"][i]
         ierr = rel_l2(I, np.abs(ref) ** 2)
         assert ierr <= 3 * tol, f"view {i}: intensity rel-L2 {ierr:.3e}"
         # the intensity is |u|^2 of the same float32 field
         assert np.allclose(I, np.abs(f.astype(np.complex128)) ** 2, rtol=1e-5, atol=1e-30 + 1e-6 * I.max())
     if res["phase"][i] is not None:
-        ph = res["phase"][i] if cols is None else res["phase"][i][:, cols[0]:cols[1]]
+        ph = res["phase"][i]
         assert np.all(ph > -np.pi) and np.all(ph <= np.pi + 1e-6)
         weighted = rel_l2(np.abs(ref) * np.exp(1j * ph), ref)
         assert weighted <= 3 * tol, f"view {i}: phase-weighted error {weighted:.3e}"
@@ -125,27 +126,24 @@ def test_plan_query_reports_lengths(P):
     assert ws == 8 * 1024 * 1024
 
 
-def sample_columns(n, width=4):
-    return [(0, width), (n // 2 - width // 2, n // 2 + width // 2), (n - width, n)]
-
-
-def test_config_c2_paper_scale_sampled(P):
+def test_config_c2_paper_scale_full(P):
+    """All four paper-scale 1024^2 views (FFT length 2048 on both axes, the
+    launch shape the benchmark times): every output pixel of the field, the
+    intensity and the phase against the FP64 oracle."""
     holo, views = synth.config_c2()
     res = run(P, views, holo)
     for i, v in enumerate(views):
-        for cols in sample_columns(v["nx1"]):
-            check_view(res, i, oracle.forward(holo, v, cols=cols), cols=cols)
+        check_view(res, i, oracle.forward(holo, v))
 
 
 @pytest.mark.parametrize("n0,n1", [(2048, 2048), (4096, 4097), (2048, 256)])
-def test_large_fft_lengths_sampled(P, n0, n1):
-    """Longest supported convolutions (L = 4096 and 8192) on thin holograms."""
+def test_large_fft_lengths(P, n0, n1):
+    """Longest supported convolutions (L = 4096 and 8192) on thin holograms, every pixel."""
     ny = 8
     v = view(WAVELENGTH, 0.06, PITCH, 1.3e-6, o1=(3e-4, -1e-5), n0=(n0, ny), n1=(n1, ny))
     holo = random_field(ny, n0, seed=n0 + n1).real
     res = run(P, [v], holo, phase=False)
-    for cols in sample_columns(n1, 8):
-        check_view(res, 0, oracle.forward(holo, v, cols=cols), cols=cols)
+    check_view(res, 0, oracle.forward(holo, v))
     # the transposed direction exercises the y pass at the same lengths
     vt = view(WAVELENGTH, 0.06, PITCH, 1.3e-6, o1=(3e-4, -1e-5), n0=(ny, n0), n1=(ny, n1))
     res = run(P, [vt], holo.T.copy(), phase=False)
@@ -310,14 +308,12 @@ def test_row_pass_kernels_agree(P, n0, n1, monkeypatch):
         monkeypatch.setenv("SF_PASS_IMPL", impl)
         res[impl] = run(P, [v], holo, intensity=False, phase=False)["field"][0]
     assert np.array_equal(res["grid"], res["tma"])
-    for cols in sample_columns(n1):
-        check_view({"field": [res["tma"][:, cols[0]:cols[1]]], "intensity": [None], "phase": [None]}, 0,
-                   oracle.forward(holo, v, cols=cols))
+    check_view({"field": [res["tma"]], "intensity": [None], "phase": [None]}, 0, oracle.forward(holo, v))
 
 
 def test_many_views_one_plan(P):
     """40 ragged views of one hologram: several launches per FFT length (16 passes each), both halves of
-    the two-stream split, every length family; sampled columns of every view against the oracle."""
+    the two-stream split, every length family; every pixel of every view against the oracle."""
     rng = np.random.default_rng(21)
     n0 = (300, 260)
     sizes = [(int(a), int(b)) for a, b in rng.integers(1, 1300, size=(40, 2))]
@@ -327,6 +323,4 @@ def test_many_views_one_plan(P):
     holo = random_field(n0[1], n0[0], seed=99).real
     res = run(P, views, holo, intensity=False, phase=False)
     for i, v in enumerate(views):
-        c = (v["nx1"] // 2, min(v["nx1"], v["nx1"] // 2 + 3))
-        check_view({"field": [res["field"][i][:, c[0]:c[1]]], "intensity": [None], "phase": [None]}, 0,
-                   oracle.forward(holo, v, cols=c))
+        check_view(res, i, oracle.forward(holo, v))
