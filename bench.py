@@ -680,10 +680,10 @@ def inline_retrieval(dev):
         I = [torch.from_numpy((m / scale).astype(np.float32)).to(dev) for m in meas]
         bp = bp_sf.reconstruct(torch.from_numpy(np.sqrt(meas[1] / scale).astype(np.complex64)).to(dev))["field"][0]
         e_bp = aligned_error(bp.cpu().numpy(), obj)
-        u0 = torch.ones((1024, 1024), dtype=torch.complex64, device=dev)
+        u0 = torch.ones((1024, 1024), dtype=torch.complex64, device=dev) / scale ** 0.5  # unit-mean intensities
         torch.cuda.synchronize()
         t0 = _t.perf_counter()
-        u, losses = phase_retrieval(sf, I, n_iter=200, u_init=u0, lr=0.1)
+        u, losses = phase_retrieval(sf, I, n_iter=200, u_init=u0, lr=0.1 / scale ** 0.5)
         torch.cuda.synchronize()
         secs = _t.perf_counter() - t0
         e_pr = aligned_error(u.cpu().numpy(), obj)

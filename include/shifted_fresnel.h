@@ -53,12 +53,21 @@ extern "C" {
 #define SF_IN_COMPLEX 8u    /* the hologram is complex64 instead of float32 (same for every view of a plan) */
 
 /* ---- precision selector ---- */
-#define SF_PREC_FP32 0   /* FP32 FFT stages on CUDA cores; phases exact (64-bit fixed point) */
-#define SF_PREC_FP16TC 1 /* radix-16/8 DFT stages as FP16 tensor-core products, FP32 accumulation */
-#define SF_PREC_BF16TC 2 /* same with BF16 operands */
-/* The tensor-core precisions apply to axes whose FFT length is 2048 or 4096;
- * other axes, the adjoint and the batch path run in FP32.  Chirps, twiddles,
- * spectrum and accumulation stay FP32 (phases exact) in every precision. */
+#define SF_PREC_FP32 0     /* FP32 FFT stages on CUDA cores; phases exact (64-bit fixed point) */
+#define SF_PREC_FP16TC 1   /* DFT stages as FP16 tensor-core products, FP32 accumulation */
+#define SF_PREC_BF16TC 2   /* same with BF16 operands */
+#define SF_PREC_FP16X3TC 3 /* FP16 operands split into hi + lo parts, three products per stage */
+#define SF_PREC_BF16X3TC 4 /* BF16 operands split into hi + lo parts, three products per stage */
+/* Tensor-core precisions.  An axis of FFT length 2048 whose input and output
+ * lengths are at most 1024 (the paper's 2N padding, e.g. 1024 -> 1024) runs
+ * the four-step pass on tcgen05 (2048 = 64 x 32: two DFT matrix products
+ * each way, operands in shared memory, FP32 accumulators in tensor memory,
+ * one CTA per SM); other axes of length 2048 or 4096 run radix-16/8 stages on
+ * mma.sync (FP16TC and BF16TC only).  Every other axis, the adjoint and the
+ * persistent batch kernel run in FP32.  The x3 precisions apply to the
+ * tcgen05 axes only and run every other axis in FP32.  Chirps, twiddles,
+ * kernel spectrum and accumulation stay FP32 (phases exact) in every
+ * precision. */
 
 /* Longest linear convolution per axis: nx0 + nx1 - 1 <= SF_MAX_CONV_LENGTH. */
 #define SF_MAX_CONV_LENGTH 8192
@@ -88,7 +97,8 @@ typedef struct sf_plan_s* sf_plan;
  *   out        receives the plan handle (set to NULL on failure).
  *   views      host array of n_views view descriptions (copied; not retained).
  *   n_views    1 .. 4096.
- *   precision  SF_PREC_FP32, SF_PREC_FP16TC or SF_PREC_BF16TC.
+ *   precision  SF_PREC_FP32, SF_PREC_FP16TC, SF_PREC_BF16TC, SF_PREC_FP16X3TC or
+ *              SF_PREC_BF16X3TC.
  *   device     CUDA device ordinal the plan is bound to (made current).
  *   stream     stream for the set-up kernels; the call synchronises it
  *              before returning.

@@ -32,6 +32,8 @@ SF_IN_COMPLEX = 8
 SF_PREC_FP32 = 0
 SF_PREC_FP16TC = 1
 SF_PREC_BF16TC = 2
+SF_PREC_FP16X3TC = 3
+SF_PREC_BF16X3TC = 4
 SF_MAX_CONV_LENGTH = 8192
 
 

@@ -34,7 +34,8 @@ struct ViewState {
   sf_view v;
   AxisCoef ax[2];          // [0] = x, [1] = y; device pointers into the arena
   AxisCoef adj[2];         // adjoint passes: [0] along x (nx1 -> nx0), [1] along y (ny1 -> ny0)
-  float2* hpos[2] = {nullptr, nullptr};  // kernel spectra in position order (tensor-core axes)
+  float2* hpos[2] = {nullptr, nullptr};  // kernel spectra in position order (mma.sync tensor-core axes)
+  float2* hnat[2] = {nullptr, nullptr};  // kernel spectra in natural order / sqrt(L) (tcgen05 axes)
   float2* work = nullptr;  // [nx1][ny0] intermediate after the x pass (transposed)
   float2* st_out = nullptr;  // host-I/O staging (lazily allocated)
   float* st_int = nullptr;
@@ -90,6 +91,7 @@ struct sf_plan_s {
   std::map<int, float4*> tw;  // per-stage twiddle tables per FFT length
   int precision = SF_PREC_FP32;
   uint32_t* tc_frags = nullptr;  // per-lane DFT fragments and twiddle tables of the tensor-core pass
+  void* t5_consts = nullptr;     // DFT operands and twiddles of the tcgen05 row pass
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
   AxisCoef* axes_dev = nullptr;  // coefficient table read by the chirp and spectrum kernels
   int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA
@@ -452,7 +454,7 @@ long long env_ll(const char* name, long long dflt) {
 // memcpy(descriptors <- pinned table), memset(counters), persistent kernel.
 // Every FFT length of the plan fits the persistent batch kernel.
 bool batch_persistent_supported(sf_plan p) {
-  if (p->tc_frags) return false;  // its tiles are the FP32 network only
+  if (p->precision != SF_PREC_FP32) return false;  // its tiles are the FP32 network only
   for (const ViewState& vs : p->views)
     for (int ph = 0; ph < 2; ++ph)
       if (!batch_length_supported(vs.ax[ph].L)) return false;
@@ -617,15 +619,21 @@ bool persistent_eligible(sf_plan p, int L, PassKind kind, const PassBatch& b) {
 }
 
 // One launch of the row pass over the descriptors of b (all FFT length L;
-// view_of[k] is descriptor k's view): the tensor-core pass on tensor-core
-// plans, the persistent bulk-copy pass where the plan chose it and the rows
-// allow it, else the one-tile-per-CTA pass.  max_rows: the most rows of any
+// view_of[k] is descriptor k's view): on reduced-precision plans the tcgen05
+// pass where its length and the 2N padding allow, else the mma.sync pass
+// (FP16 / BF16 plans); the persistent bulk-copy pass where the plan chose it
+// and the rows allow it, else the one-tile-per-CTA pass.  max_rows: the most rows of any
 // descriptor.
 cudaError_t launch_row_pass(sf_plan plan, int axis, int L, PassBatch& b, const int* view_of, int max_rows,
                             cudaStream_t s) {
   const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
   cudaError_t e;
-  if (plan->tc_frags && tc_length_supported(L)) {
+  bool t5 = plan->t5_consts && t5_length_supported(L);
+  for (int k = 0; k < b.count && t5; ++k) t5 = 2 * b.d[k].n0 <= L && 2 * b.d[k].n1 <= L;
+  if (t5) {
+    for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[view_of[k]].hnat[axis];
+    e = launch_pass_t5(L, plan->precision, kind, b, plan->t5_consts, plan->dev_err, plan->sms, s);
+  } else if (plan->tc_frags && tc_length_supported(L)) {
     for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[view_of[k]].hpos[axis];
     const int G = tc_rows_per_cta(L);
     e = launch_pass_tc(L, plan->precision, kind, b, (max_rows + G - 1) / G, plan->tc_frags, s);
@@ -754,7 +762,7 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
       const int need = a == 0 ? views[i].nx0 + views[i].nx1 - 1 : views[i].ny0 + views[i].ny1 - 1;
       const int P = next_fft_length(need, false), Q = allow_mixed ? next_fft_length(need, true) : P;
       int L = Q;
-      if (precision != SF_PREC_FP32 && tc_length_supported(P)) {
+      if (precision != SF_PREC_FP32 && (tc_length_supported(P) || t5_length_supported(P))) {
         L = P;
       } else if (tune && Q != P) {
         const double cp = best(P, kind_of(a), prunable(i, a, P), nullptr);
@@ -1116,9 +1124,15 @@ cudaError_t build_view_vectors(sf_plan p, cudaStream_t s) {
   }
   for (ViewState& vs : p->views)
     for (int a = 0; a < 2 && e == cudaSuccess; ++a)
-      if (vs.hpos[a]) {
-        e = launch_hpos(vs.ax[a].L, vs.ax[a].H, vs.hpos[a], s);
-        ++g_launches;
+      {
+        if (vs.hpos[a] && e == cudaSuccess) {
+          e = launch_hpos(vs.ax[a].L, vs.ax[a].H, vs.hpos[a], s);
+          ++g_launches;
+        }
+        if (vs.hnat[a] && e == cudaSuccess) {
+          e = launch_hnat(vs.ax[a].L, vs.ax[a].H, vs.hnat[a], s);
+          ++g_launches;
+        }
       }
   return e;
 }
@@ -1130,8 +1144,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   if (!out) return SF_ERR_INVALID_ARG;
   *out = nullptr;
   if (!views || n_views < 1 || n_views > kMaxViews) return SF_ERR_INVALID_ARG;
-  if (precision != SF_PREC_FP32 && precision != SF_PREC_FP16TC && precision != SF_PREC_BF16TC)
-    return SF_ERR_INVALID_ARG;
+  if (precision != SF_PREC_FP32 && !t5_precision(precision)) return SF_ERR_INVALID_ARG;
   for (int i = 0; i < n_views; ++i) {
     int rc = validate_view(views[i]);
     if (rc) return rc;
@@ -1165,7 +1178,9 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   Arena ar;
   std::map<int, size_t> tw_off;
   std::vector<size_t> off_cin(4 * n_views), off_cout(4 * n_views), off_H(4 * n_views), off_work(n_views);
-  std::vector<size_t> off_hpos(2 * n_views, SIZE_MAX);
+  std::vector<size_t> off_hpos(2 * n_views, SIZE_MAX), off_hnat(2 * n_views, SIZE_MAX);
+  const bool mma_sync_tables = precision == SF_PREC_FP16TC || precision == SF_PREC_BF16TC;
+  bool any_t5 = false;
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.v = views[i];
@@ -1183,11 +1198,17 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       off_H[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.L);
     }
     off_work[i] = ar.take(sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1);
-    for (int a = 0; a < 2; ++a)
-      off_hpos[2 * i + a] = (precision != SF_PREC_FP32 && tc_length_supported(vs.ax[a].L))
+    for (int a = 0; a < 2; ++a) {
+      off_hpos[2 * i + a] = (mma_sync_tables && tc_length_supported(vs.ax[a].L))
                                 ? ar.take(sizeof(float2) * vs.ax[a].L) : SIZE_MAX;
+      if (precision != SF_PREC_FP32 && t5_length_supported(vs.ax[a].L)) {
+        off_hnat[2 * i + a] = ar.take(sizeof(float2) * vs.ax[a].L);
+        any_t5 = true;
+      }
+    }
   }
-  const size_t off_frags = precision != SF_PREC_FP32 ? ar.take(sizeof(uint32_t) * tc_table_words()) : SIZE_MAX;
+  const size_t off_frags = mma_sync_tables ? ar.take(sizeof(uint32_t) * tc_table_words()) : SIZE_MAX;
+  const size_t off_t5 = any_t5 ? ar.take(t5_const_bytes(2048, precision)) : SIZE_MAX;
   const size_t off_err = ar.take(sizeof(int));
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
   if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
@@ -1201,8 +1222,10 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.work = reinterpret_cast<float2*>(base + off_work[i]);
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a) {
       if (off_hpos[2 * i + a] != SIZE_MAX) vs.hpos[a] = reinterpret_cast<float2*>(base + off_hpos[2 * i + a]);
+      if (off_hnat[2 * i + a] != SIZE_MAX) vs.hnat[a] = reinterpret_cast<float2*>(base + off_hnat[2 * i + a]);
+    }
     for (int a = 0; a < 2; ++a) {
       AxisCoef& c = vs.ax[a];
       c.cin = reinterpret_cast<float2*>(base + off_cin[2 * i + a]);
@@ -1232,6 +1255,13 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     p->tc_frags = reinterpret_cast<uint32_t*>(base + off_frags);
     e = launch_tc_tables(p->tc_frags, precision, s);
     g_launches += 3;  // fragments and the twiddle tables of both lengths
+  }
+  std::vector<unsigned char> t5_host;  // kept alive until the stream is synchronised below
+  if (off_t5 != SIZE_MAX && e == cudaSuccess) {
+    p->t5_consts = base + off_t5;
+    t5_host.resize(t5_const_bytes(2048, precision));
+    t5_build_consts(2048, precision, t5_host.data());
+    e = cudaMemcpyAsync(p->t5_consts, t5_host.data(), t5_host.size(), cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -1413,7 +1443,8 @@ cudaError_t execute_host_outputs(sf_plan plan, const ExecBuffers& io, bool pipel
     // column keeps rows of the intermediate 16-byte aligned).
     for (int vi = 0; vi < nv && e == cudaSuccess; ++vi) {
       const int nx1 = plan->views[vi].v.nx1;
-      const int half = (vi == 0 || vi == nv - 1) && !plan->tc_frags && nx1 >= 256 ? (nx1 / 2) & ~15 : 0;
+      const int half =
+          (vi == 0 || vi == nv - 1) && plan->precision == SF_PREC_FP32 && nx1 >= 256 ? (nx1 / 2) & ~15 : 0;
       e = cudaStreamWaitEvent(ys, plan->x_done[vi], 0);
       if (e == cudaSuccess && half) {
         e = y_pass(vi, 0, half, false);
@@ -1546,7 +1577,7 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   // first view's x pass on the first half (FP32 passes; the split row keeps
   // the second half's rows 16-byte aligned).
   int split_row = 0;
-  if (holo_host && pipeline && !plan->tc_frags && plan->ny0 >= 256 && holo_bytes >= ((size_t)1 << 20))
+  if (holo_host && pipeline && plan->precision == SF_PREC_FP32 && plan->ny0 >= 256 && holo_bytes >= ((size_t)1 << 20))
     split_row = (plan->ny0 / 2) & ~15;
   cudaError_t e = cudaSuccess;
   if (holo_host) {

@@ -83,6 +83,17 @@ cudaError_t launch_hpos(int L, const float2* Hreg, float2* Hpos, cudaStream_t s)
 cudaError_t launch_pass_tc(int L, int prec, PassKind kind, const PassBatch& b, int grid_x, const uint32_t* tables,
                            cudaStream_t s);
 
+// Mixed-precision row pass on tcgen05 (sf_tcgen05.cu): lengths with the four-step
+// DFT-GEMM split; passes need n0, n1 <= L / 2.  Precisions FP16TC, BF16TC and
+// their hi + lo (x3) forms.
+bool t5_length_supported(int L);
+bool t5_precision(int prec);
+size_t t5_const_bytes(int L, int prec);
+void t5_build_consts(int L, int prec, void* host);
+cudaError_t launch_hnat(int L, const float2* Hreg, float2* Hn, cudaStream_t s);
+cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, const void* consts, int* err, int sms,
+                           cudaStream_t s);
+
 // host helpers shared by the entry points (defined in sf_api.cu)
 int validate_view(const sf_view& v);
 // smallest supported FFT length >= need (powers of two only unless allow_mixed)

@@ -1,0 +1,603 @@
+// sf_tcgen05.cu -- mixed-precision row pass on the sm_100-family tensor
+// cores: the length-L convolution of Section 2.2 steps 4-8 as four dense DFT
+// matrix products issued with tcgen05.mma (FP16 or BF16 operands in shared
+// memory, FP32 accumulators in tensor memory), chirps, twiddles and kernel
+// spectrum applied in FP32 between them.
+//
+// Four-step split of the FFT of length L = R1 * R2 (R2 = 32, R1 = L / 32):
+//   n = R2 n1 + n2,  k = k1 + R1 k2
+//   X[k1 + R1 k2] = sum_n2 W_R2^{n2 k2} W_L^{n2 k1} sum_n1 x[R2 n1 + n2] W_R1^{n1 k1}
+// and the inverse in the mirrored order, each inverse DFT taken as
+// conj(DFT(conj(.))) so that one DFT matrix serves both directions.  With the
+// paper's 2N padding (n0, n1 <= L / 2, required here) only n1 < R1 / 2 is
+// nonzero on input and only n1 < R1 / 2 survives the crop, which halves the
+// first and the last product.
+//
+// Every product is the real GEMM D (128 x N) = A (128 x K) B (K x N) of the
+// block form [Re | Im] [[Fr, Fi], [-Fi, Fr]] of a unitary-scaled DFT matrix
+// F; a CTA holds kGroups independent groups of four warps, and a group
+// transforms a tile of kRows = 4 rows at a time:
+//
+//   stage A   rows (r, n2), K = (re, im) of n1 < R1/2, N = (re, im) of k1
+//   twiddle   W_L^{n2 k1} (FP32), to the stage-B operand (transpose via
+//             an MN-major operand layout)
+//   stage B   rows (r, k1), K = n2, N = k2; R1 / 32 products of 128 rows
+//   spectrum  x FFT(h) / sqrt(L) (natural order), conjugated into the
+//             stage-B^H operand (K-major)
+//   stage B^H rows (r, k1), K = k2, N = n2
+//   twiddle   W_L^{n2 k1} again (the conjugations cancel), to the stage-A^H
+//             operand (MN-major)
+//   stage A^H rows (r, n2), K = k1, N = n1 < R1/2
+//   output    conj, undo the scales, x output chirp, transposed store
+//
+// Thread (warp w of the group, lane l) reads tensor-memory lane 32 w + l, so
+// it always holds complete complex values; every operand store is a 16-byte
+// chunk of 8 consecutive K (K-major) or M (MN-major) elements.  Rows are
+// normalised by a power of two from their largest input component before the
+// first conversion (exact), which keeps FP16 in range.  The x3 precisions
+// split each operand into hi + lo parts and accumulate hi*hi + hi*lo + lo*hi.
+//
+// The kernel is persistent (one CTA per SM, tiles round-robin over the
+// groups); each MMA completion is awaited through an mbarrier with a bounded
+// poll.  On expiry the group sets the plan's device error word, waits once
+// more (bounded), leaves its tile loop and the CTA frees its tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sf_kernels.cuh"
+#include "sf_umma.cuh"
+
+namespace sf {
+namespace t5 {
+
+constexpr int kR2 = 32;        // inner radix: the lanes of a warp
+constexpr int kRows = 4;       // rows per tile (one warp per row in the first stage)
+constexpr int kGroups = 2;     // 4-warp groups per CTA
+constexpr int kThreads = 128 * kGroups;
+constexpr long long kSpin = 1ll << 22;  // mbarrier polls before a wait gives up
+
+template <int PREC>
+struct Prec {
+  static constexpr bool kBf16 = PREC == SF_PREC_BF16TC || PREC == SF_PREC_BF16X3TC;
+  static constexpr bool kSplit = PREC == SF_PREC_FP16X3TC || PREC == SF_PREC_BF16X3TC;
+};
+
+template <int L>
+struct Shape {
+  static constexpr int R1 = L / kR2;
+  static constexpr int KA = R1 / 2;  // nonzero n1 on input
+  static constexpr int NA = R1 / 2;  // kept n1 on output
+  static_assert(R1 == 64, "the first tcgen05 row pass is built for L = 2048");
+  // real GEMM shapes (M = 128 throughout)
+  static constexpr int A_K = 2 * KA, A_N = 2 * R1;    // stage A
+  static constexpr int B_K = 2 * kR2, B_N = 2 * kR2;  // stages B and B^H
+  static constexpr int H_K = 2 * R1, H_N = 2 * NA;    // stage A^H
+  static constexpr int QB = kRows * R1 / 128;         // products per middle stage
+  // constant image: the three DFT matrices (K-major B operands), hi then lo, then the twiddles
+  static constexpr int BA_BYTES = A_N * A_K * 2, BB_BYTES = B_N * B_K * 2, BH_BYTES = H_N * H_K * 2;
+  static constexpr int MAT_BYTES = BA_BYTES + BB_BYTES + BH_BYTES;
+  static constexpr int TW_LD = kR2 + 1;  // padded row of the twiddle table T[k1][n2] (float2)
+  static constexpr int TW_BYTES = R1 * TW_LD * 8;
+  // per-group operand buffer: the largest stage operand, also the output staging tile
+  static constexpr int OP_BYTES = 128 * H_K * 2;
+  static_assert(QB * 128 * B_K * 2 <= OP_BYTES && kRows * (L / 2) * 8 <= OP_BYTES, "operand buffer");
+  static constexpr int align(int b) { return (b + 1023) & ~1023; }
+  static constexpr int const_bytes(bool split) { return (split ? 2 : 1) * MAT_BYTES + TW_BYTES; }
+  static constexpr int op_offset(bool split) { return align(const_bytes(split)); }
+  static constexpr int group_bytes(bool split) { return (split ? 2 : 1) * OP_BYTES; }
+  static constexpr int misc_offset(bool split) { return op_offset(split) + kGroups * group_bytes(split); }
+  static constexpr int smem_bytes(bool split) { return misc_offset(split) + 64; }
+};
+
+// K-major operand (rows of K elements): core matrices along K are adjacent.
+__host__ __device__ constexpr int kmaj_off(int mn, int kk, int K) {
+  return (mn >> 3) * (K / 8) * 128 + (kk >> 3) * 128 + (mn & 7) * 16 + (kk & 7) * 2;
+}
+// MN-major operand with M = 128 (8-element runs of M): core matrices along M are adjacent.
+__host__ __device__ constexpr int mnmaj_off(int m, int kk) { return (m >> 3) * 128 + (kk >> 3) * 2048 + (kk & 7) * 16 + (m & 7) * 2; }
+
+template <bool BF>
+__device__ __forceinline__ uint32_t pack2(float a, float b, float& ra, float& rb) {
+  if constexpr (BF) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 f = __bfloat1622float2(h);
+    ra = a - f.x;
+    rb = b - f.y;
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(h);
+    ra = a - f.x;
+    rb = b - f.y;
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+
+// Store 8 values as one 16-byte chunk (hi) and, for the split precisions, the
+// chunk of their rounding remainders (lo) at the same offset of the lo buffer.
+template <int PREC>
+__device__ __forceinline__ void store8(unsigned char* hi, int off, const float (&v)[8]) {
+  constexpr bool BF = Prec<PREC>::kBf16;
+  float r[8];
+  uint4 h;
+  h.x = pack2<BF>(v[0], v[1], r[0], r[1]);
+  h.y = pack2<BF>(v[2], v[3], r[2], r[3]);
+  h.z = pack2<BF>(v[4], v[5], r[4], r[5]);
+  h.w = pack2<BF>(v[6], v[7], r[6], r[7]);
+  *reinterpret_cast<uint4*>(hi + off) = h;
+  if constexpr (Prec<PREC>::kSplit) {
+    float t[8];
+    uint4 lo;
+    lo.x = pack2<BF>(r[0], r[1], t[0], t[1]);
+    lo.y = pack2<BF>(r[2], r[3], t[2], t[3]);
+    lo.z = pack2<BF>(r[4], r[5], t[4], t[5]);
+    lo.w = pack2<BF>(r[6], r[7], t[6], t[7]);
+    *reinterpret_cast<uint4*>(hi + Shape<2048>::OP_BYTES + off) = lo;
+  }
+}
+
+__device__ __forceinline__ void group_bar(int g) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+// Group barrier that also ANDs a flag over the group's 128 threads.
+__device__ __forceinline__ bool group_bar_and(int g, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbarrier.cta.red.and.pred po, %2, 128, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + g)
+      : "memory");
+  return r != 0;
+}
+
+// One GEMM of ksteps K = 16 slices into tensor-memory columns d (issued by one thread).
+template <bool SPLIT>
+__device__ __forceinline__ void gemm(uint32_t d, uint32_t a, uint32_t a_lo, uint32_t a_lbo, uint32_t a_sbo,
+                                     uint32_t a_step, uint32_t bm, uint32_t bm_lo, uint32_t b_sbo, int ksteps,
+                                     uint32_t idesc) {
+  for (int k = 0; k < ksteps; ++k) {
+    const uint64_t ad = umma::sdesc(a + k * a_step, a_lbo, a_sbo);
+    const uint64_t bd = umma::sdesc(bm + k * 256, 128, b_sbo);
+    umma::mma(d, ad, bd, idesc, k > 0);
+    if constexpr (SPLIT) {
+      umma::mma(d, ad, umma::sdesc(bm_lo + k * 256, 128, b_sbo), idesc, 1);
+      umma::mma(d, umma::sdesc(a_lo + k * a_step, a_lbo, a_sbo), bd, idesc, 1);
+    }
+  }
+}
+
+struct Args {
+  const uint4* consts;  // constant image (Shape::const_bytes)
+  int* err;             // device error word
+  int total_tiles;
+  int tile_off[kMaxPassBatch + 1];
+};
+
+template <int L, int KIND, int PREC>
+__global__ void __launch_bounds__(kThreads, 1)
+k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
+  using S = Shape<L>;
+  constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
+  constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int g = threadIdx.x >> 7, tq = threadIdx.x & 127, wq = tq >> 5, l = tq & 31;
+  unsigned char* const op = sm + S::op_offset(SPLIT) + g * S::group_bytes(SPLIT);
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + S::misc_offset(SPLIT));
+  uint32_t* const tbase = reinterpret_cast<uint32_t*>(sm + S::misc_offset(SPLIT) + 8 * kGroups);
+  const float2* const tw = reinterpret_cast<const float2*>(sm + (SPLIT ? 2 : 1) * S::MAT_BYTES);
+
+  for (int i = threadIdx.x; i < S::const_bytes(SPLIT) / 16; i += kThreads)
+    reinterpret_cast<uint4*>(sm)[i] = a.consts[i];
+  if (tq == 0) umma::mbar_init(bars + g, 1);
+  if (threadIdx.x < 32) umma::tmem_alloc(tbase, 128 * kGroups);
+  umma::fence_smem_to_async();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+
+  const uint32_t tm = *tbase + 128u * g;
+  const uint32_t lanes = (uint32_t)(32 * wq) << 16;  // this warp's tensor-memory lanes
+  const uint32_t s_op = umma::smem_u32(op), s_lo = s_op + S::OP_BYTES;
+  const uint32_t s_ba = umma::smem_u32(sm), s_bb = s_ba + S::BA_BYTES, s_bh = s_bb + S::BB_BYTES;
+  constexpr uint32_t LO = SPLIT ? S::MAT_BYTES : 0;
+  uint32_t parity = 0;
+  bool ok = true;
+
+  // wait for the group's last commit (one poller), then agree on the outcome
+  auto await = [&]() {
+    bool w = true;
+    if (tq == 0) {
+      w = umma::mbar_wait(bars + g, parity, kSpin);
+      if (!w) {
+        atomicExch(a.err, 1);
+        umma::mbar_wait(bars + g, parity, kSpin);
+      }
+    }
+    parity ^= 1;
+    ok = group_bar_and(g, w);
+    umma::fence_after_sync();
+  };
+  // operands written -> visible to the tensor core; earlier tensor-memory reads ordered before the next MMA
+  auto publish = [&]() {
+    umma::fence_smem_to_async();
+    umma::fence_before_sync();
+    group_bar(g);
+  };
+
+  for (int tile = blockIdx.x * kGroups + g; tile < a.total_tiles; tile += gridDim.x * kGroups) {
+    int p = 0;
+    while (tile >= a.tile_off[p + 1]) ++p;
+    const PassDesc& d = b.d[p];
+    const int row0 = (tile - a.tile_off[p]) * kRows;
+    const int n0 = d.n0, n1 = d.n1;
+
+    // ---- input x chirp (steps 2-3), row normalisation, stage-A operand (K-major)
+    float inv_scale;
+    {
+      const int row = row0 + wq;
+      const bool valid = row < d.rows;
+      float2 x[KA];
+      float mx = 0.f;
+#pragma unroll
+      for (int i = 0; i < KA; ++i) {
+        const int n = kR2 * i + l;
+        float2 v = make_float2(0.f, 0.f);
+        if (valid && n < n0) {
+          const float2 c = __ldg(d.cin + n);
+          if constexpr (KIND == PASS_X_REAL) {
+            v = cscale(c, __ldg(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + n));
+          } else {
+            v = cmul(__ldg(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + n), c);
+          }
+        }
+        x[i] = v;
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int e = 0;
+      if (mx > 0.f) frexpf(mx, &e);
+      const float s = ldexpf(1.f, -e);  // max * s in [0.5, 1)
+      inv_scale = ldexpf(1.f, e);
+      const int m = 32 * wq + l;
+#pragma unroll
+      for (int c = 0; c < KA / 8; ++c) {
+        float re[8], im[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          re[j] = x[8 * c + j].x * s;
+          im[j] = x[8 * c + j].y * s;
+        }
+        store8<PREC>(op, kmaj_off(m, 8 * c, S::A_K), re);
+        store8<PREC>(op, kmaj_off(m, KA + 8 * c, S::A_K), im);
+      }
+    }
+    publish();
+    if (tq == 0) {
+      umma::fence_after_sync();
+      gemm<SPLIT>(tm, s_op, s_lo, 128, (S::A_K / 8) * 128, 256, s_ba, s_ba + LO, (S::A_K / 8) * 128,
+                  S::A_K / 16, umma::idesc_f16(128, S::A_N, BF, false, false));
+      umma::commit(bars + g);
+    }
+    await();
+    if (!ok) break;
+
+    // ---- twiddle W_L^{n2 k1}; stage-B operand rows (r', k1), K = n2 (MN-major)
+    {
+      const int q = wq >> 1, rp = wq & 1;
+      unsigned char* opq = op + q * 128 * S::B_K * 2;
+#pragma unroll
+      for (int j = 0; j < R1 / 16; ++j) {
+        float re[16], im[16];
+        umma::tmem_ld16(tm + lanes + 16 * j, re);
+        umma::tmem_ld16(tm + lanes + R1 + 16 * j, im);
+        umma::tmem_wait_ld();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float yr[8], yi[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k1 = 16 * j + 8 * h + i;
+            const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + l]);
+            yr[i] = y.x;
+            yi[i] = y.y;
+          }
+          const int m = R1 * rp + 16 * j + 8 * h;
+          store8<PREC>(opq, mnmaj_off(m, l), yr);
+          store8<PREC>(opq, mnmaj_off(m, kR2 + l), yi);
+        }
+      }
+    }
+    publish();
+    if (tq == 0) {
+      umma::fence_after_sync();
+#pragma unroll
+      for (int q = 0; q < S::QB; ++q)
+        gemm<SPLIT>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, 2048, 128, 4096, s_bb,
+                    s_bb + LO, (S::B_K / 8) * 128, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, true, false));
+      umma::commit(bars + g);
+    }
+    await();
+    if (!ok) break;
+
+    // ---- x kernel spectrum (step 7), conjugated: stage-B^H operand rows (r', k1), K = k2 (K-major)
+    {
+      const int k1 = 32 * (wq & 1) + l, m = 32 * wq + l;
+#pragma unroll
+      for (int c = 0; c < kR2 / 16; ++c) {
+        float2 hs[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) hs[i] = __ldg(d.H + k1 + R1 * (16 * c + i));
+#pragma unroll
+        for (int q = 0; q < S::QB; ++q) {
+          float re[16], im[16];
+          umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
+          umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
+          umma::tmem_wait_ld();
+          unsigned char* opq = op + q * 128 * S::B_K * 2;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float yr[8], yi[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), hs[8 * h + i]);
+              yr[i] = y.x;
+              yi[i] = -y.y;
+            }
+            store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h, S::B_K), yr);
+            store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h, S::B_K), yi);
+          }
+        }
+      }
+    }
+    publish();
+    if (tq == 0) {
+      umma::fence_after_sync();
+#pragma unroll
+      for (int q = 0; q < S::QB; ++q)
+        gemm<SPLIT>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, 128,
+                    (S::B_K / 8) * 128, 256, s_bb, s_bb + LO, (S::B_K / 8) * 128, S::B_K / 16,
+                    umma::idesc_f16(128, S::B_N, BF, false, false));
+      umma::commit(bars + g);
+    }
+    await();
+    if (!ok) break;
+
+    // ---- twiddle W_L^{n2 k1}: stage-A^H operand rows (r, n2), K = k1 (MN-major)
+    {
+      const int k1 = 32 * (wq & 1) + l;
+#pragma unroll
+      for (int q = 0; q < S::QB; ++q) {
+        const int r = 2 * q + (wq >> 1);
+#pragma unroll
+        for (int c = 0; c < kR2 / 16; ++c) {
+          float re[16], im[16];
+          umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
+          umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
+          umma::tmem_wait_ld();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float yr[8], yi[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int n2 = 16 * c + 8 * h + i;
+              const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + n2]);
+              yr[i] = y.x;
+              yi[i] = y.y;
+            }
+            const int m = kR2 * r + 16 * c + 8 * h;
+            store8<PREC>(op, mnmaj_off(m, k1), yr);
+            store8<PREC>(op, mnmaj_off(m, R1 + k1), yi);
+          }
+        }
+      }
+    }
+    publish();
+    if (tq == 0) {
+      umma::fence_after_sync();
+      gemm<SPLIT>(tm, s_op, s_lo, 2048, 128, 4096, s_bh, s_bh + LO, (S::H_K / 8) * 128, S::H_K / 16,
+                  umma::idesc_f16(128, S::H_N, BF, true, false));
+      umma::commit(bars + g);
+    }
+    await();
+    if (!ok) break;
+
+    // ---- conj, undo the scales, x output chirp (step 9): staged as [r][n] float2
+    {
+      // the three 1/sqrt(L) stage scales (the output chirp carries the transform's 1/L)
+      const float sc = inv_scale * (float)L * sqrtf((float)L);
+      float2* stage = reinterpret_cast<float2*>(op);
+#pragma unroll
+      for (int c = 0; c < NA / 16; ++c) {
+        float re[16], im[16];
+        umma::tmem_ld16(tm + lanes + 16 * c, re);
+        umma::tmem_ld16(tm + lanes + NA + 16 * c, im);
+        umma::tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int n = kR2 * (16 * c + i) + l;
+          if (n < n1) stage[wq * (L / 2) + n] = cmul(make_float2(re[i] * sc, -im[i] * sc), __ldg(d.cout + n));
+        }
+      }
+    }
+    umma::fence_before_sync();
+    group_bar(g);
+    // ---- transposed store: output n of row r to dst[n * dst_ld + row0 + r]
+    {
+      const float2* stage = reinterpret_cast<const float2*>(op);
+      const int rows_here = min(kRows, d.rows - row0);
+      float2* const dst = d.dst;
+      float* const inten = d.inten;
+      float* const phase = d.phase;
+      const size_t ld = (size_t)d.dst_ld;
+      const bool acc = d.accumulate != 0;
+      for (int i = tq; i < n1 * kRows; i += 128) {
+        const int n = i >> 2, r = i & 3;
+        if (r < rows_here) {
+          const float2 u = stage[r * (L / 2) + n];
+          const size_t o = (size_t)n * ld + row0 + r;
+          if constexpr (KIND != PASS_Y) {
+            dst[o] = u;
+          } else {
+            if (dst) dst[o] = acc ? cadd(dst[o], u) : u;
+            if (inten) inten[o] = fmaf(u.x, u.x, u.y * u.y);
+            if (phase) phase[o] = phase_of(u);
+          }
+        }
+      }
+    }
+    group_bar(g);  // the staging tile is the next tile's operand buffer
+  }
+
+  umma::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) umma::tmem_dealloc(*tbase, 128 * kGroups);
+}
+
+// Natural-order kernel spectrum scaled by 1/sqrt(L), from the FP32 network's
+// register order: position p of that network holds frequency
+// f(p) = sum_s k_s R_0 ... R_{s-1} with k_s = (p / M_s) mod R_s (its radix-16
+// decimation-in-frequency digits, least significant first).
+template <int L>
+__global__ void k_hnat(const float2* __restrict__ Hreg, float2* __restrict__ Hn) {
+  constexpr int T = L / kE;
+  const float hs = rsqrtf((float)L);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const int p = last_pos<L, kE>(t, e);
+    int f = 0, w = 1, M = L;
+    while (M > 1) {  // stages of radix min(M', 16)
+      const int R = M > kE ? kE : M;
+      M /= R;
+      f += ((p / M) % R) * w;
+      w *= R;
+    }
+    const float2 h = Hreg[e * T + t];
+    Hn[f] = make_float2(h.x * hs, h.y * hs);
+  }
+}
+
+template <int L, int PREC>
+cudaError_t launch_t(PassKind kind, const PassBatch& b, const Args& a, int grid, cudaStream_t s) {
+  constexpr int smem = Shape<L>::smem_bytes(Prec<PREC>::kSplit);
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kThreads, smem, s>>>(b, a);
+    return cudaGetLastError();
+  };
+  switch (kind) {
+    case PASS_X_REAL: return go(k_pass_t5<L, PASS_X_REAL, PREC>);
+    case PASS_X_CPLX: return go(k_pass_t5<L, PASS_X_CPLX, PREC>);
+    case PASS_Y: return go(k_pass_t5<L, PASS_Y, PREC>);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// host: 16-bit value of v (round to nearest even) and the remainder v - value
+uint16_t to16(double v, bool bf16, double& rem) {
+  if (bf16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    rem = v - (double)__bfloat162float(h);
+    uint16_t r;
+    std::memcpy(&r, &h, 2);
+    return r;
+  }
+  const __half h = __float2half_rn((float)v);
+  rem = v - (double)__half2float(h);
+  uint16_t r;
+  std::memcpy(&r, &h, 2);
+  return r;
+}
+
+// Real block form of the unitary DFT of size R restricted to kin inputs and
+// nout outputs, as a K-major B operand image (N = 2 nout rows of K = 2 kin):
+// B[(s, i)][(t, o)], s, t in {re, im}: [re][re] = [im][im] = cos, [re][im] =
+// -sin, [im][re] = sin of 2 pi i o / R, all over sqrt(R).
+void dft_operand(int R, int kin, int nout, bool bf16, uint16_t* hi, uint16_t* lo) {
+  const int K = 2 * kin;
+  const double sc = 1.0 / std::sqrt((double)R);
+  for (int t = 0; t < 2; ++t)
+    for (int o = 0; o < nout; ++o)
+      for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < kin; ++i) {
+          const double ang = 2.0 * M_PI * (double)(((long long)i * o) % R) / R;
+          const double c = std::cos(ang) * sc, sn = -std::sin(ang) * sc;  // W_R^{i o} = c + i sn
+          const double v = (s == t) ? c : (s == 0 ? sn : -sn);
+          const int n = t * nout + o, kk = s * kin + i;
+          double rem, rem2;
+          const int off = kmaj_off(n, kk, K) / 2;
+          hi[off] = to16(v, bf16, rem);
+          if (lo) lo[off] = to16(rem, bf16, rem2);
+        }
+}
+
+}  // namespace t5
+
+bool t5_length_supported(int L) { return L == 2048; }
+bool t5_precision(int prec) {
+  return prec == SF_PREC_FP16TC || prec == SF_PREC_BF16TC || prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
+}
+
+size_t t5_const_bytes(int L, int prec) {
+  (void)L;
+  const bool split = prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
+  return (size_t)t5::Shape<2048>::const_bytes(split);
+}
+
+void t5_build_consts(int L, int prec, void* host) {
+  using S = t5::Shape<2048>;
+  (void)L;
+  const bool split = prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
+  const bool bf16 = prec == SF_PREC_BF16TC || prec == SF_PREC_BF16X3TC;
+  unsigned char* base = static_cast<unsigned char*>(host);
+  std::memset(base, 0, t5_const_bytes(L, prec));
+  uint16_t* hi = reinterpret_cast<uint16_t*>(base);
+  uint16_t* lo = split ? reinterpret_cast<uint16_t*>(base + S::MAT_BYTES) : nullptr;
+  const int o1 = S::BA_BYTES / 2, o2 = (S::BA_BYTES + S::BB_BYTES) / 2;
+  t5::dft_operand(S::R1, S::KA, S::R1, bf16, hi, lo);                               // stage A
+  t5::dft_operand(t5::kR2, t5::kR2, t5::kR2, bf16, hi + o1, lo ? lo + o1 : nullptr);  // stages B, B^H
+  t5::dft_operand(S::R1, S::R1, S::NA, bf16, hi + o2, lo ? lo + o2 : nullptr);       // stage A^H
+  float2* tw = reinterpret_cast<float2*>(base + (split ? 2 : 1) * S::MAT_BYTES);
+  for (int k1 = 0; k1 < S::R1; ++k1)
+    for (int n2 = 0; n2 < t5::kR2; ++n2) {
+      const double ang = -2.0 * M_PI * (double)(k1 * n2) / 2048.0;
+      tw[k1 * S::TW_LD + n2] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+}
+
+cudaError_t launch_hnat(int L, const float2* Hreg, float2* Hn, cudaStream_t s) {
+  if (L != 2048) return cudaErrorInvalidValue;
+  t5::k_hnat<2048><<<1, 2048 / kE, 0, s>>>(Hreg, Hn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, const void* consts, int* err, int sms,
+                           cudaStream_t s) {
+  if (L != 2048) return cudaErrorInvalidValue;
+  t5::Args a{};
+  a.consts = static_cast<const uint4*>(consts);
+  a.err = err;
+  a.tile_off[0] = 0;
+  for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + t5::kRows - 1) / t5::kRows;
+  for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
+  a.total_tiles = a.tile_off[b.count];
+  if (a.total_tiles == 0) return cudaSuccess;
+  const int grid = std::min(sms, (a.total_tiles + t5::kGroups - 1) / t5::kGroups);
+  switch (prec) {
+    case SF_PREC_FP16TC: return t5::launch_t<2048, SF_PREC_FP16TC>(kind, b, a, grid, s);
+    case SF_PREC_BF16TC: return t5::launch_t<2048, SF_PREC_BF16TC>(kind, b, a, grid, s);
+    case SF_PREC_FP16X3TC: return t5::launch_t<2048, SF_PREC_FP16X3TC>(kind, b, a, grid, s);
+    case SF_PREC_BF16X3TC: return t5::launch_t<2048, SF_PREC_BF16X3TC>(kind, b, a, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace sf
