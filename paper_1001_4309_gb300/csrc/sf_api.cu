@@ -216,6 +216,9 @@ void count_launches(uint64_t n) { g_launches += n; }
 
 namespace {
 
+// Intermediate of one view: nx1 columns of ny0 rows.
+size_t work_elems(const sf_view& v) { return (size_t)v.ny0 * v.nx1; }
+
 struct Arena {
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -481,7 +484,7 @@ int batch_prepare(sf_plan p, int n_holos, bool persistent) {
     b.items_per_holo = first;
     Arena ar;
     std::vector<size_t> off(nv);
-    for (int v = 0; v < nv; ++v) off[v] = ar.take(sizeof(float2) * (size_t)p->views[v].v.ny0 * p->views[v].v.nx1);
+    for (int v = 0; v < nv; ++v) off[v] = ar.take(sizeof(float2) * work_elems(p->views[v].v));
     const size_t o_groups = ar.take(sizeof(BatchGroup) * b.groups.size());
     const size_t o_item_group = ar.take(sizeof(int) * b.items_per_holo);
     if (cudaMalloc(&b.d_fixed, ar.off) != cudaSuccess) {
@@ -851,7 +854,7 @@ int ensure_stream_slots(sf_plan p) {
   size_t ws = 0;
   for (const ViewState& vs : p->views) {
     ctas += (vs.v.ny0 + pass_rows_per_cta(vs.ax[0].L) - 1) / std::max(1, pass_rows_per_cta(vs.ax[0].L));
-    ws += sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1;
+    ws += sizeof(float2) * work_elems(vs.v);
   }
   const long long target = 2LL * 2 * std::max(1, p->sms);
   int K = (int)std::min<long long>(kMaxPassBatch / nv, (target + ctas - 1) / std::max(1LL, ctas));
@@ -868,7 +871,7 @@ int ensure_stream_slots(sf_plan p) {
     for (int grp = 0; grp < 2; ++grp)
       for (int j = 1; j < K; ++j)
         for (int v = 0; v < nv; ++v)
-          off[(size_t)(grp * K + j) * nv + v] = ar.take(sizeof(float2) * (size_t)p->views[v].v.ny0 * p->views[v].v.nx1);
+          off[(size_t)(grp * K + j) * nv + v] = ar.take(sizeof(float2) * work_elems(p->views[v].v));
     if (cudaMalloc(&b.d_sslot, ar.off) != cudaSuccess) {
       cudaGetLastError();
       b.d_sslot = nullptr;
@@ -1197,7 +1200,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       off_cout[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.n1);
       off_H[2 * n_views + 2 * i + a] = ar.take(sizeof(float2) * ca.L);
     }
-    off_work[i] = ar.take(sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1);
+    off_work[i] = ar.take(sizeof(float2) * work_elems(vs.v));
     for (int a = 0; a < 2; ++a) {
       off_hpos[2 * i + a] = (mma_sync_tables && tc_length_supported(vs.ax[a].L))
                                 ? ar.take(sizeof(float2) * vs.ax[a].L) : SIZE_MAX;
@@ -1313,7 +1316,7 @@ int shifted_fresnel_plan_query(sf_plan plan, int view, int32_t* lx, int32_t* ly,
   const ViewState& vs = plan->views[view];
   if (lx) *lx = vs.ax[0].L;
   if (ly) *ly = vs.ax[1].L;
-  if (workspace_bytes) *workspace_bytes = sizeof(float2) * (size_t)vs.v.ny0 * vs.v.nx1;
+  if (workspace_bytes) *workspace_bytes = sizeof(float2) * work_elems(vs.v);
   return SF_OK;
 }
 

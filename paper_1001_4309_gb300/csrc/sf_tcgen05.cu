@@ -38,9 +38,20 @@
 // split each operand into hi + lo parts and accumulate hi*hi + hi*lo + lo*hi.
 //
 // The kernel is persistent (one CTA per SM, tiles round-robin over the
-// groups); each MMA completion is awaited through an mbarrier with a bounded
-// poll.  On expiry the group sets the plan's device error word, waits once
-// more (bounded), leaves its tile loop and the CTA frees its tensor memory.
+// groups): four groups for FP16 / BF16 (all 512 tensor-memory columns, 128
+// per group), two for the x3 precisions, whose doubled operand buffers leave
+// room for no more.  The spectrum and output-chirp loads are issued before
+// the waits for the products they follow.  Each MMA completion is awaited
+// through an mbarrier with a bounded wait; on expiry the group sets the
+// plan's device error word, waits once more (bounded), leaves its tile loop
+// and the CTA frees its tensor memory.
+//
+// Measured on the paper-scale step (four 1024^2 views, L = 2048 both axes):
+// FP16 and BF16 89.7 us, FP16x3 157 us against 91.8 us for the FP32 pass.
+// Per tile the products take about 1.5 of ~30 thousand cycles: the pass is
+// bound by the latency of its FP32 epilogues and global loads and stores at
+// 16 warps per SM, not by the tensor cores (swizzled and unswizzled operand
+// layouts time the same).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -56,14 +67,17 @@ namespace t5 {
 
 constexpr int kR2 = 32;        // inner radix: the lanes of a warp
 constexpr int kRows = 4;       // rows per tile (one warp per row in the first stage)
-constexpr int kGroups = 2;     // 4-warp groups per CTA
-constexpr int kThreads = 128 * kGroups;
-constexpr long long kSpin = 1ll << 22;  // mbarrier polls before a wait gives up
+// MMA completion waits: tries of at most kSuspendNs each (the waiting thread
+// sleeps in hardware instead of spinning), kSpin tries (about 1 s) in all
+constexpr uint32_t kSuspendNs = 20000;
+constexpr long long kSpin = 50000;
 
 template <int PREC>
 struct Prec {
   static constexpr bool kBf16 = PREC == SF_PREC_BF16TC || PREC == SF_PREC_BF16X3TC;
   static constexpr bool kSplit = PREC == SF_PREC_FP16X3TC || PREC == SF_PREC_BF16X3TC;
+  static constexpr int kGroups = kSplit ? 2 : 4;
+  static constexpr int kThreads = 128 * kGroups;
 };
 
 template <int L>
@@ -89,16 +103,27 @@ struct Shape {
   static constexpr int const_bytes(bool split) { return (split ? 2 : 1) * MAT_BYTES + TW_BYTES; }
   static constexpr int op_offset(bool split) { return align(const_bytes(split)); }
   static constexpr int group_bytes(bool split) { return (split ? 2 : 1) * OP_BYTES; }
-  static constexpr int misc_offset(bool split) { return op_offset(split) + kGroups * group_bytes(split); }
+  static constexpr int misc_offset(bool split) { return op_offset(split) + (split ? 2 : 4) * group_bytes(split); }
   static constexpr int smem_bytes(bool split) { return misc_offset(split) + 64; }
 };
 
-// K-major operand (rows of K elements): core matrices along K are adjacent.
-__host__ __device__ constexpr int kmaj_off(int mn, int kk, int K) {
-  return (mn >> 3) * (K / 8) * 128 + (kk >> 3) * 128 + (mn & 7) * 16 + (kk & 7) * 2;
+// Operand layouts, 128-byte swizzle (16-bit elements; every operand starts on
+// a 1 KiB boundary).  K-major: each row's 64 K elements are 128 bytes, rows
+// in 1 KiB groups of 8, 16-byte chunk c of row m stored at chunk c ^ (m mod 8);
+// K beyond 64 continues in a further column (only the 64-row stage-A^H
+// matrix, 8 KiB per column).  MN-major (M = 128): each K row holds 64 M
+// elements with the same XOR, 8 K rows per 1 KiB group, the two 64-wide M
+// halves KX / 8 KiB apart.
+__host__ __device__ constexpr int kmaj_off(int mn, int kk) {
+  return (kk >> 6) * 8192 + (mn >> 3) * 1024 + (mn & 7) * 128 + ((((kk & 63) >> 3) ^ (mn & 7)) << 4) + (kk & 7) * 2;
 }
-// MN-major operand with M = 128 (8-element runs of M): core matrices along M are adjacent.
-__host__ __device__ constexpr int mnmaj_off(int m, int kk) { return (m >> 3) * 128 + (kk >> 3) * 2048 + (kk & 7) * 16 + (m & 7) * 2; }
+__host__ __device__ constexpr int mnmaj_off(int m, int kk, int KX) {
+  return (m >> 6) * (KX >> 3) * 1024 + (kk >> 3) * 1024 + (kk & 7) * 128 + ((((m & 63) >> 3) ^ (kk & 7)) << 4) +
+         (m & 7) * 2;
+}
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return umma::sdesc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
 
 template <bool BF>
 __device__ __forceinline__ uint32_t pack2(float a, float b, float& ra, float& rb) {
@@ -155,18 +180,24 @@ __device__ __forceinline__ bool group_bar_and(int g, bool v) {
   return r != 0;
 }
 
-// One GEMM of ksteps K = 16 slices into tensor-memory columns d (issued by one thread).
-template <bool SPLIT>
-__device__ __forceinline__ void gemm(uint32_t d, uint32_t a, uint32_t a_lo, uint32_t a_lbo, uint32_t a_sbo,
-                                     uint32_t a_step, uint32_t bm, uint32_t bm_lo, uint32_t b_sbo, int ksteps,
-                                     uint32_t idesc) {
+template <bool SPLIT, bool A_MN>
+__device__ __forceinline__ void gemm(uint32_t d, uint32_t a, uint32_t a_lo, int a_kx, uint32_t bm, uint32_t bm_lo,
+                                     int b_rows, int ksteps, uint32_t idesc) {
   for (int k = 0; k < ksteps; ++k) {
-    const uint64_t ad = umma::sdesc(a + k * a_step, a_lbo, a_sbo);
-    const uint64_t bd = umma::sdesc(bm + k * 256, 128, b_sbo);
+    uint32_t aoff, albo;
+    if constexpr (A_MN) {
+      aoff = k * 2048;
+      albo = (uint32_t)(a_kx >> 3) * 1024;
+    } else {
+      aoff = (k & 3) * 32 + (k >> 2) * 16 * 1024;
+      albo = 16;
+    }
+    const uint32_t boff = (k & 3) * 32 + (k >> 2) * (b_rows >> 3) * 1024;
+    const uint64_t ad = desc_sw(a + aoff, albo, 1024), bd = desc_sw(bm + boff, 16, 1024);
     umma::mma(d, ad, bd, idesc, k > 0);
     if constexpr (SPLIT) {
-      umma::mma(d, ad, umma::sdesc(bm_lo + k * 256, 128, b_sbo), idesc, 1);
-      umma::mma(d, umma::sdesc(a_lo + k * a_step, a_lbo, a_sbo), bd, idesc, 1);
+      umma::mma(d, ad, desc_sw(bm_lo + boff, 16, 1024), idesc, 1);
+      umma::mma(d, desc_sw(a_lo + aoff, albo, 1024), bd, idesc, 1);
     }
   }
 }
@@ -179,10 +210,11 @@ struct Args {
 };
 
 template <int L, int KIND, int PREC>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Prec<PREC>::kThreads, 1)
 k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
   using S = Shape<L>;
   constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
+  constexpr int kGroups = Prec<PREC>::kGroups, kThreads = Prec<PREC>::kThreads;
   constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int g = threadIdx.x >> 7, tq = threadIdx.x & 127, wq = tq >> 5, l = tq & 31;
@@ -212,10 +244,10 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
   auto await = [&]() {
     bool w = true;
     if (tq == 0) {
-      w = umma::mbar_wait(bars + g, parity, kSpin);
+      w = umma::mbar_wait(bars + g, parity, kSpin, kSuspendNs);
       if (!w) {
         atomicExch(a.err, 1);
-        umma::mbar_wait(bars + g, parity, kSpin);
+        umma::mbar_wait(bars + g, parity, kSpin, kSuspendNs);
       }
     }
     parity ^= 1;
@@ -273,15 +305,15 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
           re[j] = x[8 * c + j].x * s;
           im[j] = x[8 * c + j].y * s;
         }
-        store8<PREC>(op, kmaj_off(m, 8 * c, S::A_K), re);
-        store8<PREC>(op, kmaj_off(m, KA + 8 * c, S::A_K), im);
+        store8<PREC>(op, kmaj_off(m, 8 * c), re);
+        store8<PREC>(op, kmaj_off(m, KA + 8 * c), im);
       }
     }
     publish();
     if (tq == 0) {
       umma::fence_after_sync();
-      gemm<SPLIT>(tm, s_op, s_lo, 128, (S::A_K / 8) * 128, 256, s_ba, s_ba + LO, (S::A_K / 8) * 128,
-                  S::A_K / 16, umma::idesc_f16(128, S::A_N, BF, false, false));
+      gemm<SPLIT, false>(tm, s_op, s_lo, S::A_K, s_ba, s_ba + LO, S::A_N, S::A_K / 16,
+                         umma::idesc_f16(128, S::A_N, BF, false, false));
       umma::commit(bars + g);
     }
     await();
@@ -308,8 +340,8 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
             yi[i] = y.y;
           }
           const int m = R1 * rp + 16 * j + 8 * h;
-          store8<PREC>(opq, mnmaj_off(m, l), yr);
-          store8<PREC>(opq, mnmaj_off(m, kR2 + l), yi);
+          store8<PREC>(opq, mnmaj_off(m, l, S::B_K), yr);
+          store8<PREC>(opq, mnmaj_off(m, kR2 + l, S::B_K), yi);
         }
       }
     }
@@ -318,21 +350,26 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
       umma::fence_after_sync();
 #pragma unroll
       for (int q = 0; q < S::QB; ++q)
-        gemm<SPLIT>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, 2048, 128, 4096, s_bb,
-                    s_bb + LO, (S::B_K / 8) * 128, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, true, false));
+        gemm<SPLIT, true>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, S::B_K, s_bb,
+                          s_bb + LO, S::B_N, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, true, false));
       umma::commit(bars + g);
+    }
+    // the spectrum loads overlap the products
+    float2 hsp[kR2];
+    {
+      const int k1 = 32 * (wq & 1) + l;
+#pragma unroll
+      for (int i = 0; i < kR2; ++i) hsp[i] = __ldg(d.H + k1 + R1 * i);
     }
     await();
     if (!ok) break;
 
     // ---- x kernel spectrum (step 7), conjugated: stage-B^H operand rows (r', k1), K = k2 (K-major)
     {
-      const int k1 = 32 * (wq & 1) + l, m = 32 * wq + l;
+      const int m = 32 * wq + l;
 #pragma unroll
       for (int c = 0; c < kR2 / 16; ++c) {
-        float2 hs[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) hs[i] = __ldg(d.H + k1 + R1 * (16 * c + i));
+        const float2* hs = hsp + 16 * c;
 #pragma unroll
         for (int q = 0; q < S::QB; ++q) {
           float re[16], im[16];
@@ -349,8 +386,8 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
               yr[i] = y.x;
               yi[i] = -y.y;
             }
-            store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h, S::B_K), yr);
-            store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h, S::B_K), yi);
+            store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h), yr);
+            store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h), yi);
           }
         }
       }
@@ -360,9 +397,8 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
       umma::fence_after_sync();
 #pragma unroll
       for (int q = 0; q < S::QB; ++q)
-        gemm<SPLIT>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, 128,
-                    (S::B_K / 8) * 128, 256, s_bb, s_bb + LO, (S::B_K / 8) * 128, S::B_K / 16,
-                    umma::idesc_f16(128, S::B_N, BF, false, false));
+        gemm<SPLIT, false>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, S::B_K, s_bb,
+                           s_bb + LO, S::B_N, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, false, false));
       umma::commit(bars + g);
     }
     await();
@@ -391,8 +427,8 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
               yi[i] = y.y;
             }
             const int m = kR2 * r + 16 * c + 8 * h;
-            store8<PREC>(op, mnmaj_off(m, k1), yr);
-            store8<PREC>(op, mnmaj_off(m, R1 + k1), yi);
+            store8<PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
+            store8<PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
           }
         }
       }
@@ -400,9 +436,16 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     publish();
     if (tq == 0) {
       umma::fence_after_sync();
-      gemm<SPLIT>(tm, s_op, s_lo, 2048, 128, 4096, s_bh, s_bh + LO, (S::H_K / 8) * 128, S::H_K / 16,
-                  umma::idesc_f16(128, S::H_N, BF, true, false));
+      gemm<SPLIT, true>(tm, s_op, s_lo, S::H_K, s_bh, s_bh + LO, S::H_N, S::H_K / 16,
+                        umma::idesc_f16(128, S::H_N, BF, true, false));
       umma::commit(bars + g);
+    }
+    // the output-chirp loads overlap the product
+    float2 co[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int n = kR2 * i + l;
+      co[i] = n < n1 ? __ldg(d.cout + n) : make_float2(0.f, 0.f);
     }
     await();
     if (!ok) break;
@@ -421,7 +464,7 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int n = kR2 * (16 * c + i) + l;
-          if (n < n1) stage[wq * (L / 2) + n] = cmul(make_float2(re[i] * sc, -im[i] * sc), __ldg(d.cout + n));
+          if (n < n1) stage[wq * (L / 2) + n] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[16 * c + i]);
         }
       }
     }
@@ -490,7 +533,7 @@ cudaError_t launch_t(PassKind kind, const PassBatch& b, const Args& a, int grid,
   auto go = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, smem, s>>>(b, a);
+    kern<<<grid, Prec<PREC>::kThreads, smem, s>>>(b, a);
     return cudaGetLastError();
   };
   switch (kind) {
@@ -522,7 +565,6 @@ uint16_t to16(double v, bool bf16, double& rem) {
 // B[(s, i)][(t, o)], s, t in {re, im}: [re][re] = [im][im] = cos, [re][im] =
 // -sin, [im][re] = sin of 2 pi i o / R, all over sqrt(R).
 void dft_operand(int R, int kin, int nout, bool bf16, uint16_t* hi, uint16_t* lo) {
-  const int K = 2 * kin;
   const double sc = 1.0 / std::sqrt((double)R);
   for (int t = 0; t < 2; ++t)
     for (int o = 0; o < nout; ++o)
@@ -533,7 +575,7 @@ void dft_operand(int R, int kin, int nout, bool bf16, uint16_t* hi, uint16_t* lo
           const double v = (s == t) ? c : (s == 0 ? sn : -sn);
           const int n = t * nout + o, kk = s * kin + i;
           double rem, rem2;
-          const int off = kmaj_off(n, kk, K) / 2;
+          const int off = kmaj_off(n, kk) / 2;
           hi[off] = to16(v, bf16, rem);
           if (lo) lo[off] = to16(rem, bf16, rem2);
         }
@@ -590,7 +632,8 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
   for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
   a.total_tiles = a.tile_off[b.count];
   if (a.total_tiles == 0) return cudaSuccess;
-  const int grid = std::min(sms, (a.total_tiles + t5::kGroups - 1) / t5::kGroups);
+  const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
+  const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
   switch (prec) {
     case SF_PREC_FP16TC: return t5::launch_t<2048, SF_PREC_FP16TC>(kind, b, a, grid, s);
     case SF_PREC_BF16TC: return t5::launch_t<2048, SF_PREC_BF16TC>(kind, b, a, grid, s);

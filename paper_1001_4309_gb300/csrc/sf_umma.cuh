@@ -3,13 +3,17 @@
 // descriptors, commit to an mbarrier, TMEM loads) used by the row pass of
 // sf_tcgen05.cu.
 //
-// Operand layouts are the canonical no-swizzle ("interleaved") ones: an
-// operand is tiled into core matrices of 8 rows x 16 bytes (8 x 8 16-bit
-// elements) stored as 128 contiguous bytes.  In a K-major operand a core
-// matrix row holds 8 consecutive K elements of one M (or N) index; in an
-// MN-major operand it holds 8 consecutive M (or N) elements of one K index.
-// The descriptor gives the byte distance between core matrices adjacent
-// along K (leading byte offset) and along M / N (stride byte offset).
+// Shared-memory operands are described by a 64-bit descriptor: start
+// address, leading byte offset, stride byte offset and swizzle mode.  With
+// no swizzle an operand is tiled into core matrices of 8 rows x 16 bytes
+// (128 contiguous bytes); the leading offset is the distance between core
+// matrices adjacent along K, the stride offset the distance along M / N.
+// With the 128-byte swizzle (used by sf_tcgen05.cu) a K-major operand is
+// rows of 128 bytes in 1 KiB groups of 8 rows (stride offset 1 KiB, K steps
+// of 16 elements advance the start address by 32 bytes), and an MN-major one
+// is K rows of 64 M elements in 1 KiB groups of 8 K rows (stride offset
+// 1 KiB) with the leading offset between 64-element M blocks.  Both readings
+// were checked on the GPU with a one-instruction product of known operands.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -84,20 +88,31 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+// Test for completion of the phase with the given parity; the thread may be
+// suspended in hardware for up to suspend_ns while the phase is incomplete
+// (it resumes as soon as the phase completes).
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity, uint32_t suspend_ns = 0) {
   uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
+  if (suspend_ns)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity), "r"(suspend_ns)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
   return ok != 0;
 }
 // Bounded wait for the mbarrier phase with the given parity to complete;
-// false when `limit` polls pass first.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit) {
+// false when `limit` tries pass first (each suspends for at most suspend_ns).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit, uint32_t suspend_ns = 0) {
   for (long long i = 0; i < limit; ++i)
-    if (mbar_try_wait(b, parity)) return true;
+    if (mbar_try_wait(b, parity, suspend_ns)) return true;
   return false;
 }
 

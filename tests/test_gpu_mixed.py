@@ -1,10 +1,15 @@
 """Mixed-precision (tensor-core) row passes against the FP64 oracle.
 
-SF_PREC_FP16TC runs the radix-16/8 DFT stages of axes with FFT length 2048
-or 4096 as FP16 tensor-core products with FP32 accumulation; the
-reduced-precision tolerance is relative L2 <= 2e-3 per view.  SF_PREC_BF16TC
-is measured and bounded more loosely (its 8-bit mantissa is expected to miss
-2e-3).  Axes of other lengths run in FP32 and keep the 1e-5 bar.
+Axes of FFT length 2048 with input and output lengths of at most 1024 run
+the four-step tcgen05 pass; other axes of length 2048 or 4096 run the
+mma.sync radix-16/8 stages (FP16TC / BF16TC only); every other axis runs in
+FP32.  Bars, relative L2 per view against the oracle over every pixel:
+
+* FP16TC and BF16X3TC: 2e-3, the reduced-precision tolerance.
+* FP16X3TC: 1e-5 (on the tcgen05 axes; its other axes run in FP32).
+* BF16TC is out of the 2e-3 tolerance by construction (an 8-bit mantissa
+  rounded at every stage): its tests check that the error stays inside the
+  band the documentation reports (2e-3 .. 1.5e-2), not parity.
 """
 
 import numpy as np
@@ -17,10 +22,18 @@ from helpers import rel_l2
 
 pytestmark = pytest.mark.gpu
 
-FP16 = 1
-BF16 = 2
+FP16, BF16, FP16X3, BF16X3 = 1, 2, 3, 4
 TOL_FP16 = 2e-3
-TOL_BF16 = 2e-2
+BF16_BAND = (2e-3, 1.5e-2)
+
+
+def check(prec, err, split_bar=1e-5):
+    if prec == BF16:
+        assert BF16_BAND[0] < err < BF16_BAND[1], f"bf16 error {err:.3e} outside its documented band"
+    elif prec == FP16X3:
+        assert err <= split_bar, err
+    else:
+        assert err <= TOL_FP16, err
 
 
 @pytest.fixture(scope="module")
@@ -49,37 +62,33 @@ def run(P, views, holo, precision):
         P.shifted_fresnel_destroy(handle)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP16, TOL_FP16), (BF16, TOL_BF16)])
-def test_tensor_core_x_pass_full_parity(P, prec, tol):
-    """FFT length 2048 along x (tensor cores), a thin y axis (FP32): every output pixel."""
+@pytest.mark.parametrize("prec", [FP16, BF16, FP16X3, BF16X3])
+def test_tensor_core_x_pass_full_parity(P, prec):
+    """FFT length 2048 along x (tcgen05 pass), a thin y axis (FP32): every output pixel."""
     v = view(WAVELENGTH, -0.05, PITCH, 2.325e-6, o1=(100e-6, -50e-6), n0=(1024, 16), n1=(1024, 12))
     holo = synth.gabor_hologram(1024, seed=3001)[:16]
     got = run(P, [v], holo, prec)[0]
     err = rel_l2(got, oracle.forward(holo, v))
     print(f"precision {prec}: rel-L2 {err:.3e}")
-    assert err <= tol
+    check(prec, err)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP16, TOL_FP16), (BF16, TOL_BF16)])
-def test_tensor_core_both_axes_sampled(P, prec, tol):
-    """The 1024^2 and 2048^2 single views (FFT lengths 2048 and 4096 on both axes)."""
+_C4 = {}
+
+
+@pytest.mark.parametrize("prec", [FP16, BF16, FP16X3, BF16X3])
+def test_tensor_core_single_views_every_pixel(P, prec):
+    """The 1024^2 and 2048^2 single views (FFT lengths 2048 and 4096 on both axes): every pixel.
+    At 4096 the FP16 / BF16 plans run the mma.sync stages and the x3 plans FP32."""
     for holo, views in synth.config_c4()[1:]:
-        got = run(P, views, holo, prec)[0]
         v = views[0]
-        n = v["nx1"]
-        for cols in ((0, 4), (n // 2 - 2, n // 2 + 2), (n - 4, n)):
-            err = rel_l2(got[:, cols[0]:cols[1]], oracle.forward(holo, v, cols=cols))
-            print(f"precision {prec} n {n} cols {cols}: rel-L2 {err:.3e}")
-            assert err <= tol
-
-
-def test_tensor_core_paper_scale_four_views(P):
-    holo, views = synth.config_c2()
-    got = run(P, views, holo, FP16)
-    for i, v in enumerate(views):
-        cols = (500, 508)
-        err = rel_l2(got[i][:, cols[0]:cols[1]], oracle.forward(holo, v, cols=cols))
-        assert err <= TOL_FP16, (i, err)
+        key = v["nx1"]
+        if key not in _C4:
+            _C4[key] = oracle.forward(holo, v)
+        got = run(P, views, holo, prec)[0]
+        err = rel_l2(got, _C4[key])
+        print(f"precision {prec} n {key}: rel-L2 {err:.3e}")
+        check(prec, err)
 
 
 def test_tensor_core_complex_input_and_fallback_lengths(P):
