@@ -42,6 +42,11 @@ PAPER_CONTEXT = {  # the paper's own figures (Section 3), other hardware: contex
            "(2x GTX 295, CUDA 2.3, CUFFT), loop including host copies",
     "cpu": "the same four views in 9,542 ms (about 0.42 views/s) on a Core2Quad Q6600"}
 PAPER_GPU_VIEWS_PER_S = 4 / 0.060  # the paper's four views in about 60 ms, host copies included
+# plan precision (SF_PREC_*) and the arithmetic type the bench line reports for it
+PRECISIONS = {"fp32": (0, "f32"), "fp16tc": (1, "f16"), "bf16tc": (2, "bf16"), "fp16x3tc": (3, "f16x3"),
+              "bf16x3tc": (4, "bf16x3")}
+# real GEMM flops per row of the tcgen05 pass at L = 2048 (four products of 524288 flops; x3: three each)
+T5_FLOPS_PER_ROW = 4 * 2 * 32 * 64 * 128
 
 
 _ORACLE_VIEWS = {}  # (id of hologram, view) -> (hologram, oracle view): each whole view computed once
@@ -84,6 +89,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the tensor-core precision measurements")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / phase-retrieval measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="minimum oracle time for cpu_baseline")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32",
+                    help="arithmetic of the timed step (fp32: the headline; the others run the tensor-core passes)")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -256,7 +263,8 @@ def run_ours(a):
     V = len(views)
     torch.cuda.synchronize()
     t_plan = time.perf_counter()
-    sf = P.ShiftedFresnel(views, device=local)  # plan creation synchronises its stream
+    prec_code, prec_dtype = PRECISIONS[a.precision]
+    sf = P.ShiftedFresnel(views, device=local, precision=prec_code)  # plan creation synchronises its stream
     plan_ms = (time.perf_counter() - t_plan) * 1e3
     lengths = [sf.sizes(i)[:2] for i in range(V)]
     holo = torch.from_numpy(holo_np).to(dev)
@@ -320,7 +328,8 @@ def run_ours(a):
     dom_bytes, dom_flops = alg[dom]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     hbm_peak = float(peaks["hbm_gbs"])
-    kernel_key = f"k_pass<2048,{'PASS_Y' if dom == 'y' else 'PASS_X_REAL'}>"
+    kname = "k_pass" if prec_code == 0 else "k_pass_t5"
+    kernel_key = f"{kname}<2048,{'PASS_Y' if dom == 'y' else 'PASS_X_REAL'}>"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": ncu_traffic(kernel_key),
                 "kernel": kernel_key, "peak_source": f"{peak_kind} hbm_gbs",
@@ -334,11 +343,21 @@ def run_ours(a):
     sm_max_mhz = clk.get("sm_max_mhz") or 2070.0
     fp32_peak = sm_count * 128 * 2 * sm_max_mhz * 1e6 / 1e12
     dom_tflops = dom_flops / (dom_ms * 1e-3) / 1e12
-    roofline["alu_co_bound"] = {
-        "bound": "alu", "achieved": round(dom_tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-        "frac": round(dom_tflops / fp32_peak, 4),
-        "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flops/FMA x {sm_max_mhz:.0f} MHz",
-        "flops": "nominal 2 x 5 L log2 L per row (forward + inverse FFT)"}
+    if prec_code == 0:
+        roofline["alu_co_bound"] = {
+            "bound": "alu", "achieved": round(dom_tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+            "frac": round(dom_tflops / fp32_peak, 4),
+            "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flops/FMA x {sm_max_mhz:.0f} MHz",
+            "flops": "nominal 2 x 5 L log2 L per row (forward + inverse FFT)"}
+    else:
+        rows_dom = sum(v["ny0"] if dom == "x" else v["nx1"] for v in views)
+        mult = 3 if a.precision.endswith("x3tc") else 1
+        t_tflops = mult * T5_FLOPS_PER_ROW * rows_dom / (dom_ms * 1e-3) / 1e12
+        bpeak = float(peaks.get("bf16_tflops", 1900.0))
+        roofline["tensor_co_bound"] = {
+            "bound": "tensor", "achieved": round(t_tflops, 2), "peak": bpeak, "unit": "TFLOP/s",
+            "frac": round(t_tflops / bpeak, 4), "peak_source": f"{peak_kind} bf16_tflops (FP16 has the same dense rate)",
+            "flops": f"real GEMM flops of the four DFT products per row ({T5_FLOPS_PER_ROW}{' x 3' if mult == 3 else ''})"}
     passes = {p: {"ms": round(m, 5), "algorithmic_bytes": alg[p][0],
                   "gbs": round(alg[p][0] / (m * 1e-3) / 1e9, 1),
                   "nominal_tflops": round(alg[p][1] / (m * 1e-3) / 1e12, 2)}
@@ -400,9 +419,9 @@ def run_ours(a):
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 5),
             "ms_per_step_median": round(statistics.median(step_ms), 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec_dtype,
             "data": "synthetic (seeded in-line Gabor holograms; the paper's real holograms are not available)",
-            "config": {"workload": WORKLOAD, "views_per_step": V, "fft_lengths": lengths[0],
+            "config": {"workload": WORKLOAD, "views_per_step": V, "fft_lengths": lengths[0], "precision": a.precision,
                        "outputs": "complex64 field per view", "l2": "flushed between timed steps (256 MiB write, then 256 MiB read of another buffer)",
                        "inputs": "device-resident hologram and outputs",
                        "parallelism": f"replicas x{world} (views independent per rank)"},
@@ -414,7 +433,7 @@ def run_ours(a):
             "io_lower_bound": {"bytes_per_step": io_bytes,
                                "hbm_frac": round(io_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak, 4),
                                "what": "hologram read once + complex views written once"},
-            "accuracy_fp32": accuracy,
+            f"accuracy_{a.precision}": accuracy,
             "plan_ms": round(plan_ms, 2),
             "paper_context": dict(PAPER_CONTEXT, e2e_over_paper_gpu=round(e2e["value"] / PAPER_GPU_VIEWS_PER_S, 1)),
             "plain_path": plain,
@@ -557,7 +576,8 @@ def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm
     import synth
     import paper_1001_4309_gb300 as P
     precs = (("fp32", P.binding.SF_PREC_FP32), ("fp16tc", P.binding.SF_PREC_FP16TC),
-             ("bf16tc", P.binding.SF_PREC_BF16TC))
+             ("bf16tc", P.binding.SF_PREC_BF16TC), ("fp16x3tc", P.binding.SF_PREC_FP16X3TC),
+             ("bf16x3tc", P.binding.SF_PREC_BF16X3TC))
     res = {"fp32_value": round(fp32_value, 1)}
     for name, prec in precs[1:]:
         ms, fields = time_precision(views, holo, prec, dev, stream, flush, a.steps, a.warmup)
@@ -575,10 +595,24 @@ def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm
             ms, fields = time_precision(vs, h, prec, dev, stream, flush, 20, 3)
             e = view_errors(h_np, vs, fields)[0]
             entry[name] = {"views_per_s": round(1 / (ms * 1e-3), 1), "rel_l2": e["rel_l2"],
-                           "max_abs_rel": e["max_abs_rel"]}
+                           "max_abs_rel": e["max_abs_rel"], "row_pass": row_pass_kind(vs[0], prec)}
         singles.append(entry)
     res["single_views"] = singles
     return res
+
+
+def row_pass_kind(v, prec):
+    """Which row pass a square view's axes run at a precision (the library's dispatch rule, for labels)."""
+    L = 1
+    while L < v["nx0"] + v["nx1"] - 1:
+        L *= 2
+    if prec == 0:
+        return "fp32"
+    if L == 2048 and 2 * v["nx0"] <= L and 2 * v["nx1"] <= L:
+        return "tcgen05"
+    if L in (2048, 4096) and prec in (1, 2):
+        return "mma.sync"
+    return f"fp32 (no tensor-core pass at FFT length {L})"
 
 
 def differentiable(dev, stream):
