@@ -366,7 +366,9 @@ int shifted_fresnel_set_profile_events(sf_plan plan, void* const* events, int n_
  * cleared, but calls that overlap on the GPU (other streams, other host
  * threads on the same device) race and corrupt each other's results.  The
  * first call on each device looks up the array's device address, which may
- * load the module: make that first call before any stream capture.
+ * load the module: make that first call before any stream capture.  The
+ * address is kept per device and CUDA context; after a device reset the next
+ * call looks it up again (make that call outside stream capture too).
  * Errors: SF_ERR_INVALID_ARG, SF_ERR_UNSUPPORTED_SIZE, SF_ERR_DEVICE_MISMATCH,
  * SF_ERR_CUDA.
  */

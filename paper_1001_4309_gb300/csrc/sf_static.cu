@@ -21,7 +21,9 @@
 //     each other's results;
 //   - the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress, which may load the module), so make that first
-//     call before any stream capture.
+//     call before any stream capture; the address is kept per device and
+//     CUDA context, so the first call after a device reset (a new context)
+//     looks it up again and must also come before any capture.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -49,22 +51,49 @@ static_assert(sizeof(float2) * SF_STATIC_MAX_FFT_LENGTH <= kVecBytes, "vector sl
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_dev[kMaxDevices] = {};
+struct ScratchAddr {
+  void* addr = nullptr;  // device address of the array ...
+  void* ctx = nullptr;   // ... in this context (a device reset makes a new one)
+};
+ScratchAddr g_scratch[kMaxDevices];
 
-// Device address of the scratch array on the current device `dev`.
+// The calling thread's current CUDA context (driver cuCtxGetCurrent, reached
+// through the runtime's entry-point query); nullptr if unavailable.
+void* current_context() {
+  using Fn = int (*)(void**);
+  static const Fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (Fn) nullptr;
+    }
+    return reinterpret_cast<Fn>(f);
+  }();
+  void* c = nullptr;
+  if (!fn || fn(&c) != 0) return nullptr;
+  return c;
+}
+
+// Device address of the scratch array on the current device `dev`, looked up
+// once per device and context (again after a device reset).
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return SF_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_dev[dev]) {
+  ScratchAddr& sa = g_scratch[dev];
+  void* ctx = current_context();
+  if (!sa.addr || !ctx || ctx != sa.ctx) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, sf_static_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return SF_ERR_CUDA;
     }
-    g_scratch_dev[dev] = p;
+    sa.addr = p;
+    sa.ctx = current_context();  // the lookup has made the context current if it was not
   }
-  *out = g_scratch_dev[dev];
+  *out = sa.addr;
   return SF_OK;
 }
 

@@ -100,3 +100,32 @@ def test_static_entry_rejects_sizes_beyond_its_scratch(P):
     too_big = view(WAVELENGTH, 0.05, PITCH, PITCH, n0=(8, 1100), n1=(1000, 8))  # nx1 * ny0 > 2^20
     assert P.shifted_fresnel_execute_static(too_big, holo.data_ptr(), out.data_ptr(), check=False) \
         == P.SF_ERR_UNSUPPORTED_SIZE
+
+
+VIEW_D = view(WAVELENGTH, 0.05, PITCH, 2.0e-6, o1=(2e-4, -1e-4), n0=(1024, 1024), n1=(1024, 1024))  # L 2048, 2^20
+
+
+def test_static_entry_allocates_nothing_at_its_largest_view(P):
+    """The largest supported view (FFT length 2048 on both axes, nx1 * ny0 = 2^20), with every output
+    combination, including an intensity image alone: same results as the plan path, and the device's
+    free memory does not change across the calls (after a first call, which may load the module)."""
+    import torch
+    hd = inputs(VIEW_D, 4)
+    ref = plan_path(P, VIEW_D, hd)
+    shp = (VIEW_D["ny1"], VIEW_D["nx1"])
+    f = torch.empty(shp, dtype=torch.complex64, device="cuda")
+    I = torch.empty(shp, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    P.shifted_fresnel_execute_static(VIEW_D, hd.data_ptr(), f.data_ptr(), None, None, stream=s)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    I.zero_()
+    P.shifted_fresnel_execute_static(VIEW_D, hd.data_ptr(), None, I.data_ptr(), None, stream=s)  # intensity only
+    torch.cuda.synchronize()
+    intensity_only = I.cpu().numpy()
+    P.shifted_fresnel_execute_static(VIEW_D, hd.data_ptr(), f.data_ptr(), I.data_ptr(), None, stream=s)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert rel_l2(f.cpu().numpy(), ref["field"].cpu().numpy()) <= TOL
+    assert rel_l2(intensity_only, ref["intensity"].cpu().numpy()) <= 3 * TOL
+    assert np.array_equal(intensity_only, I.cpu().numpy())
