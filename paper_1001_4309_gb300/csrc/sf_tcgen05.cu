@@ -67,6 +67,8 @@ namespace t5 {
 
 constexpr int kR2 = 32;        // inner radix: the lanes of a warp
 constexpr int kRows = 4;       // rows per tile (one warp per row in the first stage)
+constexpr int kGroupWarps = 8;  // warps per group: two per tensor-memory lane quarter
+constexpr int kGroupThreads = 32 * kGroupWarps;
 // MMA completion waits: tries of at most kSuspendNs each (the waiting thread
 // sleeps in hardware instead of spinning), kSpin tries (about 1 s) in all
 constexpr uint32_t kSuspendNs = 20000;
@@ -77,7 +79,7 @@ struct Prec {
   static constexpr bool kBf16 = PREC == SF_PREC_BF16TC || PREC == SF_PREC_BF16X3TC;
   static constexpr bool kSplit = PREC == SF_PREC_FP16X3TC || PREC == SF_PREC_BF16X3TC;
   static constexpr int kGroups = kSplit ? 2 : 4;
-  static constexpr int kThreads = 128 * kGroups;
+  static constexpr int kThreads = kGroupThreads * kGroups;
 };
 
 template <int L>
@@ -104,7 +106,8 @@ struct Shape {
   static constexpr int op_offset(bool split) { return align(const_bytes(split)); }
   static constexpr int group_bytes(bool split) { return (split ? 2 : 1) * OP_BYTES; }
   static constexpr int misc_offset(bool split) { return op_offset(split) + (split ? 2 : 4) * group_bytes(split); }
-  static constexpr int smem_bytes(bool split) { return misc_offset(split) + 64; }
+  // misc: one mbarrier per group, the tensor-memory base, per-warp row maxima (from byte 64)
+  static constexpr int smem_bytes(bool split) { return misc_offset(split) + 64 + 4 * kGroupWarps * 4; }
 };
 
 // Operand layouts, 128-byte swizzle (16-bit elements; every operand starts on
@@ -166,16 +169,16 @@ __device__ __forceinline__ void store8(unsigned char* hi, int off, const float (
 }
 
 __device__ __forceinline__ void group_bar(int g) {
-  asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kGroupThreads) : "memory");
 }
-// Group barrier that also ANDs a flag over the group's 128 threads.
+// Group barrier that also ANDs a flag over the group's threads.
 __device__ __forceinline__ bool group_bar_and(int g, bool v) {
   uint32_t r;
   asm volatile(
-      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbarrier.cta.red.and.pred po, %2, 128, pi;\n\t"
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbarrier.cta.red.and.pred po, %2, %3, pi;\n\t"
       "selp.u32 %0, 1, 0, po;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)v), "r"(1 + g)
+      : "r"((uint32_t)v), "r"(1 + g), "n"(kGroupThreads)
       : "memory");
   return r != 0;
 }
@@ -216,11 +219,16 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
   constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
   constexpr int kGroups = Prec<PREC>::kGroups, kThreads = Prec<PREC>::kThreads;
   constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
+  constexpr int KH = KA / 2, NH = NA / 2, CH = kR2 / 2;  // each warp's half of n1 (in, out) and of n2 / k2
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int g = threadIdx.x >> 7, tq = threadIdx.x & 127, wq = tq >> 5, l = tq & 31;
+  const int g = threadIdx.x / kGroupThreads, tq = threadIdx.x % kGroupThreads;
+  // warp gw of the group: tensor-memory lane quarter wq, column half hh
+  const int gw = tq >> 5, wq = gw & 3, hh = gw >> 2, l = tq & 31;
   unsigned char* const op = sm + S::op_offset(SPLIT) + g * S::group_bytes(SPLIT);
-  uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + S::misc_offset(SPLIT));
-  uint32_t* const tbase = reinterpret_cast<uint32_t*>(sm + S::misc_offset(SPLIT) + 8 * kGroups);
+  unsigned char* const misc = sm + S::misc_offset(SPLIT);
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(misc);
+  uint32_t* const tbase = reinterpret_cast<uint32_t*>(misc + 8 * kGroups);
+  float* const rowmax = reinterpret_cast<float*>(misc + 64) + kGroupWarps * g;
   const float2* const tw = reinterpret_cast<const float2*>(sm + (SPLIT ? 2 : 1) * S::MAT_BYTES);
 
   for (int i = threadIdx.x; i < S::const_bytes(SPLIT) / 16; i += kThreads)
@@ -268,16 +276,18 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     const int row0 = (tile - a.tile_off[p]) * kRows;
     const int n0 = d.n0, n1 = d.n1;
 
-    // ---- input x chirp (steps 2-3), row normalisation, stage-A operand (K-major)
+    // ---- input x chirp (steps 2-3), row normalisation, stage-A operand (K-major).
+    // Warp (wq, hh) takes row wq, n1 in [KH hh, KH hh + KH); the row's maximum
+    // is combined with the other half's through shared memory.
     float inv_scale;
     {
       const int row = row0 + wq;
       const bool valid = row < d.rows;
-      float2 x[KA];
+      float2 x[KH];
       float mx = 0.f;
 #pragma unroll
-      for (int i = 0; i < KA; ++i) {
-        const int n = kR2 * i + l;
+      for (int i = 0; i < KH; ++i) {
+        const int n = kR2 * (KH * hh + i) + l;
         float2 v = make_float2(0.f, 0.f);
         if (valid && n < n0) {
           const float2 c = __ldg(d.cin + n);
@@ -292,21 +302,24 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (l == 0) rowmax[gw] = mx;
+      group_bar(g);
+      mx = fmaxf(mx, rowmax[gw ^ 4]);
       int e = 0;
       if (mx > 0.f) frexpf(mx, &e);
       const float s = ldexpf(1.f, -e);  // max * s in [0.5, 1)
       inv_scale = ldexpf(1.f, e);
       const int m = 32 * wq + l;
 #pragma unroll
-      for (int c = 0; c < KA / 8; ++c) {
+      for (int c = 0; c < KH / 8; ++c) {
         float re[8], im[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           re[j] = x[8 * c + j].x * s;
           im[j] = x[8 * c + j].y * s;
         }
-        store8<PREC>(op, kmaj_off(m, 8 * c), re);
-        store8<PREC>(op, kmaj_off(m, KA + 8 * c), im);
+        store8<PREC>(op, kmaj_off(m, KH * hh + 8 * c), re);
+        store8<PREC>(op, kmaj_off(m, KA + KH * hh + 8 * c), im);
       }
     }
     publish();
@@ -319,12 +332,14 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     await();
     if (!ok) break;
 
-    // ---- twiddle W_L^{n2 k1}; stage-B operand rows (r', k1), K = n2 (MN-major)
+    // ---- twiddle W_L^{n2 k1}; stage-B operand rows (r', k1), K = n2 (MN-major).
+    // Lane (r = wq, n2 = l); warp half hh takes k1 in [R1/2 hh, R1/2 hh + R1/2).
     {
       const int q = wq >> 1, rp = wq & 1;
       unsigned char* opq = op + q * 128 * S::B_K * 2;
 #pragma unroll
-      for (int j = 0; j < R1 / 16; ++j) {
+      for (int jj = 0; jj < R1 / 32; ++jj) {
+        const int j = (R1 / 32) * hh + jj;
         float re[16], im[16];
         umma::tmem_ld16(tm + lanes + 16 * j, re);
         umma::tmem_ld16(tm + lanes + R1 + 16 * j, im);
@@ -354,41 +369,39 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
                           s_bb + LO, S::B_N, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, true, false));
       umma::commit(bars + g);
     }
-    // the spectrum loads overlap the products
-    float2 hsp[kR2];
+    // the spectrum loads overlap the products: this thread's k1, k2 in [CH hh, CH hh + CH)
+    float2 hsp[CH];
     {
       const int k1 = 32 * (wq & 1) + l;
 #pragma unroll
-      for (int i = 0; i < kR2; ++i) hsp[i] = __ldg(d.H + k1 + R1 * i);
+      for (int i = 0; i < CH; ++i) hsp[i] = __ldg(d.H + k1 + R1 * (CH * hh + i));
     }
     await();
     if (!ok) break;
 
-    // ---- x kernel spectrum (step 7), conjugated: stage-B^H operand rows (r', k1), K = k2 (K-major)
+    // ---- x kernel spectrum (step 7), conjugated: stage-B^H operand rows (r', k1), K = k2 (K-major).
+    // Warp half hh takes k2 in [CH hh, CH hh + CH).
     {
       const int m = 32 * wq + l;
+      const int c = hh;
 #pragma unroll
-      for (int c = 0; c < kR2 / 16; ++c) {
-        const float2* hs = hsp + 16 * c;
+      for (int q = 0; q < S::QB; ++q) {
+        float re[16], im[16];
+        umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
+        umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
+        umma::tmem_wait_ld();
+        unsigned char* opq = op + q * 128 * S::B_K * 2;
 #pragma unroll
-        for (int q = 0; q < S::QB; ++q) {
-          float re[16], im[16];
-          umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
-          umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
-          umma::tmem_wait_ld();
-          unsigned char* opq = op + q * 128 * S::B_K * 2;
+        for (int h = 0; h < 2; ++h) {
+          float yr[8], yi[8];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float yr[8], yi[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), hs[8 * h + i]);
-              yr[i] = y.x;
-              yi[i] = -y.y;
-            }
-            store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h), yr);
-            store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h), yi);
+          for (int i = 0; i < 8; ++i) {
+            const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), hsp[8 * h + i]);
+            yr[i] = y.x;
+            yi[i] = -y.y;
           }
+          store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h), yr);
+          store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h), yi);
         }
       }
     }
@@ -404,32 +417,31 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     await();
     if (!ok) break;
 
-    // ---- twiddle W_L^{n2 k1}: stage-A^H operand rows (r, n2), K = k1 (MN-major)
+    // ---- twiddle W_L^{n2 k1}: stage-A^H operand rows (r, n2), K = k1 (MN-major).
+    // Lane (r', k1); warp half hh takes n2 in [CH hh, CH hh + CH).
     {
       const int k1 = 32 * (wq & 1) + l;
+      const int c = hh;
 #pragma unroll
       for (int q = 0; q < S::QB; ++q) {
         const int r = 2 * q + (wq >> 1);
+        float re[16], im[16];
+        umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
+        umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
+        umma::tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < kR2 / 16; ++c) {
-          float re[16], im[16];
-          umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
-          umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
-          umma::tmem_wait_ld();
+        for (int h = 0; h < 2; ++h) {
+          float yr[8], yi[8];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float yr[8], yi[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int n2 = 16 * c + 8 * h + i;
-              const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + n2]);
-              yr[i] = y.x;
-              yi[i] = y.y;
-            }
-            const int m = kR2 * r + 16 * c + 8 * h;
-            store8<PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
-            store8<PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
+          for (int i = 0; i < 8; ++i) {
+            const int n2 = 16 * c + 8 * h + i;
+            const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + n2]);
+            yr[i] = y.x;
+            yi[i] = y.y;
           }
+          const int m = kR2 * r + 16 * c + 8 * h;
+          store8<PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
+          store8<PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
         }
       }
     }
@@ -440,11 +452,11 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
                         umma::idesc_f16(128, S::H_N, BF, true, false));
       umma::commit(bars + g);
     }
-    // the output-chirp loads overlap the product
-    float2 co[NA];
+    // the output-chirp loads overlap the product: this thread's n1 in [NH hh, NH hh + NH)
+    float2 co[NH];
 #pragma unroll
-    for (int i = 0; i < NA; ++i) {
-      const int n = kR2 * i + l;
+    for (int i = 0; i < NH; ++i) {
+      const int n = kR2 * (NH * hh + i) + l;
       co[i] = n < n1 ? __ldg(d.cout + n) : make_float2(0.f, 0.f);
     }
     await();
@@ -456,15 +468,15 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
       const float sc = inv_scale * (float)L * sqrtf((float)L);
       float2* stage = reinterpret_cast<float2*>(op);
 #pragma unroll
-      for (int c = 0; c < NA / 16; ++c) {
-        float re[16], im[16];
-        umma::tmem_ld16(tm + lanes + 16 * c, re);
-        umma::tmem_ld16(tm + lanes + NA + 16 * c, im);
+      for (int c = 0; c < NH / 8; ++c) {
+        float re[8], im[8];
+        umma::tmem_ld8(tm + lanes + NH * hh + 8 * c, re);
+        umma::tmem_ld8(tm + lanes + NA + NH * hh + 8 * c, im);
         umma::tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int n = kR2 * (16 * c + i) + l;
-          if (n < n1) stage[wq * (L / 2) + n] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[16 * c + i]);
+        for (int i = 0; i < 8; ++i) {
+          const int n = kR2 * (NH * hh + 8 * c + i) + l;
+          if (n < n1) stage[wq * (L / 2) + n] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[8 * c + i]);
         }
       }
     }
@@ -479,7 +491,7 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
       float* const phase = d.phase;
       const size_t ld = (size_t)d.dst_ld;
       const bool acc = d.accumulate != 0;
-      for (int i = tq; i < n1 * kRows; i += 128) {
+      for (int i = tq; i < n1 * kRows; i += kGroupThreads) {
         const int n = i >> 2, r = i & 3;
         if (r < rows_here) {
           const float2 u = stage[r * (L / 2) + n];
