@@ -107,7 +107,8 @@ struct Shape {
   static constexpr int op_offset(bool split) { return align(const_bytes(split)); }
   static constexpr int group_bytes(bool split) { return (split ? 2 : 1) * OP_BYTES; }
   static constexpr int misc_offset(bool split) { return op_offset(split) + (split ? 2 : 4) * group_bytes(split); }
-  // misc: one mbarrier per group, the tensor-memory base, per-warp row maxima (from byte 64)
+  // misc: one MMA mbarrier per group (from byte 0), the constant-image mbarrier (32), the
+  // tensor-memory base (48), per-warp row maxima (from byte 64)
   static constexpr int smem_bytes(bool split) { return misc_offset(split) + 64 + 4 * kGroupWarps * 4; }
 };
 
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(Prec<PREC>::kThreads, 1)
 k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
   using S = Shape<L>;
   constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
-  constexpr int kGroups = Prec<PREC>::kGroups, kThreads = Prec<PREC>::kThreads;
+  constexpr int kGroups = Prec<PREC>::kGroups;
   constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
   constexpr int KH = KA / 2, NH = NA / 2, CH = kR2 / 2;  // each warp's half of n1 (in, out) and of n2 / k2
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -234,18 +235,23 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
   unsigned char* const op = sm + S::op_offset(SPLIT) + g * S::group_bytes(SPLIT);
   unsigned char* const misc = sm + S::misc_offset(SPLIT);
   uint64_t* const bars = reinterpret_cast<uint64_t*>(misc);
-  uint32_t* const tbase = reinterpret_cast<uint32_t*>(misc + 8 * kGroups);
+  uint64_t* const cbar = reinterpret_cast<uint64_t*>(misc + 32);
+  uint32_t* const tbase = reinterpret_cast<uint32_t*>(misc + 48);
   float* const rowmax = reinterpret_cast<float*>(misc + 64) + kGroupWarps * g;
   const float2* const tw = reinterpret_cast<const float2*>(sm + (SPLIT ? 2 : 1) * S::MAT_BYTES);
 
-  for (int i = threadIdx.x; i < S::const_bytes(SPLIT) / 16; i += kThreads)
-    reinterpret_cast<uint4*>(sm)[i] = a.consts[i];
   if (tq == 0) umma::mbar_init(bars + g, 1);
+  if (threadIdx.x == 0) umma::mbar_init(cbar, 1);
   if (threadIdx.x < 32) umma::tmem_alloc(tbase, 128 * kGroups);
-  umma::fence_smem_to_async();
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
+  // the constant image arrives by one bulk copy while the first tile's inputs load
+  if (threadIdx.x == 0) {
+    umma::mbar_arrive_expect_tx(cbar, S::const_bytes(SPLIT));
+    umma::bulk_g2s(sm, a.consts, S::const_bytes(SPLIT), cbar);
+  }
+  bool consts_ready = false;
 
   const uint32_t tm = *tbase + 128u * g;
   const uint32_t lanes = (uint32_t)(32 * wq) << 16;  // this warp's tensor-memory lanes
@@ -329,6 +335,16 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
         store8<PREC>(op, kmaj_off(m, KH * hh + 8 * c), re);
         store8<PREC>(op, kmaj_off(m, KA + KH * hh + 8 * c), im);
       }
+    }
+    if (!consts_ready) {  // first tile: every thread sees the constant image before using it
+      bool w = umma::mbar_wait(cbar, 0, kSpin, kSuspendNs);
+      if (!w && threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        umma::mbar_wait(cbar, 0, kSpin, kSuspendNs);
+      }
+      consts_ready = true;
+      ok = group_bar_and(g, w);
+      if (!ok) break;
     }
     publish();
     if (tq == 0) {

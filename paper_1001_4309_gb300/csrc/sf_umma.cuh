@@ -93,6 +93,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// One arrival on b that also adds bytes to its expected transaction count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// Bulk copy global -> this CTA's shared memory (both addresses 16-byte aligned,
+// bytes a multiple of 16), completed as transactions on mbarrier b.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
 // 2D tensor store (TMA) of a box from this CTA's shared memory; coordinates in
 // elements, innermost first; joins the thread's current bulk async-group.
 __device__ __forceinline__ void tma_store_2d(const void* tmap, const void* src, int x, int y) {
