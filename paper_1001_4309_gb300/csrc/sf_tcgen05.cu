@@ -74,6 +74,7 @@ constexpr int kGroupThreads = 32 * kGroupWarps;
 // sleeps in hardware instead of spinning), kSpin tries (about 1 s) in all
 constexpr uint32_t kSuspendNs = 20000;
 constexpr long long kSpin = 50000;
+constexpr unsigned kStaggerNs = 1000;  // start offset between a CTA's groups
 
 template <int PREC>
 struct Prec {
@@ -252,6 +253,10 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     umma::bulk_g2s(sm, a.consts, S::const_bytes(SPLIT), cbar);
   }
   bool consts_ready = false;
+  // Groups start kStaggerNs apart: their products then reach the SM's tensor core at
+  // different times instead of queueing behind one another, and their loads and stores
+  // spread out in time.
+  if (kStaggerNs > 0 && g > 0) __nanosleep(kStaggerNs * g);
 
   const uint32_t tm = *tbase + 128u * g;
   const uint32_t lanes = (uint32_t)(32 * wq) << 16;  // this warp's tensor-memory lanes
