@@ -26,6 +26,7 @@
 
 #include "sf_fft.cuh"
 #include "sf_internal.h"
+#include "sf_umma.cuh"
 
 // CTA size and resident warps per SM the power-of-two row passes are built for
 constexpr int kPassCtaThreads = 256;
@@ -114,10 +115,12 @@ struct StagedSrc {
 // transposed (dst[p * dst_ld + r]) through a shared-memory tile so the G rows
 // of the tile leave as G-element contiguous runs.  With SPARE, the CTA may
 // have more threads than the tile's G T (a CTA sized for another length):
-// those only join the CTA barriers and the final store loop.
+// those only join the CTA barriers and the final store loop.  With out_map
+// (G even, no SPARE), thread 0 sends the tile out by 2D tensor stores instead
+// and waits only until they have read shared memory.
 template <int L, int KIND, typename Src, bool SPARE = false, int CTA = pass_cta_target(L), bool PRUNE = false>
 __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw,
-                                             const Src& src) {
+                                             const Src& src, const CUtensorMap* out_map = nullptr) {
   using Sh = PassShape<L, CTA>;
   constexpr int T = Sh::T, G = Sh::G, E = fft_e(L);
   // PRUNE (caller-checked: n0 <= L / 2 and n1 <= L / 2, E = 16): positions
@@ -154,6 +157,18 @@ __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2
   } else {
     __syncthreads();
   }
+  if constexpr (!SPARE && G % 2 == 0) {
+    if (out_map) {
+      umma::fence_smem_to_async();  // the tile's shared-memory writes, to the tensor stores
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int j = 0; j * kOutBoxN < n1; ++j) umma::tma_store_2d(out_map, smem + j * kOutBoxN * G, 2 * row0, j * kOutBoxN);
+        umma::bulk_commit();
+        umma::bulk_wait_read();
+      }
+      return;
+    }
+  }
   __syncthreads();
   // descriptor fields in registers: a descriptor in global memory (batch
   // kernel) would otherwise be re-read after every store
@@ -181,21 +196,23 @@ __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2
 }
 
 template <int L, int KIND, bool COHERENT, bool SPARE = false, int CTA = pass_cta_target(L), bool PRUNE = false>
-__device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw) {
+__device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* smem, const float4* __restrict__ tw,
+                                         const CUtensorMap* out_map = nullptr) {
   row_tile_src<L, KIND, GlobalSrc<KIND, COHERENT>, SPARE, CTA, PRUNE>(d, row0, smem, tw,
-                                                                      GlobalSrc<KIND, COHERENT>{d});
+                                                                      GlobalSrc<KIND, COHERENT>{d}, out_map);
 }
 
 // Row pass: tile blockIdx.x of pass blockIdx.y.  PRUNE: every pass of the
 // launch has n0 <= L / 2 and n1 <= L / 2 (the paper's 2N padding).
 template <int L, int KIND, bool PRUNE>
 __global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
-k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw) {
-  extern __shared__ float2 smem[];
+k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, const __grid_constant__ OutMaps om) {
+  extern __shared__ __align__(128) float2 smem[];
   const PassDesc& d = b.d[blockIdx.y];
   const int row0 = blockIdx.x * PassShape<L>::G;
   if (row0 >= d.rows) return;  // whole CTA past this pass's rows
-  row_tile<L, KIND, false, false, pass_cta_target(L), PRUNE>(d, row0, smem, tw);
+  row_tile<L, KIND, false, false, pass_cta_target(L), PRUNE>(d, row0, smem, tw,
+                                                             om.use[blockIdx.y] ? &om.map[blockIdx.y] : nullptr);
 }
 
 // The pruned network applies to the radix-16 (power-of-two) lengths.
@@ -236,12 +253,15 @@ template <int L>
 cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s) {
   using Sh = PassShape<L>;
   const dim3 grid(grid_x, b.count), block(Sh::THREADS);
+  OutMaps om;
+  for (int k = 0; k < kMaxPassBatch; ++k)
+    om.use[k] = k < b.count && Sh::G % 2 == 0 && output_tensor_map(kind, b.d[k], Sh::G, &om.map[k]) ? 1 : 0;
   auto go = [&](auto kern) {
     if (Sh::SMEM > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
       if (e != cudaSuccess) return e;
     }
-    kern<<<grid, block, Sh::SMEM, s>>>(b, tw);
+    kern<<<grid, block, Sh::SMEM, s>>>(b, tw, om);
     return cudaGetLastError();
   };
   if constexpr (is_pow2(L)) {

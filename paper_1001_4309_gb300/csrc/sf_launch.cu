@@ -28,6 +28,42 @@ int fft_length_slot(int L) {
 
 bool fft_length_supported(int L) { return fft_length_slot(L) >= 0; }
 
+namespace {
+// cuTensorMapEncodeTiled from the driver (null when it cannot be reached)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+}  // namespace
+
+bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorMap* map) {
+  if (!d.dst || d.rows <= 0 || d.n1 <= 0 || box_rows <= 0 || (box_rows & 1) != 0) return false;
+  if (kind == PASS_Y && (d.inten || d.phase || d.accumulate)) return false;
+  if ((reinterpret_cast<uintptr_t>(d.dst) & 15) != 0 || (d.dst_ld & 1) != 0) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, d.dst) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeDevice) return false;
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return false;
+  const cuuint64_t dims[2] = {2 * (cuuint64_t)d.rows, (cuuint64_t)d.n1};
+  const cuuint64_t strides[1] = {(cuuint64_t)d.dst_ld * 8};
+  const cuuint32_t box[2] = {2 * (cuuint32_t)box_rows, (cuuint32_t)kOutBoxN};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.dst, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 #define SF_LENGTH_SWITCH(L, CALL)                 \
   switch (L) {                                    \
     case 64: { constexpr int LL = 64; CALL; }     \

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 namespace sf {
 
@@ -46,5 +47,20 @@ struct PassBatch {
   PassDesc d[kMaxPassBatch];
   int count;
 };
+
+// Outputs of a row tile leaving by 2D tensor stores (TMA): pass k's output is
+// the float tensor {2 rows, n1} with row pitch dst_ld complex values, written
+// in boxes of (all the tile's rows) x kOutBoxN outputs from a [n][row] tile.
+constexpr int kOutBoxN = 256;
+struct OutMaps {
+  int use[kMaxPassBatch];  // pass k stores through map[k] (else plain stores)
+  CUtensorMap map[kMaxPassBatch];
+};
+
+// Encodes pass d's output tensor map for tiles of box_rows rows.  False (plain
+// stores) when the pass also writes intensity or phase, accumulates, is not in
+// plain device memory, has rows that do not start on 16-byte boundaries, or the
+// driver's encoder is unavailable.
+bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorMap* map);
 
 }  // namespace sf

@@ -208,8 +208,6 @@ __device__ __forceinline__ void gemm(uint32_t d, uint32_t a, uint32_t a_lo, int 
   }
 }
 
-// Output box of the tensor stores: all kRows rows (as float pairs) of 256 outputs.
-constexpr int kBoxN = 256;
 
 struct Args {
   const uint4* consts;  // constant image (Shape::const_bytes)
@@ -514,11 +512,11 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     group_bar(g);
     // ---- transposed store: output n of row r to dst[n * dst_ld + row0 + r]
     if (a.tma_store[p]) {
-      // tensor stores of kBoxN outputs x kRows rows, clipped to the pass's rows and n1; they
+      // tensor stores of kOutBoxN outputs x kRows rows, clipped to the pass's rows and n1; they
       // complete in the background, and the buffer is next written after the wait above
       if (tq == 0) {
-        for (int j = 0; j * kBoxN < n1; ++j)
-          umma::tma_store_2d(&a.out_map[p], op + j * kBoxN * kRows * 8, 2 * row0, j * kBoxN);
+        for (int j = 0; j * kOutBoxN < n1; ++j)
+          umma::tma_store_2d(&a.out_map[p], op + j * kOutBoxN * kRows * 8, 2 * row0, j * kOutBoxN);
         umma::bulk_commit();
       }
     } else {
@@ -672,37 +670,6 @@ cudaError_t launch_hnat(int L, const float2* Hreg, float2* Hn, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-namespace {
-// cuTensorMapEncodeTiled from the driver (null when it cannot be reached: plain stores then)
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }();
-  return fn;
-}
-
-// Tensor map of pass d's complex output as floats {2 rows, n1}, box {2 kRows, kBoxN}, when the
-// pass writes only the complex field (no intensity, phase or accumulation) and its rows start
-// on 16-byte boundaries.
-bool output_tensor_map(PassKind kind, const PassDesc& d, CUtensorMap* map) {
-  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-  if (!encode || !d.dst || d.rows <= 0 || d.n1 <= 0) return false;
-  if (kind == PASS_Y && (d.inten || d.phase || d.accumulate)) return false;
-  if ((reinterpret_cast<uintptr_t>(d.dst) & 15) != 0 || (d.dst_ld & 1) != 0) return false;
-  const cuuint64_t dims[2] = {2 * (cuuint64_t)d.rows, (cuuint64_t)d.n1};
-  const cuuint64_t strides[1] = {(cuuint64_t)d.dst_ld * 8};
-  const cuuint32_t box[2] = {2 * t5::kRows, t5::kBoxN};
-  const cuuint32_t estr[2] = {1, 1};
-  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.dst, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-}  // namespace
 
 cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, const void* consts, int* err, int sms,
                            cudaStream_t s) {
@@ -714,7 +681,7 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
   for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + t5::kRows - 1) / t5::kRows;
   for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
   a.total_tiles = a.tile_off[b.count];
-  for (int k = 0; k < b.count; ++k) a.tma_store[k] = output_tensor_map(kind, b.d[k], &a.out_map[k]) ? 1 : 0;
+  for (int k = 0; k < b.count; ++k) a.tma_store[k] = output_tensor_map(kind, b.d[k], t5::kRows, &a.out_map[k]) ? 1 : 0;
   if (a.total_tiles == 0) return cudaSuccess;
   const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
   const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
