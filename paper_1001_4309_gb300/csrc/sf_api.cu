@@ -92,6 +92,7 @@ struct sf_plan_s {
   int precision = SF_PREC_FP32;
   uint32_t* tc_frags = nullptr;  // per-lane DFT fragments and twiddle tables of the tensor-core pass
   void* t5_consts = nullptr;     // DFT operands and twiddles of the tcgen05 row pass
+  int* t5_sched = nullptr;       // tile counter and per-view x-tile counts of the fused tcgen05 launch
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
   AxisCoef* axes_dev = nullptr;  // coefficient table read by the chirp and spectrum kernels
   int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA
@@ -1212,6 +1213,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   }
   const size_t off_frags = mma_sync_tables ? ar.take(sizeof(uint32_t) * tc_table_words()) : SIZE_MAX;
   const size_t off_t5 = any_t5 ? ar.take(t5_const_bytes(2048, precision)) : SIZE_MAX;
+  const size_t off_sched = any_t5 ? ar.take(sizeof(int) * (1 + kMaxPassBatch)) : SIZE_MAX;
   const size_t off_err = ar.take(sizeof(int));
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
   if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
@@ -1260,6 +1262,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     g_launches += 3;  // fragments and the twiddle tables of both lengths
   }
   std::vector<unsigned char> t5_host;  // kept alive until the stream is synchronised below
+  if (off_sched != SIZE_MAX) p->t5_sched = reinterpret_cast<int*>(base + off_sched);
   if (off_t5 != SIZE_MAX && e == cudaSuccess) {
     p->t5_consts = base + off_t5;
     t5_host.resize(t5_const_bytes(2048, precision));
@@ -1482,6 +1485,62 @@ cudaError_t execute_host_outputs(sf_plan plan, const ExecBuffers& io, bool pipel
 
 // Device outputs on `s` alone: every view's x pass, then every y pass, each
 // grouped by FFT length; profiling events (when attached) bracket the passes.
+// An FP16 or BF16 plan (the x3 precisions, two groups per SM, measure
+// faster with one launch per pass) whose views all run both axes on the
+// tcgen05 pass (FFT length 2048 with the 2N padding on both axes), at most
+// kMaxPassBatch / 2 views.
+bool fused_t5_eligible(sf_plan p) {
+  const int nv = (int)p->views.size();
+  if (p->precision != SF_PREC_FP16TC && p->precision != SF_PREC_BF16TC) return false;
+  if (!p->t5_consts || !p->t5_sched || nv < 1 || nv > kMaxPassBatch / 2) return false;
+  for (const ViewState& vs : p->views)
+    for (int a = 0; a < 2; ++a) {
+      const AxisCoef& c = vs.ax[a];
+      if (!t5_length_supported(c.L) || 2 * c.n0 > c.L || 2 * c.n1 > c.L || !vs.hnat[a]) return false;
+    }
+  return true;
+}
+
+// Device outputs of a plan that fused_t5_eligible accepts: the x and y passes
+// of every view in one persistent tcgen05 launch, each view's y tiles
+// starting as soon as its x tiles are done.
+cudaError_t execute_fused_t5(sf_plan plan, const ExecBuffers& io, cudaStream_t s) {
+  const int nv = (int)plan->views.size();
+  PassBatch b;
+  std::memset(&b, 0, sizeof(b));
+  for (int axis = 0; axis < 2; ++axis)
+    for (int vi = 0; vi < nv; ++vi) {
+      const ViewState& vs = plan->views[vi];
+      const AxisCoef& c = vs.ax[axis];
+      PassDesc& d = b.d[b.count++];
+      d.cin = c.cin;
+      d.cout = c.cout;
+      d.H = vs.hnat[axis];
+      d.n0 = c.n0;
+      d.n1 = c.n1;
+      if (axis == 0) {
+        d.src = io.src;
+        d.dst = io.work[vi];
+        d.rows = vs.v.ny0;
+        d.src_ld = vs.v.nx0;
+        d.dst_ld = vs.v.ny0;
+      } else {
+        d.src = io.work[vi];
+        d.dst = io.dout[vi];
+        d.inten = io.dint[vi];
+        d.phase = io.dph[vi];
+        d.rows = vs.v.nx1;
+        d.src_ld = vs.v.ny0;
+        d.dst_ld = vs.v.nx1;
+      }
+    }
+  const PassKind kx = plan->in_complex ? PASS_X_CPLX : PASS_X_REAL;
+  const cudaError_t e =
+      launch_views_t5(2048, plan->precision, kx, b, nv, plan->t5_consts, plan->dev_err, plan->t5_sched, plan->sms, s);
+  ++g_launches;
+  return e;
+}
+
 cudaError_t execute_single_stream(sf_plan plan, const ExecBuffers& io, cudaStream_t s) {
   auto none = [](const int*, int) { return cudaSuccess; };
   cudaError_t e = cudaSuccess;
@@ -1563,13 +1622,15 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   }
 
   // Schedule: host outputs -> execute_host_outputs (pipelined unless
-  // SF_EXECUTE_SINGLE_STREAM=1); device outputs of two or more views without
-  // profiling events -> execute_split_halves (unless SF_EXECUTE_SINGLE_STREAM=1);
-  // otherwise execute_single_stream.
+  // SF_EXECUTE_SINGLE_STREAM=1); device outputs without profiling events ->
+  // execute_fused_t5 where every axis runs the tcgen05 pass, else
+  // execute_split_halves for two or more views (neither with
+  // SF_EXECUTE_SINGLE_STREAM=1); otherwise execute_single_stream.
   const bool host_out = !io.d2h.empty();
   const bool single = env_is("SF_EXECUTE_SINGLE_STREAM", "1");
   const bool pipeline = host_out && !single;
-  const bool split = !host_out && !plan->prof[0] && nv >= 2 && !single;
+  const bool fused = !host_out && !plan->prof[0] && !single && fused_t5_eligible(plan);
+  const bool split = !fused && !host_out && !plan->prof[0] && nv >= 2 && !single;
   if (host_out || split) {
     int rc = pipeline ? ensure_pipeline_resources(plan)
              : host_out ? ensure_copy_resources(plan)
@@ -1593,6 +1654,7 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   }
   if (e == cudaSuccess) {
     e = host_out ? execute_host_outputs(plan, io, pipeline, split_row, s)
+        : fused  ? execute_fused_t5(plan, io, s)
         : split  ? execute_split_halves(plan, io, s)
                  : execute_single_stream(plan, io, s);
   }

@@ -93,6 +93,12 @@ void t5_build_consts(int L, int prec, void* host);
 cudaError_t launch_hnat(int L, const float2* Hreg, float2* Hn, cudaStream_t s);
 cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, const void* consts, int* err, int sms,
                            cudaStream_t s);
+// Both passes of nx views in one persistent launch: b holds the nx x passes
+// then the nx y passes (same view order); sched is 1 + nx device ints that
+// the launch zeroes first and uses to schedule tiles and order each view's y
+// tiles after its x tiles.
+cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b, int nx, const void* consts, int* err,
+                            int* sched, int sms, cudaStream_t s);
 
 // host helpers shared by the entry points (defined in sf_api.cu)
 int validate_view(const sf_view& v);

@@ -75,6 +75,9 @@ constexpr int kGroupThreads = 32 * kGroupWarps;
 constexpr uint32_t kSuspendNs = 20000;
 constexpr long long kSpin = 50000;
 constexpr unsigned kStaggerNs = 1000;  // start offset between a CTA's groups
+// waits of a fused launch's y tiles for their view's x tiles: kDepSpin polls kDepSleepNs apart (about 1 s)
+constexpr long long kDepSpin = 4000000;
+constexpr unsigned kDepSleepNs = 256;
 
 template <int PREC>
 struct Prec {
@@ -109,8 +112,8 @@ struct Shape {
   static constexpr int group_bytes(bool split) { return (split ? 2 : 1) * OP_BYTES; }
   static constexpr int misc_offset(bool split) { return op_offset(split) + (split ? 2 : 4) * group_bytes(split); }
   // misc: one MMA mbarrier per group (from byte 0), the constant-image mbarrier (32), the
-  // tensor-memory base (48), per-warp row maxima (from byte 64)
-  static constexpr int smem_bytes(bool split) { return misc_offset(split) + 64 + 4 * kGroupWarps * 4; }
+  // tensor-memory base (48), per-warp row maxima (64 .. 191), per-group tile claims (192 .. 207)
+  static constexpr int smem_bytes(bool split) { return misc_offset(split) + 256; }
 };
 
 // Operand layouts, 128-byte swizzle (16-bit elements; every operand starts on
@@ -219,49 +222,105 @@ struct Args {
   CUtensorMap out_map[kMaxPassBatch];
 };
 
-template <int L, int KIND, int PREC>
-__global__ void __launch_bounds__(Prec<PREC>::kThreads, 1)
-k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
-  using S = Shape<L>;
-  constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
-  constexpr int kGroups = Prec<PREC>::kGroups;
-  constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
-  constexpr int KH = KA / 2, NH = NA / 2, CH = kR2 / 2;  // each warp's half of n1 (in, out) and of n2 / k2
-  extern __shared__ __align__(1024) unsigned char sm[];
-  const int g = threadIdx.x / kGroupThreads, tq = threadIdx.x % kGroupThreads;
-  // warp gw of the group: tensor-memory lane quarter wq, column half hh
-  const int gw = tq >> 5, wq = gw & 3, hh = gw >> 2, l = tq & 31;
-  unsigned char* const op = sm + S::op_offset(SPLIT) + g * S::group_bytes(SPLIT);
-  unsigned char* const misc = sm + S::misc_offset(SPLIT);
-  uint64_t* const bars = reinterpret_cast<uint64_t*>(misc);
-  uint64_t* const cbar = reinterpret_cast<uint64_t*>(misc + 32);
-  uint32_t* const tbase = reinterpret_cast<uint32_t*>(misc + 48);
-  float* const rowmax = reinterpret_cast<float*>(misc + 64) + kGroupWarps * g;
-  const float2* const tw = reinterpret_cast<const float2*>(sm + (SPLIT ? 2 : 1) * S::MAT_BYTES);
+// Source loads: read-only path, or through L2 only (COHERENT) for data that
+// other CTAs of the same launch wrote.
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld_src(const T* p) {
+  if constexpr (COHERENT) return __ldcg(p);
+  else return __ldg(p);
+}
 
-  if (tq == 0) umma::mbar_init(bars + g, 1);
-  if (threadIdx.x == 0) umma::mbar_init(cbar, 1);
+// One group's shared-memory regions, tensor-memory columns and wait state.
+template <int L, int PREC>
+struct GroupCtx {
+  int g, tq, gw, wq, hh, l;  // group; thread in group; warp gw = (lane quarter wq, column half hh); lane
+  unsigned char* op;         // operand / staging buffer
+  uint64_t* bars;            // MMA completion mbarriers (one per group)
+  uint64_t* cbar;            // constant-image mbarrier
+  float* rowmax;             // this group's per-warp row maxima
+  const float2* tw;          // twiddle table
+  uint32_t tm, lanes;        // tensor-memory columns of the group, lanes of the warp
+  uint32_t parity;           // phase of bars[g] to wait for next
+  bool consts_ready;         // the constant image has been waited for
+};
+
+// Shared-memory layout, mbarriers, tensor memory, the constant-image copy and
+// the group stagger, at kernel entry.
+template <int L, int PREC>
+__device__ __forceinline__ GroupCtx<L, PREC> group_setup(unsigned char* sm, const uint4* consts) {
+  using S = Shape<L>;
+  constexpr bool SPLIT = Prec<PREC>::kSplit;
+  constexpr int kGroups = Prec<PREC>::kGroups;
+  GroupCtx<L, PREC> c;
+  c.g = threadIdx.x / kGroupThreads;
+  c.tq = threadIdx.x % kGroupThreads;
+  c.gw = c.tq >> 5;
+  c.wq = c.gw & 3;
+  c.hh = c.gw >> 2;
+  c.l = c.tq & 31;
+  c.op = sm + S::op_offset(SPLIT) + c.g * S::group_bytes(SPLIT);
+  unsigned char* const misc = sm + S::misc_offset(SPLIT);
+  c.bars = reinterpret_cast<uint64_t*>(misc);
+  c.cbar = reinterpret_cast<uint64_t*>(misc + 32);
+  uint32_t* const tbase = reinterpret_cast<uint32_t*>(misc + 48);
+  c.rowmax = reinterpret_cast<float*>(misc + 64) + kGroupWarps * c.g;
+  c.tw = reinterpret_cast<const float2*>(sm + (SPLIT ? 2 : 1) * S::MAT_BYTES);
+  if (c.tq == 0) umma::mbar_init(c.bars + c.g, 1);
+  if (threadIdx.x == 0) umma::mbar_init(c.cbar, 1);
   if (threadIdx.x < 32) umma::tmem_alloc(tbase, 128 * kGroups);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   // the constant image arrives by one bulk copy while the first tile's inputs load
   if (threadIdx.x == 0) {
-    umma::mbar_arrive_expect_tx(cbar, S::const_bytes(SPLIT));
-    umma::bulk_g2s(sm, a.consts, S::const_bytes(SPLIT), cbar);
+    umma::mbar_arrive_expect_tx(c.cbar, S::const_bytes(SPLIT));
+    umma::bulk_g2s(sm, consts, S::const_bytes(SPLIT), c.cbar);
   }
-  bool consts_ready = false;
+  c.consts_ready = false;
+  c.parity = 0;
+  c.tm = *tbase + 128u * c.g;
+  c.lanes = (uint32_t)(32 * c.wq) << 16;
   // Groups start kStaggerNs apart: their products then reach the SM's tensor core at
   // different times instead of queueing behind one another, and their loads and stores
   // spread out in time.
-  if (kStaggerNs > 0 && g > 0) __nanosleep(kStaggerNs * g);
+  if (kStaggerNs > 0 && c.g > 0) __nanosleep(kStaggerNs * c.g);
+  return c;
+}
 
-  const uint32_t tm = *tbase + 128u * g;
-  const uint32_t lanes = (uint32_t)(32 * wq) << 16;  // this warp's tensor-memory lanes
+// This group's tensor stores complete, then the CTA frees its tensor memory.
+template <int L, int PREC>
+__device__ __forceinline__ void group_teardown(unsigned char* sm, const GroupCtx<L, PREC>& c) {
+  using S = Shape<L>;
+  if (c.tq == 0) umma::bulk_wait();
+  umma::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32)
+    umma::tmem_dealloc(*reinterpret_cast<uint32_t*>(sm + S::misc_offset(Prec<PREC>::kSplit) + 48),
+                       128 * Prec<PREC>::kGroups);
+}
+
+// One tile: rows row0 .. row0 + kRows - 1 of pass d, steps 2-9 along the
+// pass's axis.  out_map: the pass's output tensor map (tensor stores), else
+// plain stores.  False when an MMA or constant-image wait gave up (err set).
+template <int L, int KIND, int PREC, bool COHERENT>
+__device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned char* sm, const PassDesc& d, int row0,
+                                        const CUtensorMap* out_map, int* err) {
+  using S = Shape<L>;
+  constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
+  constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
+  constexpr int KH = KA / 2, NH = NA / 2, CH = kR2 / 2;  // each warp's half of n1 (in, out) and of n2 / k2
+  const int g = ctx.g, tq = ctx.tq, gw = ctx.gw, wq = ctx.wq, hh = ctx.hh, l = ctx.l;
+  unsigned char* const op = ctx.op;
+  uint64_t* const bars = ctx.bars;
+  uint64_t* const cbar = ctx.cbar;
+  float* const rowmax = ctx.rowmax;
+  const float2* const tw = ctx.tw;
+  const uint32_t tm = ctx.tm, lanes = ctx.lanes;
+  uint32_t& parity = ctx.parity;
+  bool& consts_ready = ctx.consts_ready;
   const uint32_t s_op = umma::smem_u32(op), s_lo = s_op + S::OP_BYTES;
   const uint32_t s_ba = umma::smem_u32(sm), s_bb = s_ba + S::BA_BYTES, s_bh = s_bb + S::BB_BYTES;
   constexpr uint32_t LO = SPLIT ? S::MAT_BYTES : 0;
-  uint32_t parity = 0;
   bool ok = true;
 
   // wait for the group's last commit (one poller), then agree on the outcome
@@ -270,7 +329,7 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     if (tq == 0) {
       w = umma::mbar_wait(bars + g, parity, kSpin, kSuspendNs);
       if (!w) {
-        atomicExch(a.err, 1);
+        atomicExch(err, 1);
         umma::mbar_wait(bars + g, parity, kSpin, kSuspendNs);
       }
     }
@@ -284,271 +343,337 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
     umma::fence_before_sync();
     group_bar(g);
   };
+  const int n0 = d.n0, n1 = d.n1;
 
-  for (int tile = blockIdx.x * kGroups + g; tile < a.total_tiles; tile += gridDim.x * kGroups) {
-    int p = 0;
-    while (tile >= a.tile_off[p + 1]) ++p;
-    const PassDesc& d = b.d[p];
-    const int row0 = (tile - a.tile_off[p]) * kRows;
-    const int n0 = d.n0, n1 = d.n1;
-
-    // ---- input x chirp (steps 2-3), row normalisation, stage-A operand (K-major).
-    // Warp (wq, hh) takes row wq, n1 in [KH hh, KH hh + KH); the row's maximum
-    // is combined with the other half's through shared memory.
-    float inv_scale;
-    {
-      const int row = row0 + wq;
-      const bool valid = row < d.rows;
-      float2 x[KH];
-      float mx = 0.f;
+  // ---- input x chirp (steps 2-3), row normalisation, stage-A operand (K-major).
+  // Warp (wq, hh) takes row wq, n1 in [KH hh, KH hh + KH); the row's maximum
+  // is combined with the other half's through shared memory.
+  float inv_scale;
+  {
+    const int row = row0 + wq;
+    const bool valid = row < d.rows;
+    float2 x[KH];
+    float mx = 0.f;
 #pragma unroll
-      for (int i = 0; i < KH; ++i) {
-        const int n = kR2 * (KH * hh + i) + l;
-        float2 v = make_float2(0.f, 0.f);
-        if (valid && n < n0) {
-          const float2 c = __ldg(d.cin + n);
-          if constexpr (KIND == PASS_X_REAL) {
-            v = cscale(c, __ldg(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + n));
-          } else {
-            v = cmul(__ldg(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + n), c);
-          }
-        }
-        x[i] = v;
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (l == 0) rowmax[gw] = mx;
-      if (tq == 0) umma::bulk_wait_read();  // the previous tile's tensor stores have read the buffer
-      group_bar(g);
-      mx = fmaxf(mx, rowmax[gw ^ 4]);
-      int e = 0;
-      if (mx > 0.f) frexpf(mx, &e);
-      const float s = ldexpf(1.f, -e);  // max * s in [0.5, 1)
-      inv_scale = ldexpf(1.f, e);
-      const int m = 32 * wq + l;
-#pragma unroll
-      for (int c = 0; c < KH / 8; ++c) {
-        float re[8], im[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          re[j] = x[8 * c + j].x * s;
-          im[j] = x[8 * c + j].y * s;
-        }
-        store8<PREC>(op, kmaj_off(m, KH * hh + 8 * c), re);
-        store8<PREC>(op, kmaj_off(m, KA + KH * hh + 8 * c), im);
-      }
-    }
-    if (!consts_ready) {  // first tile: every thread sees the constant image before using it
-      bool w = umma::mbar_wait(cbar, 0, kSpin, kSuspendNs);
-      if (!w && threadIdx.x == 0) {
-        atomicExch(a.err, 1);
-        umma::mbar_wait(cbar, 0, kSpin, kSuspendNs);
-      }
-      consts_ready = true;
-      ok = group_bar_and(g, w);
-      if (!ok) break;
-    }
-    publish();
-    if (tq == 0) {
-      umma::fence_after_sync();
-      gemm<SPLIT, false>(tm, s_op, s_lo, S::A_K, s_ba, s_ba + LO, S::A_N, S::A_K / 16,
-                         umma::idesc_f16(128, S::A_N, BF, false, false));
-      umma::commit(bars + g);
-    }
-    await();
-    if (!ok) break;
-
-    // ---- twiddle W_L^{n2 k1}; stage-B operand rows (r', k1), K = n2 (MN-major).
-    // Lane (r = wq, n2 = l); warp half hh takes k1 in [R1/2 hh, R1/2 hh + R1/2).
-    {
-      const int q = wq >> 1, rp = wq & 1;
-      unsigned char* opq = op + q * 128 * S::B_K * 2;
-#pragma unroll
-      for (int jj = 0; jj < R1 / 32; ++jj) {
-        const int j = (R1 / 32) * hh + jj;
-        float re[16], im[16];
-        umma::tmem_ld16(tm + lanes + 16 * j, re);
-        umma::tmem_ld16(tm + lanes + R1 + 16 * j, im);
-        umma::tmem_wait_ld();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float yr[8], yi[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k1 = 16 * j + 8 * h + i;
-            const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + l]);
-            yr[i] = y.x;
-            yi[i] = y.y;
-          }
-          const int m = R1 * rp + 16 * j + 8 * h;
-          store8<PREC>(opq, mnmaj_off(m, l, S::B_K), yr);
-          store8<PREC>(opq, mnmaj_off(m, kR2 + l, S::B_K), yi);
+    for (int i = 0; i < KH; ++i) {
+      const int n = kR2 * (KH * hh + i) + l;
+      float2 v = make_float2(0.f, 0.f);
+      if (valid && n < n0) {
+        const float2 c = __ldg(d.cin + n);
+        if constexpr (KIND == PASS_X_REAL) {
+          v = cscale(c, ld_src<COHERENT>(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + n));
+        } else {
+          v = cmul(ld_src<COHERENT>(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + n), c);
         }
       }
+      x[i] = v;
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
-    publish();
-    if (tq == 0) {
-      umma::fence_after_sync();
 #pragma unroll
-      for (int q = 0; q < S::QB; ++q)
-        gemm<SPLIT, true>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, S::B_K, s_bb,
-                          s_bb + LO, S::B_N, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, true, false));
-      umma::commit(bars + g);
-    }
-    // the spectrum loads overlap the products: this thread's k1, k2 in [CH hh, CH hh + CH)
-    float2 hsp[CH];
-    {
-      const int k1 = 32 * (wq & 1) + l;
-#pragma unroll
-      for (int i = 0; i < CH; ++i) hsp[i] = __ldg(d.H + k1 + R1 * (CH * hh + i));
-    }
-    await();
-    if (!ok) break;
-
-    // ---- x kernel spectrum (step 7), conjugated: stage-B^H operand rows (r', k1), K = k2 (K-major).
-    // Warp half hh takes k2 in [CH hh, CH hh + CH).
-    {
-      const int m = 32 * wq + l;
-      const int c = hh;
-#pragma unroll
-      for (int q = 0; q < S::QB; ++q) {
-        float re[16], im[16];
-        umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
-        umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
-        umma::tmem_wait_ld();
-        unsigned char* opq = op + q * 128 * S::B_K * 2;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float yr[8], yi[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), hsp[8 * h + i]);
-            yr[i] = y.x;
-            yi[i] = -y.y;
-          }
-          store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h), yr);
-          store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h), yi);
-        }
-      }
-    }
-    publish();
-    if (tq == 0) {
-      umma::fence_after_sync();
-#pragma unroll
-      for (int q = 0; q < S::QB; ++q)
-        gemm<SPLIT, false>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, S::B_K, s_bb,
-                           s_bb + LO, S::B_N, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, false, false));
-      umma::commit(bars + g);
-    }
-    await();
-    if (!ok) break;
-
-    // ---- twiddle W_L^{n2 k1}: stage-A^H operand rows (r, n2), K = k1 (MN-major).
-    // Lane (r', k1); warp half hh takes n2 in [CH hh, CH hh + CH).
-    {
-      const int k1 = 32 * (wq & 1) + l;
-      const int c = hh;
-#pragma unroll
-      for (int q = 0; q < S::QB; ++q) {
-        const int r = 2 * q + (wq >> 1);
-        float re[16], im[16];
-        umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
-        umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
-        umma::tmem_wait_ld();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float yr[8], yi[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int n2 = 16 * c + 8 * h + i;
-            const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + n2]);
-            yr[i] = y.x;
-            yi[i] = y.y;
-          }
-          const int m = kR2 * r + 16 * c + 8 * h;
-          store8<PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
-          store8<PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
-        }
-      }
-    }
-    publish();
-    if (tq == 0) {
-      umma::fence_after_sync();
-      gemm<SPLIT, true>(tm, s_op, s_lo, S::H_K, s_bh, s_bh + LO, S::H_N, S::H_K / 16,
-                        umma::idesc_f16(128, S::H_N, BF, true, false));
-      umma::commit(bars + g);
-    }
-    // the output-chirp loads overlap the product: this thread's n1 in [NH hh, NH hh + NH)
-    float2 co[NH];
-#pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      const int n = kR2 * (NH * hh + i) + l;
-      co[i] = n < n1 ? __ldg(d.cout + n) : make_float2(0.f, 0.f);
-    }
-    await();
-    if (!ok) break;
-
-    // ---- conj, undo the scales, x output chirp (step 9): staged as [n][r] float2 (the tensor-store box)
-    {
-      // the three 1/sqrt(L) stage scales (the output chirp carries the transform's 1/L)
-      const float sc = inv_scale * (float)L * sqrtf((float)L);
-      float2* stage = reinterpret_cast<float2*>(op);
-#pragma unroll
-      for (int c = 0; c < NH / 8; ++c) {
-        float re[8], im[8];
-        umma::tmem_ld8(tm + lanes + NH * hh + 8 * c, re);
-        umma::tmem_ld8(tm + lanes + NA + NH * hh + 8 * c, im);
-        umma::tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int n = kR2 * (NH * hh + 8 * c + i) + l;
-          if (n < n1) stage[n * kRows + wq] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[8 * c + i]);
-        }
-      }
-    }
-    umma::fence_smem_to_async();
-    umma::fence_before_sync();
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (l == 0) rowmax[gw] = mx;
+    if (tq == 0) umma::bulk_wait_read();  // the previous tile's tensor stores have read the buffer
     group_bar(g);
-    // ---- transposed store: output n of row r to dst[n * dst_ld + row0 + r]
-    if (a.tma_store[p]) {
-      // tensor stores of kOutBoxN outputs x kRows rows, clipped to the pass's rows and n1; they
-      // complete in the background, and the buffer is next written after the wait above
-      if (tq == 0) {
-        for (int j = 0; j * kOutBoxN < n1; ++j)
-          umma::tma_store_2d(&a.out_map[p], op + j * kOutBoxN * kRows * 8, 2 * row0, j * kOutBoxN);
-        umma::bulk_commit();
+    mx = fmaxf(mx, rowmax[gw ^ 4]);
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    const float s = ldexpf(1.f, -e);  // max * s in [0.5, 1)
+    inv_scale = ldexpf(1.f, e);
+    const int m = 32 * wq + l;
+#pragma unroll
+    for (int c = 0; c < KH / 8; ++c) {
+      float re[8], im[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        re[j] = x[8 * c + j].x * s;
+        im[j] = x[8 * c + j].y * s;
       }
-    } else {
-      const float2* stage = reinterpret_cast<const float2*>(op);
-      const int rows_here = min(kRows, d.rows - row0);
-      float2* const dst = d.dst;
-      float* const inten = d.inten;
-      float* const phase = d.phase;
-      const size_t ld = (size_t)d.dst_ld;
-      const bool acc = d.accumulate != 0;
-      for (int i = tq; i < n1 * kRows; i += kGroupThreads) {
-        const int n = i >> 2, r = i & 3;
-        if (r < rows_here) {
-          const float2 u = stage[i];
-          const size_t o = (size_t)n * ld + row0 + r;
-          if constexpr (KIND != PASS_Y) {
-            dst[o] = u;
-          } else {
-            if (dst) dst[o] = acc ? cadd(dst[o], u) : u;
-            if (inten) inten[o] = fmaf(u.x, u.x, u.y * u.y);
-            if (phase) phase[o] = phase_of(u);
-          }
-        }
-      }
-      group_bar(g);  // the staging tile is the next tile's operand buffer
+      store8<PREC>(op, kmaj_off(m, KH * hh + 8 * c), re);
+      store8<PREC>(op, kmaj_off(m, KA + KH * hh + 8 * c), im);
     }
   }
+  if (!consts_ready) {  // first tile: every thread sees the constant image before using it
+    bool w = umma::mbar_wait(cbar, 0, kSpin, kSuspendNs);
+    if (!w && threadIdx.x == 0) {
+      atomicExch(err, 1);
+      umma::mbar_wait(cbar, 0, kSpin, kSuspendNs);
+    }
+    consts_ready = true;
+    ok = group_bar_and(g, w);
+    if (!ok) return false;
+  }
+  publish();
+  if (tq == 0) {
+    umma::fence_after_sync();
+    gemm<SPLIT, false>(tm, s_op, s_lo, S::A_K, s_ba, s_ba + LO, S::A_N, S::A_K / 16,
+                       umma::idesc_f16(128, S::A_N, BF, false, false));
+    umma::commit(bars + g);
+  }
+  await();
+  if (!ok) return false;
 
-  if (tq == 0) umma::bulk_wait();  // this group's tensor stores are complete
+  // ---- twiddle W_L^{n2 k1}; stage-B operand rows (r', k1), K = n2 (MN-major).
+  // Lane (r = wq, n2 = l); warp half hh takes k1 in [R1/2 hh, R1/2 hh + R1/2).
+  {
+    const int q = wq >> 1, rp = wq & 1;
+    unsigned char* opq = op + q * 128 * S::B_K * 2;
+#pragma unroll
+    for (int jj = 0; jj < R1 / 32; ++jj) {
+      const int j = (R1 / 32) * hh + jj;
+      float re[16], im[16];
+      umma::tmem_ld16(tm + lanes + 16 * j, re);
+      umma::tmem_ld16(tm + lanes + R1 + 16 * j, im);
+      umma::tmem_wait_ld();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float yr[8], yi[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k1 = 16 * j + 8 * h + i;
+          const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + l]);
+          yr[i] = y.x;
+          yi[i] = y.y;
+        }
+        const int m = R1 * rp + 16 * j + 8 * h;
+        store8<PREC>(opq, mnmaj_off(m, l, S::B_K), yr);
+        store8<PREC>(opq, mnmaj_off(m, kR2 + l, S::B_K), yi);
+      }
+    }
+  }
+  publish();
+  if (tq == 0) {
+    umma::fence_after_sync();
+#pragma unroll
+    for (int q = 0; q < S::QB; ++q)
+      gemm<SPLIT, true>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, S::B_K, s_bb,
+                        s_bb + LO, S::B_N, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, true, false));
+    umma::commit(bars + g);
+  }
+  // the spectrum loads overlap the products: this thread's k1, k2 in [CH hh, CH hh + CH)
+  float2 hsp[CH];
+  {
+    const int k1 = 32 * (wq & 1) + l;
+#pragma unroll
+    for (int i = 0; i < CH; ++i) hsp[i] = __ldg(d.H + k1 + R1 * (CH * hh + i));
+  }
+  await();
+  if (!ok) return false;
+
+  // ---- x kernel spectrum (step 7), conjugated: stage-B^H operand rows (r', k1), K = k2 (K-major).
+  // Warp half hh takes k2 in [CH hh, CH hh + CH).
+  {
+    const int m = 32 * wq + l;
+    const int c = hh;
+#pragma unroll
+    for (int q = 0; q < S::QB; ++q) {
+      float re[16], im[16];
+      umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
+      umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
+      umma::tmem_wait_ld();
+      unsigned char* opq = op + q * 128 * S::B_K * 2;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float yr[8], yi[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), hsp[8 * h + i]);
+          yr[i] = y.x;
+          yi[i] = -y.y;
+        }
+        store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h), yr);
+        store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h), yi);
+      }
+    }
+  }
+  publish();
+  if (tq == 0) {
+    umma::fence_after_sync();
+#pragma unroll
+    for (int q = 0; q < S::QB; ++q)
+      gemm<SPLIT, false>(tm + 64 * q, s_op + q * 128 * S::B_K * 2, s_lo + q * 128 * S::B_K * 2, S::B_K, s_bb,
+                         s_bb + LO, S::B_N, S::B_K / 16, umma::idesc_f16(128, S::B_N, BF, false, false));
+    umma::commit(bars + g);
+  }
+  await();
+  if (!ok) return false;
+
+  // ---- twiddle W_L^{n2 k1}: stage-A^H operand rows (r, n2), K = k1 (MN-major).
+  // Lane (r', k1); warp half hh takes n2 in [CH hh, CH hh + CH).
+  {
+    const int k1 = 32 * (wq & 1) + l;
+    const int c = hh;
+#pragma unroll
+    for (int q = 0; q < S::QB; ++q) {
+      const int r = 2 * q + (wq >> 1);
+      float re[16], im[16];
+      umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
+      umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
+      umma::tmem_wait_ld();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float yr[8], yi[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int n2 = 16 * c + 8 * h + i;
+          const float2 y = cmul(make_float2(re[8 * h + i], im[8 * h + i]), tw[k1 * S::TW_LD + n2]);
+          yr[i] = y.x;
+          yi[i] = y.y;
+        }
+        const int m = kR2 * r + 16 * c + 8 * h;
+        store8<PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
+        store8<PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
+      }
+    }
+  }
+  publish();
+  if (tq == 0) {
+    umma::fence_after_sync();
+    gemm<SPLIT, true>(tm, s_op, s_lo, S::H_K, s_bh, s_bh + LO, S::H_N, S::H_K / 16,
+                      umma::idesc_f16(128, S::H_N, BF, true, false));
+    umma::commit(bars + g);
+  }
+  // the output-chirp loads overlap the product: this thread's n1 in [NH hh, NH hh + NH)
+  float2 co[NH];
+#pragma unroll
+  for (int i = 0; i < NH; ++i) {
+    const int n = kR2 * (NH * hh + i) + l;
+    co[i] = n < n1 ? __ldg(d.cout + n) : make_float2(0.f, 0.f);
+  }
+  await();
+  if (!ok) return false;
+
+  // ---- conj, undo the scales, x output chirp (step 9): staged as [n][r] float2 (the tensor-store box)
+  {
+    // the three 1/sqrt(L) stage scales (the output chirp carries the transform's 1/L)
+    const float sc = inv_scale * (float)L * sqrtf((float)L);
+    float2* stage = reinterpret_cast<float2*>(op);
+#pragma unroll
+    for (int c = 0; c < NH / 8; ++c) {
+      float re[8], im[8];
+      umma::tmem_ld8(tm + lanes + NH * hh + 8 * c, re);
+      umma::tmem_ld8(tm + lanes + NA + NH * hh + 8 * c, im);
+      umma::tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int n = kR2 * (NH * hh + 8 * c + i) + l;
+        if (n < n1) stage[n * kRows + wq] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[8 * c + i]);
+      }
+    }
+  }
+  umma::fence_smem_to_async();
   umma::fence_before_sync();
-  __syncthreads();
-  if (threadIdx.x < 32) umma::tmem_dealloc(*tbase, 128 * kGroups);
+  group_bar(g);
+  // ---- transposed store: output n of row r to dst[n * dst_ld + row0 + r]
+  if (out_map) {
+    // tensor stores of kOutBoxN outputs x kRows rows, clipped to the pass's rows and n1; they
+    // complete in the background, and the buffer is next written after the wait above
+    if (tq == 0) {
+      for (int j = 0; j * kOutBoxN < n1; ++j)
+        umma::tma_store_2d(out_map, op + j * kOutBoxN * kRows * 8, 2 * row0, j * kOutBoxN);
+      umma::bulk_commit();
+    }
+  } else {
+    const float2* stage = reinterpret_cast<const float2*>(op);
+    const int rows_here = min(kRows, d.rows - row0);
+    float2* const dst = d.dst;
+    float* const inten = d.inten;
+    float* const phase = d.phase;
+    const size_t ld = (size_t)d.dst_ld;
+    const bool acc = d.accumulate != 0;
+    for (int i = tq; i < n1 * kRows; i += kGroupThreads) {
+      const int n = i >> 2, r = i & 3;
+      if (r < rows_here) {
+        const float2 u = stage[i];
+        const size_t o = (size_t)n * ld + row0 + r;
+        if constexpr (KIND != PASS_Y) {
+          dst[o] = u;
+        } else {
+          if (dst) dst[o] = acc ? cadd(dst[o], u) : u;
+          if (inten) inten[o] = fmaf(u.x, u.x, u.y * u.y);
+          if (phase) phase[o] = phase_of(u);
+        }
+      }
+    }
+    group_bar(g);  // the staging tile is the next tile's operand buffer
+  }
+  return true;
+}
+
+template <int L, int KIND, int PREC>
+__global__ void __launch_bounds__(Prec<PREC>::kThreads, 1)
+k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
+  constexpr int kGroups = Prec<PREC>::kGroups;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  GroupCtx<L, PREC> c = group_setup<L, PREC>(sm, reinterpret_cast<const uint4*>(a.consts));
+  for (int tile = blockIdx.x * kGroups + c.g; tile < a.total_tiles; tile += gridDim.x * kGroups) {
+    int p = 0;
+    while (tile >= a.tile_off[p + 1]) ++p;
+    if (!tile_t5<L, KIND, PREC, false>(c, sm, b.d[p], (tile - a.tile_off[p]) * kRows,
+                                       a.tma_store[p] ? &a.out_map[p] : nullptr, a.err))
+      break;
+  }
+  group_teardown<L, PREC>(sm, c);
+}
+
+// Both passes of up to kMaxPassBatch / 2 views in one persistent launch.
+// Passes 0 .. nx - 1 are the views' x passes, nx .. 2 nx - 1 their y passes
+// (same view order).  Groups claim tiles in order from a global counter, so
+// every x tile is claimed before any y tile; a y tile of view v waits
+// (bounded) until all x tiles of view v have signalled that their part of the
+// intermediate is written.  x tiles never wait, so the claims cannot
+// deadlock even when not every CTA of the grid is resident.
+struct FuseArgs {
+  int* sched;  // [0]: next tile to claim, [1 + v]: completed x tiles of view v; zero at launch
+  int nx;      // views
+};
+
+// Bounded wait until *ctr >= need (acquire at GPU scope); false (err set) when it gives up.
+__device__ __forceinline__ bool wait_count(const int* ctr, int need, int* err) {
+  for (long long i = 0; i < kDepSpin; ++i) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= need) return true;
+    __nanosleep(kDepSleepNs);
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+template <int L, int KIND_X, int PREC>
+__global__ void __launch_bounds__(Prec<PREC>::kThreads, 1)
+k_views_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a, const FuseArgs f) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  GroupCtx<L, PREC> c = group_setup<L, PREC>(sm, reinterpret_cast<const uint4*>(a.consts));
+  int* const claim = reinterpret_cast<int*>(sm + Shape<L>::misc_offset(Prec<PREC>::kSplit) + 192);
+  for (;;) {
+    if (c.tq == 0) claim[c.g] = atomicAdd(f.sched, 1);
+    group_bar(c.g);  // every thread reads the claim before the tile's next barrier
+    const int tile = claim[c.g];
+    if (tile >= a.total_tiles) break;
+    int p = 0;
+    while (tile >= a.tile_off[p + 1]) ++p;
+    const int row0 = (tile - a.tile_off[p]) * kRows;
+    const CUtensorMap* om = a.tma_store[p] ? &a.out_map[p] : nullptr;
+    if (p < f.nx) {
+      if (!tile_t5<L, KIND_X, PREC, false>(c, sm, b.d[p], row0, om, a.err)) break;
+      // this tile's rows of the intermediate are written: tensor stores complete, then release
+      if (c.tq == 0) {
+        if (om) {
+          umma::bulk_wait();
+          umma::fence_async_to_global();
+        }
+        __threadfence();
+        atomicAdd(f.sched + 1 + p, 1);
+      }
+    } else {
+      const int v = p - f.nx;
+      bool w = true;
+      if (c.tq == 0) w = wait_count(f.sched + 1 + v, a.tile_off[v + 1] - a.tile_off[v], a.err);
+      if (!group_bar_and(c.g, w)) break;
+      if (!tile_t5<L, PASS_Y, PREC, true>(c, sm, b.d[p], row0, om, a.err)) break;
+    }
+  }
+  group_teardown<L, PREC>(sm, c);
 }
 
 // Natural-order kernel spectrum scaled by 1/sqrt(L), from the FP32 network's
@@ -590,6 +715,21 @@ cudaError_t launch_t(PassKind kind, const PassBatch& b, const Args& a, int grid,
     case PASS_X_CPLX: return go(k_pass_t5<L, PASS_X_CPLX, PREC>);
     case PASS_Y: return go(k_pass_t5<L, PASS_Y, PREC>);
   }
+  return cudaErrorInvalidValue;
+}
+
+template <int L, int PREC>
+cudaError_t launch_fused_t(PassKind kind_x, const PassBatch& b, const Args& a, const FuseArgs& f, int grid,
+                           cudaStream_t s) {
+  constexpr int smem = Shape<L>::smem_bytes(Prec<PREC>::kSplit);
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, Prec<PREC>::kThreads, smem, s>>>(b, a, f);
+    return cudaGetLastError();
+  };
+  if (kind_x == PASS_X_REAL) return go(k_views_t5<L, PASS_X_REAL, PREC>);
+  if (kind_x == PASS_X_CPLX) return go(k_views_t5<L, PASS_X_CPLX, PREC>);
   return cudaErrorInvalidValue;
 }
 
@@ -690,6 +830,33 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
     case SF_PREC_BF16TC: return t5::launch_t<2048, SF_PREC_BF16TC>(kind, b, a, grid, s);
     case SF_PREC_FP16X3TC: return t5::launch_t<2048, SF_PREC_FP16X3TC>(kind, b, a, grid, s);
     case SF_PREC_BF16X3TC: return t5::launch_t<2048, SF_PREC_BF16X3TC>(kind, b, a, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b, int nx, const void* consts, int* err,
+                            int* sched, int sms, cudaStream_t s) {
+  if (L != 2048 || nx <= 0 || 2 * nx != b.count || kind_x == PASS_Y) return cudaErrorInvalidValue;
+  t5::Args a{};
+  a.consts = static_cast<const uint4*>(consts);
+  a.err = err;
+  a.tile_off[0] = 0;
+  for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + t5::kRows - 1) / t5::kRows;
+  for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
+  a.total_tiles = a.tile_off[b.count];
+  for (int k = 0; k < b.count; ++k)
+    a.tma_store[k] = output_tensor_map(k < nx ? kind_x : PASS_Y, b.d[k], t5::kRows, &a.out_map[k]) ? 1 : 0;
+  if (a.total_tiles == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(int) * (1 + nx), s);
+  if (e != cudaSuccess) return e;
+  const t5::FuseArgs f{sched, nx};
+  const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
+  const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
+  switch (prec) {
+    case SF_PREC_FP16TC: return t5::launch_fused_t<2048, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s);
+    case SF_PREC_BF16TC: return t5::launch_fused_t<2048, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s);
+    case SF_PREC_FP16X3TC: return t5::launch_fused_t<2048, SF_PREC_FP16X3TC>(kind_x, b, a, f, grid, s);
+    case SF_PREC_BF16X3TC: return t5::launch_fused_t<2048, SF_PREC_BF16X3TC>(kind_x, b, a, f, grid, s);
   }
   return cudaErrorInvalidValue;
 }

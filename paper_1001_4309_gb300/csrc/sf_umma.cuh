@@ -59,6 +59,8 @@ __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // generic-proxy shared-memory writes -> visible to the tensor core's operand reads
 __device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// completed async-proxy (bulk copy) writes to global memory, ordered before later generic accesses
+__device__ __forceinline__ void fence_async_to_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // TMEM allocation by one whole warp; the base address lands in *dst.
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
