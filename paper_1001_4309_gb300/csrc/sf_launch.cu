@@ -43,8 +43,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
-bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorMap* map) {
+bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorMap* map, bool swizzle32) {
   if (!d.dst || d.rows <= 0 || d.n1 <= 0 || box_rows <= 0 || (box_rows & 1) != 0) return false;
+  if (swizzle32 && box_rows != 4) return false;
   if (kind == PASS_Y && (d.inten || d.phase || d.accumulate)) return false;
   if ((reinterpret_cast<uintptr_t>(d.dst) & 15) != 0 || (d.dst_ld & 1) != 0) return false;
   cudaPointerAttributes at;
@@ -60,7 +61,7 @@ bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorM
   const cuuint32_t box[2] = {2 * (cuuint32_t)box_rows, (cuuint32_t)kOutBoxN};
   const cuuint32_t estr[2] = {1, 1};
   return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.dst, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                swizzle32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -57,10 +57,12 @@ struct OutMaps {
   CUtensorMap map[kMaxPassBatch];
 };
 
-// Encodes pass d's output tensor map for tiles of box_rows rows.  False (plain
-// stores) when the pass also writes intensity or phase, accumulates, is not in
-// plain device memory, has rows that do not start on 16-byte boundaries, or the
-// driver's encoder is unavailable.
-bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorMap* map);
+// Encodes pass d's output tensor map for tiles of box_rows rows; swizzle32:
+// the box in shared memory is in the 32-byte swizzle (16-byte chunk index
+// XOR bit 7 of the offset; box_rows = 4).  False (plain stores) when the pass
+// also writes intensity or phase, accumulates, is not in plain device memory,
+// has rows that do not start on 16-byte boundaries, or the driver's encoder is
+// unavailable.
+bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorMap* map, bool swizzle32 = false);
 
 }  // namespace sf

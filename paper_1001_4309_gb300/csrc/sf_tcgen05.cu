@@ -299,6 +299,14 @@ __device__ __forceinline__ void group_teardown(unsigned char* sm, const GroupCtx
                        128 * Prec<PREC>::kGroups);
 }
 
+// Output staging tile: output n of row r (kRows = 4 rows, 32 bytes per n) at
+// float2 index 4 n + r with the tensor map's 32-byte swizzle applied (16-byte
+// chunk r / 2 XOR bit 2 of n), so a warp writing 32 consecutive n of one row
+// spreads over twice as many banks as the plain layout.
+__device__ __forceinline__ int stage_idx(int n, int r) {
+  return kRows * n + ((((r >> 1) ^ (n >> 2)) & 1) << 1) + (r & 1);
+}
+
 // One tile: rows row0 .. row0 + kRows - 1 of pass d, steps 2-9 along the
 // pass's axis.  out_map: the pass's output tensor map (tensor stores), else
 // plain stores.  False when an MMA or constant-image wait gave up (err set).
@@ -556,7 +564,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int n = kR2 * (NH * hh + 8 * c + i) + l;
-        if (n < n1) stage[n * kRows + wq] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[8 * c + i]);
+        if (n < n1) stage[stage_idx(n, wq)] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[8 * c + i]);
       }
     }
   }
@@ -583,7 +591,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
     for (int i = tq; i < n1 * kRows; i += kGroupThreads) {
       const int n = i >> 2, r = i & 3;
       if (r < rows_here) {
-        const float2 u = stage[i];
+        const float2 u = stage[stage_idx(n, r)];
         const size_t o = (size_t)n * ld + row0 + r;
         if constexpr (KIND != PASS_Y) {
           dst[o] = u;
@@ -821,7 +829,8 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
   for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + t5::kRows - 1) / t5::kRows;
   for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
   a.total_tiles = a.tile_off[b.count];
-  for (int k = 0; k < b.count; ++k) a.tma_store[k] = output_tensor_map(kind, b.d[k], t5::kRows, &a.out_map[k]) ? 1 : 0;
+  for (int k = 0; k < b.count; ++k)
+    a.tma_store[k] = output_tensor_map(kind, b.d[k], t5::kRows, &a.out_map[k], true) ? 1 : 0;
   if (a.total_tiles == 0) return cudaSuccess;
   const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
   const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
@@ -845,7 +854,7 @@ cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b
   for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
   a.total_tiles = a.tile_off[b.count];
   for (int k = 0; k < b.count; ++k)
-    a.tma_store[k] = output_tensor_map(k < nx ? kind_x : PASS_Y, b.d[k], t5::kRows, &a.out_map[k]) ? 1 : 0;
+    a.tma_store[k] = output_tensor_map(k < nx ? kind_x : PASS_Y, b.d[k], t5::kRows, &a.out_map[k], true) ? 1 : 0;
   if (a.total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(int) * (1 + nx), s);
   if (e != cudaSuccess) return e;
