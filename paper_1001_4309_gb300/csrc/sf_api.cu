@@ -95,7 +95,7 @@ struct sf_plan_s {
   int* t5_sched = nullptr;       // tile counter and per-view x-tile counts of the fused tcgen05 launch
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
   AxisCoef* axes_dev = nullptr;  // coefficient table read by the chirp and spectrum kernels
-  int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA
+  int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA, 2 / 3 grid with half / twice the rows per CTA
   int sms = 0;
   void* arena = nullptr;
   void* st_holo = nullptr;
@@ -644,8 +644,11 @@ cudaError_t launch_row_pass(sf_plan plan, int axis, int L, PassBatch& b, const i
   } else if (persistent_eligible(plan, L, kind, b)) {
     e = launch_pass_persistent(L, kind, b, plan->tw[L], plan->dev_err, plan->sms, s);
   } else {
-    const int G = pass_rows_per_cta(L);
-    e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s);
+    const int slot = fft_length_slot(L);
+    const int impl = slot >= 0 ? plan->impl[slot][kind] : 0;
+    const int variant = impl >= 2 ? impl - 1 : 0;  // rows per CTA: default, half, double
+    const int G = pass_rows_per_cta(L, variant);
+    e = launch_pass(L, kind, b, (max_rows + G - 1) / G, plan->tw[L], s, variant);
   }
   ++g_launches;
   return e;
@@ -718,9 +721,12 @@ cudaError_t launch_axis(sf_plan plan, int axis, const void* src, float2* const* 
 // FFT length per (view, axis) and row-pass kernel per (length, kind).
 //   default: the smallest supported length (SF_FFT_LENGTHS=pow2 keeps powers
 //            of two only); the persistent kernel at 4096, the one-tile-per-CTA
-//            kernel elsewhere (SF_PASS_IMPL=grid|tma forces one);
+//            kernel with its default rows per CTA elsewhere (SF_PASS_IMPL=
+//            grid|tma forces one; half|double: the one-tile-per-CTA kernel with
+//            half or twice the rows per CTA where that variant exists);
 //   SF_AUTOTUNE=1: per axis the cheaper of the two candidate lengths, per
-//            (length, kind) the cheaper kernel, by measured time per row.
+//            (length, kind) the cheapest of the kernels and rows-per-CTA
+//            variants, by measured time per row.
 // Tensor-core plans keep the power of two where the tensor-core pass takes it.
 struct PlanChoices {
   std::vector<int> L;  // [2 * view + axis]
@@ -739,7 +745,14 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
   const char* impl_env = std::getenv("SF_PASS_IMPL");
   const bool force_grid = impl_env && std::string(impl_env) == "grid";
   const bool force_tma = impl_env && std::string(impl_env) == "tma";
-  auto impl_default = [&](int L) { return force_tma ? 1 : force_grid ? 0 : (L == 4096 ? 1 : 0); };
+  const int force_variant = impl_env && std::string(impl_env) == "half"     ? 1
+                            : impl_env && std::string(impl_env) == "double" ? 2
+                                                                             : 0;
+  auto impl_default = [&](int L) {
+    if (force_variant) return pass_rows_per_cta(L, force_variant) > 0 ? 1 + force_variant : 0;
+    if (!tma_length_supported(L)) return 0;
+    return force_tma ? 1 : force_grid ? 0 : (L == 4096 ? 1 : 0);
+  };
   const bool tune = autotune_mode() == 1;
   auto kind_of = [&](int axis) {
     return axis == 1 ? PASS_Y : (p->in_complex ? PASS_X_CPLX : PASS_X_REAL);
@@ -747,7 +760,7 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
   // best measured cost of (L, kind, prunable) over the kernels, remembering the kernel
   auto best = [&](int L, PassKind kind, bool prune, int* impl) {
     double b = -1;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
       const double ns = row_cost_ns(p->device, L, kind, k, prune, p->sms, s);
       if (ns > 0 && (b < 0 || ns < b)) {
         b = ns;
@@ -778,8 +791,8 @@ PlanChoices plan_choices(sf_plan p, const sf_view* views, int n_views, int preci
   for (int slot = 0; slot < kNumFftLengths; ++slot)
     for (int k = 0; k < 3; ++k) {
       const int L = kFftLengths[slot];
-      c.impl[slot][k] = tma_length_supported(L) ? impl_default(L) : 0;
-      if (!tune || !tma_length_supported(L)) continue;
+      c.impl[slot][k] = impl_default(L);
+      if (!tune) continue;
       bool used = false, all_prunable = true;
       for (int i = 0; i < n_views; ++i)
         for (int a = 0; a < 2; ++a)

@@ -138,12 +138,15 @@ constexpr int kZGradBlocks = 304;
 void count_launches(uint64_t n);
 
 // launchers (one translation unit per FFT length family)
-cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s);
+// variant: the CTA size (0 default, 1 half the rows per CTA, 2 twice; pass_rows_per_cta(L, variant) = 0
+// where a variant does not exist)
+cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s,
+                        int variant = 0);
 cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const float4* tw, cudaStream_t s);
 cudaError_t launch_chirps(const AxisCoef* axes_dev, int n_axes, int max_n, cudaStream_t s);
 size_t twiddle_entries(int L);
 void build_twiddles(int L, float4* host_table);
-int pass_rows_per_cta(int L);
+int pass_rows_per_cta(int L, int variant = 0);
 bool fft_length_supported(int L);
 int fft_length_slot(int L);  // index in kFftLengths, -1 if unsupported
 

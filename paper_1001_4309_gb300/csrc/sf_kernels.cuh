@@ -44,6 +44,18 @@ constexpr int pass_cta_target(int L) {
   return !is_pow2(L) ? 192 : (L == 4096 ? 2 * kPassCtaThreads : kPassCtaThreads);
 }
 
+// Alternative CTA sizes of the one-tile-per-CTA row pass that the autotuner
+// may choose per (L, kind): variant 1 holds half the default rows per CTA,
+// variant 2 twice as many; 0 where a variant does not exist (powers of two
+// from 1024 to 4096 only, at least one row and at most 512 threads, so the
+// 128-register budget holds).
+constexpr int pass_cta_variant(int L, int v) {
+  if (v == 0) return pass_cta_target(L);
+  if (!is_pow2(L) || L < 1024 || L > 4096 || (v != 1 && v != 2)) return 0;
+  const int c = v == 1 ? pass_cta_target(L) / 2 : pass_cta_target(L) * 2;
+  return (c < L / kE || c > 512) ? 0 : c;
+}
+
 // G rows of T = L / E threads per CTA.  Registers: powers of two for 16 warps
 // per SM (128 per thread), the lengths with a factor 3 for 12 (up to 168).
 template <int L, int CTA = pass_cta_target(L)>
@@ -204,15 +216,14 @@ __device__ __forceinline__ void row_tile(const PassDesc& d, int row0, float2* sm
 
 // Row pass: tile blockIdx.x of pass blockIdx.y.  PRUNE: every pass of the
 // launch has n0 <= L / 2 and n1 <= L / 2 (the paper's 2N padding).
-template <int L, int KIND, bool PRUNE>
-__global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
+template <int L, int KIND, bool PRUNE, int CTA = pass_cta_target(L)>
+__global__ void __launch_bounds__(PassShape<L, CTA>::THREADS, PassShape<L, CTA>::MIN_BLOCKS)
 k_pass(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, const __grid_constant__ OutMaps om) {
   extern __shared__ __align__(128) float2 smem[];
   const PassDesc& d = b.d[blockIdx.y];
-  const int row0 = blockIdx.x * PassShape<L>::G;
+  const int row0 = blockIdx.x * PassShape<L, CTA>::G;
   if (row0 >= d.rows) return;  // whole CTA past this pass's rows
-  row_tile<L, KIND, false, false, pass_cta_target(L), PRUNE>(d, row0, smem, tw,
-                                                             om.use[blockIdx.y] ? &om.map[blockIdx.y] : nullptr);
+  row_tile<L, KIND, false, false, CTA, PRUNE>(d, row0, smem, tw, om.use[blockIdx.y] ? &om.map[blockIdx.y] : nullptr);
 }
 
 // The pruned network applies to the radix-16 (power-of-two) lengths.
@@ -249,9 +260,10 @@ __global__ void __launch_bounds__(L / fft_e(L)) k_hspec(const AxisCoef* __restri
   for (int e = 0; e < E; ++e) a.H[e * T + t] = v[e];
 }
 
-template <int L>
-cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s) {
-  using Sh = PassShape<L>;
+// The one-tile-per-CTA row pass with CTA threads (pass_cta_variant(L, v)).
+template <int L, int CTA>
+cudaError_t launch_pass_cta(PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s) {
+  using Sh = PassShape<L, CTA>;
   const dim3 grid(grid_x, b.count), block(Sh::THREADS);
   OutMaps om;
   for (int k = 0; k < kMaxPassBatch; ++k)
@@ -267,19 +279,22 @@ cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const f
   if constexpr (is_pow2(L)) {
     if (pass_prunable<L>(b)) {
       switch (kind) {
-        case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL, true>);
-        case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX, true>);
-        case PASS_Y: return go(k_pass<L, PASS_Y, true>);
+        case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL, true, CTA>);
+        case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX, true, CTA>);
+        case PASS_Y: return go(k_pass<L, PASS_Y, true, CTA>);
       }
     }
   }
   switch (kind) {
-    case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL, false>);
-    case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX, false>);
-    case PASS_Y: return go(k_pass<L, PASS_Y, false>);
+    case PASS_X_REAL: return go(k_pass<L, PASS_X_REAL, false, CTA>);
+    case PASS_X_CPLX: return go(k_pass<L, PASS_X_CPLX, false, CTA>);
+    case PASS_Y: return go(k_pass<L, PASS_Y, false, CTA>);
   }
   return cudaErrorInvalidValue;
 }
+
+template <int L>
+cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s);
 
 template <int L>
 cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float4* tw, cudaStream_t s) {
@@ -292,6 +307,13 @@ cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float4* t
   return cudaGetLastError();
 }
 
+// launch_pass_t<L>: the default CTA size (the variants are instantiated on
+// their own, SF_INSTANTIATE_VARIANT, and reached through launch_pass_variant).
+template <int L>
+cudaError_t launch_pass_t(PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s) {
+  return launch_pass_cta<L, pass_cta_target(L)>(kind, b, grid_x, tw, s);
+}
+
 #define SF_INSTANTIATE_LENGTH(LL)                                                                      \
   template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float4*, cudaStream_t); \
   template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float4*, cudaStream_t);
@@ -299,5 +321,10 @@ cudaError_t launch_hspec_t(const AxisCoef* axes_dev, int n_axes, const float4* t
 #define SF_DECLARE_LENGTH(LL)                                                                                 \
   extern template cudaError_t launch_pass_t<LL>(PassKind, const PassBatch&, int, const float4*, cudaStream_t); \
   extern template cudaError_t launch_hspec_t<LL>(const AxisCoef*, int, const float4*, cudaStream_t);
+
+#define SF_INSTANTIATE_VARIANT(LL, CC) \
+  template cudaError_t launch_pass_cta<LL, CC>(PassKind, const PassBatch&, int, const float4*, cudaStream_t);
+#define SF_DECLARE_VARIANT(LL, CC) \
+  extern template cudaError_t launch_pass_cta<LL, CC>(PassKind, const PassBatch&, int, const float4*, cudaStream_t);
 
 }  // namespace sf

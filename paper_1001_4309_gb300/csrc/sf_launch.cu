@@ -19,6 +19,11 @@ SF_DECLARE_LENGTH(2304)
 SF_DECLARE_LENGTH(3072)
 SF_DECLARE_LENGTH(4608)
 SF_DECLARE_LENGTH(6144)
+SF_DECLARE_VARIANT(1024, 128)
+SF_DECLARE_VARIANT(1024, 512)
+SF_DECLARE_VARIANT(2048, 128)
+SF_DECLARE_VARIANT(2048, 512)
+SF_DECLARE_VARIANT(4096, 256)
 
 int fft_length_slot(int L) {
   for (int i = 0; i < kNumFftLengths; ++i)
@@ -83,7 +88,18 @@ bool output_tensor_map(PassKind kind, const PassDesc& d, int box_rows, CUtensorM
     default: break;                               \
   }
 
-cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s) {
+cudaError_t launch_pass(int L, PassKind kind, const PassBatch& b, int grid_x, const float4* tw, cudaStream_t s,
+                        int variant) {
+  if (variant != 0) {
+    switch (L * 4 + variant) {
+      case 1024 * 4 + 1: return launch_pass_cta<1024, pass_cta_variant(1024, 1)>(kind, b, grid_x, tw, s);
+      case 1024 * 4 + 2: return launch_pass_cta<1024, pass_cta_variant(1024, 2)>(kind, b, grid_x, tw, s);
+      case 2048 * 4 + 1: return launch_pass_cta<2048, pass_cta_variant(2048, 1)>(kind, b, grid_x, tw, s);
+      case 2048 * 4 + 2: return launch_pass_cta<2048, pass_cta_variant(2048, 2)>(kind, b, grid_x, tw, s);
+      case 4096 * 4 + 1: return launch_pass_cta<4096, pass_cta_variant(4096, 1)>(kind, b, grid_x, tw, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   SF_LENGTH_SWITCH(L, return launch_pass_t<LL>(kind, b, grid_x, tw, s))
   return cudaErrorInvalidValue;
 }
@@ -93,8 +109,18 @@ cudaError_t launch_hspec(int L, const AxisCoef* axes_dev, int n_axes, const floa
   return cudaErrorInvalidValue;
 }
 
-int pass_rows_per_cta(int L) {
-  SF_LENGTH_SWITCH(L, return PassShape<LL>::G)
+namespace {
+template <int L>
+int variant_rows(int variant) {
+  constexpr int c1 = pass_cta_variant(L, 1), c2 = pass_cta_variant(L, 2);
+  if (variant == 1) return c1 ? PassShape<L, c1 ? c1 : pass_cta_target(L)>::G : 0;
+  if (variant == 2) return c2 ? PassShape<L, c2 ? c2 : pass_cta_target(L)>::G : 0;
+  return PassShape<L>::G;
+}
+}  // namespace
+
+int pass_rows_per_cta(int L, int variant) {
+  SF_LENGTH_SWITCH(L, return variant_rows<LL>(variant))
   return 0;
 }
 

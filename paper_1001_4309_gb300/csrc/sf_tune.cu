@@ -2,8 +2,10 @@
 //
 // The cost of a row pass is (rows) x (time per row), and the time per row
 // depends only on the FFT length L, the pass kind (real x, complex x, y), the
-// kernel (one tile per CTA, or the persistent kernel with bulk-copy prefetch)
-// and whether the pass is prunable (n0, n1 <= L / 2: the radix-16 network
+// kernel and whether the pass is prunable.  Kernels (`impl`): 0 one tile per
+// CTA with the default rows per CTA, 1 the persistent kernel with bulk-copy
+// prefetch, 2 and 3 one tile per CTA with half and twice the default rows per
+// CTA (pass_cta_variant; lengths 1024 to 4096) (n0, n1 <= L / 2: the radix-16 network
 // skips the dead half of its first and last stage).  The tuner measures that
 // time per row once per device and process for each (L, kind, kernel,
 // prunable) a plan asks about: one pass over a synthetic batch of rows (zero
@@ -78,7 +80,8 @@ void append_cache_file(const Key& k, double ns) {
 
 // Time per row (ns) of one synthetic pass; < 0 if it could not be measured.
 double measure(int L, PassKind kind, int impl, bool prune, int sms, cudaStream_t s) {
-  const int G = pass_rows_per_cta(L);
+  const int variant = impl >= 2 ? impl - 1 : 0;
+  const int G = pass_rows_per_cta(L, variant);
   if (G < 1) return -1;
   // not prunable: n0 just above L / 2, keeping rows a multiple of 16 bytes
   // (the persistent kernel's bulk copies need that)
@@ -124,7 +127,7 @@ double measure(int L, PassKind kind, int impl, bool prune, int sms, cudaStream_t
     int* err = reinterpret_cast<int*>(mem + o_err);
     auto launch = [&]() {
       return impl == 1 ? launch_pass_persistent(L, kind, b, tw, err, sms, s)
-                       : launch_pass(L, kind, b, rows / G, tw, s);
+                       : launch_pass(L, kind, b, rows / G, tw, s, variant);
     };
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch();
     std::vector<float> ms;
@@ -161,6 +164,7 @@ int autotune_mode() {
 
 double row_cost_ns(int device, int L, PassKind kind, int impl, bool prune, int sms, cudaStream_t s) {
   if (impl == 1 && !tma_length_supported(L)) return -1;
+  if (impl >= 2 && pass_rows_per_cta(L, impl - 1) < 1) return -1;
   std::lock_guard<std::mutex> lock(g_mu);
   read_cache_file();
   const Key k(device_key(device), L, (int)kind, impl, prune ? 1 : 0);

@@ -299,15 +299,17 @@ def test_plain_cufft_comparison_path_matches_oracle(P):
 
 @pytest.mark.parametrize("n0,n1", [(1024, 1024), (2048, 2048), (1500, 1200)])
 def test_row_pass_kernels_agree(P, n0, n1, monkeypatch):
-    """The one-tile-per-CTA and the persistent (bulk-copy prefetch) row passes give identical views."""
+    """The one-tile-per-CTA row pass (default, half and twice the rows per CTA, where those exist) and
+    the persistent (bulk-copy prefetch) row pass give identical views."""
     ny0, ny1 = 24, 20
     v = view(WAVELENGTH, 0.045, PITCH, 1.9e-6, o1=(1e-4, 2e-5), n0=(n0, ny0), n1=(n1, ny1))
     holo = random_field(ny0, n0, seed=n0 + 11).real
     res = {}
-    for impl in ("grid", "tma"):
+    for impl in ("grid", "tma", "half", "double"):
         monkeypatch.setenv("SF_PASS_IMPL", impl)
         res[impl] = run(P, [v], holo, intensity=False, phase=False)["field"][0]
-    assert np.array_equal(res["grid"], res["tma"])
+    for impl in ("tma", "half", "double"):
+        assert np.array_equal(res["grid"], res[impl]), impl
     check_view({"field": [res["tma"]], "intensity": [None], "phase": [None]}, 0, oracle.forward(holo, v))
 
 

@@ -128,3 +128,24 @@ def test_fused_launch_eight_views_and_repeat(P):
         err = rel_l2(first[i], oracle.forward(holo, views[i]))
         print(f"view {i}: rel-L2 {err:.3e}")
         assert err <= 2e-3
+
+
+@pytest.mark.parametrize("impl", ["half", "double"])
+def test_rows_per_cta_variants_paper_scale(P, c2, impl, monkeypatch):
+    """The FP32 row pass with half (one row, plain stores) and twice (four rows, tensor stores) the
+    default rows per CTA on the paper-scale step: the same bits as the default plan."""
+    h, views, _ = c2
+    handle = plan(P, views, 0)
+    try:
+        ref, _, _ = execute(P, handle, views, h)
+    finally:
+        P.shifted_fresnel_destroy(handle)
+    monkeypatch.setenv("SF_PASS_IMPL", impl)
+    handle = plan(P, views, 0)
+    try:
+        got, _, _ = execute(P, handle, views, h)
+    finally:
+        P.shifted_fresnel_destroy(handle)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
