@@ -63,11 +63,12 @@ __device__ __forceinline__ void decode(const PersistArgs& pa, int tile, int& k, 
 
 template <int L, int KIND, bool PRUNE>
 __global__ void __launch_bounds__(PassShape<L>::THREADS, PassShape<L>::MIN_BLOCKS)
-k_pass_tma(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, const __grid_constant__ PersistArgs pa) {
+k_pass_tma(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, const __grid_constant__ PersistArgs pa,
+           const __grid_constant__ OutMaps om) {
   using Sh = PassShape<L>;
   constexpr int G = Sh::G;
   constexpr unsigned ELEM = KIND == PASS_X_REAL ? 4u : 8u;
-  extern __shared__ __align__(16) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char sm[];
   float2* exch = reinterpret_cast<float2*>(sm);
   float2* cin_s = reinterpret_cast<float2*>(sm + pa.off_cin);
   float2* cout_s = reinterpret_cast<float2*>(sm + pa.off_cout);
@@ -121,7 +122,9 @@ k_pass_tma(const __grid_constant__ PassBatch b, const float4* __restrict__ tw, c
       atomicExch(pa.err, 1);
     }
     const StagedSrc<KIND> src{cin_s, h_s, cout_s, rows + (size_t)((i & 1) * G) * pa.row_bytes, pa.row_bytes};
-    row_tile_src<L, KIND, StagedSrc<KIND>, false, pass_cta_target(L), PRUNE>(d, row0, exch, tw, src);
+    // output tiles by tensor stores where the pass allows (thread 0 waits for their shared-memory reads)
+    row_tile_src<L, KIND, StagedSrc<KIND>, false, pass_cta_target(L), PRUNE>(d, row0, exch, tw, src,
+                                                                           om.use[k] ? &om.map[k] : nullptr);
     __syncthreads();  // stage (i & 1) is free for the copy issued in the next iteration
   }
   if (failed) {
@@ -140,7 +143,13 @@ cudaError_t launch_tma_t(const PassBatch& b, const float4* tw, const PersistArgs
   auto kern = pass_prunable<L>(b) ? k_pass_tma<L, KIND, true> : k_pass_tma<L, KIND, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, PassShape<L>::THREADS, smem, s>>>(b, tw, pa);
+  OutMaps om;
+  for (int k = 0; k < kMaxPassBatch; ++k)
+    om.use[k] = k < b.count && PassShape<L>::G % 2 == 0 &&
+                        output_tensor_map((PassKind)KIND, b.d[k], PassShape<L>::G, &om.map[k])
+                    ? 1
+                    : 0;
+  kern<<<grid, PassShape<L>::THREADS, smem, s>>>(b, tw, pa, om);
   return cudaGetLastError();
 }
 
