@@ -62,7 +62,8 @@ extern "C" {
  * lengths are at most 1024 (the paper's 2N padding, e.g. 1024 -> 1024) runs
  * the four-step pass on tcgen05 (2048 = 64 x 32: two DFT matrix products
  * each way, operands in shared memory, FP32 accumulators in tensor memory,
- * one CTA per SM); other axes of length 2048 or 4096 run radix-16/8 stages on
+ * one CTA per SM; on FP16TC / BF16TC plans whose axes all take it, execute
+ * runs both passes of up to eight views in one launch); other axes of length 2048 or 4096 run radix-16/8 stages on
  * mma.sync (FP16TC and BF16TC only).  Every other axis, the adjoint and the
  * persistent batch kernel run in FP32.  The x3 precisions apply to the
  * tcgen05 axes only and run every other axis in FP32.  Chirps, twiddles,
@@ -156,20 +157,26 @@ int shifted_fresnel_plan_update(sf_plan plan, const sf_view* views, int n_views,
  * x pass starting on the first half (FP32 plans).  The caller's stream waits
  * for the last copy, so the caller synchronises its stream before reading
  * host outputs.  Every view needs at least one non-NULL output.
- * With device outputs and two or more views, the views are split into two
- * halves of about equal work run on `stream` and on a plan-owned second
- * stream (x pass then y pass each), so one half's y pass overlaps the other's
- * x pass; `stream` waits for both before the call's work is complete.
- * SF_EXECUTE_SINGLE_STREAM=1 keeps every pass on `stream` (with host
- * outputs: both passes of each view in turn, copies still on the copy
- * stream); so do profiling events set with shifted_fresnel_set_profile_events
- * when every output is device memory.
- * Implementation: each pass runs a one-tile-per-CTA kernel, or, where the
- * plan chose it (by default at FFT length 4096; SF_PASS_IMPL or the
- * autotuner, see shifted_fresnel_fft_length) and the rows' address, stride
- * and length are multiples of 16 bytes (FFT length 256 .. 4096), a
- * persistent kernel that prefetches the next rows with bulk copies while
- * transforming the current ones.
+ * With device outputs on an FP16TC or BF16TC plan of at most eight views
+ * whose axes all run the tcgen05 pass, both passes of every view run as one
+ * launch on `stream` (each view's y pass starting once its x pass is done).
+ * Otherwise, with device outputs and two or more views, the views are split
+ * into two halves of about equal work run on `stream` and on a plan-owned
+ * second stream (x pass then y pass each), so one half's y pass overlaps the
+ * other's x pass; `stream` waits for both before the call's work is
+ * complete.  SF_EXECUTE_SINGLE_STREAM=1 keeps one launch per pass on
+ * `stream` (with host outputs: both passes of each view in turn, copies
+ * still on the copy stream); so do profiling events set with
+ * shifted_fresnel_set_profile_events when every output is device memory.
+ * Implementation (FP32 passes): a one-tile-per-CTA kernel (with the plan's
+ * rows per CTA), or, where the plan chose it (by default at FFT length 4096;
+ * SF_PASS_IMPL or the autotuner, see shifted_fresnel_fft_length) and the
+ * rows' address, stride and length are multiples of 16 bytes (FFT length
+ * 256 .. 4096), a persistent kernel that prefetches the next rows with bulk
+ * copies while transforming the current ones.  Complex outputs in plain
+ * device memory with 16-byte aligned rows leave through tensor stores;
+ * intensity, phase, managed or host-mapped outputs through plain stores
+ * (the same values either way).
  * Errors: SF_ERR_INVALID_ARG, SF_ERR_DEVICE_MISMATCH, SF_ERR_OOM, SF_ERR_CUDA.
  */
 int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_out,
@@ -399,15 +406,21 @@ uint64_t shifted_fresnel_kernel_launches(void);
  *   SF_FFT_LENGTHS=pow2   powers of two only.
  *   SF_PASS_IMPL=grid|tma one-tile-per-CTA row-pass kernel everywhere, or the
  *                         persistent one for every eligible pass (default:
- *                         persistent at 4096 only).
+ *                         persistent at 4096 only); =half|double the
+ *                         one-tile-per-CTA kernel with half or twice its
+ *                         default rows per CTA where that variant exists
+ *                         (FFT lengths 1024 .. 4096).
  *   SF_AUTOTUNE=1         measure instead: per axis the cheaper of the two
  *                         candidate lengths (next power of two, next length
  *                         with a factor 3), per (length, pass kind) the
- *                         cheaper row-pass kernel, by the time per row of a
- *                         synthetic pass timed once per device and process.
+ *                         cheapest row-pass kernel and rows per CTA, by the
+ *                         time per row of a synthetic pass timed once per
+ *                         device and process.
  *   SF_AUTOTUNE_CACHE=path  file the measurements are read from and appended
  *                         to (one "device L kind kernel prunable ns_per_row"
- *                         line each; prunable: n0, n1 <= L/2, where the
+ *                         line each; kernel: 0 one tile per CTA, 1
+ *                         persistent, 2 / 3 one tile per CTA with half / twice
+ *                         the rows per CTA; prunable: n0, n1 <= L/2, where the
  *                         power-of-two network skips the dead half of its
  *                         first and last stage).
  * All choices compute the same convolution; results differ by rounding only.

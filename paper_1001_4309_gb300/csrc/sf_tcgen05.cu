@@ -15,7 +15,7 @@
 //
 // Every product is the real GEMM D (128 x N) = A (128 x K) B (K x N) of the
 // block form [Re | Im] [[Fr, Fi], [-Fi, Fr]] of a unitary-scaled DFT matrix
-// F; a CTA holds kGroups independent groups of four warps, and a group
+// F; a CTA holds kGroups independent groups of eight warps, and a group
 // transforms a tile of kRows = 4 rows at a time:
 //
 //   stage A   rows (r, n2), K = (re, im) of n1 < R1/2, N = (re, im) of k1
@@ -28,30 +28,38 @@
 //   twiddle   W_L^{n2 k1} again (the conjugations cancel), to the stage-A^H
 //             operand (MN-major)
 //   stage A^H rows (r, n2), K = k1, N = n1 < R1/2
-//   output    conj, undo the scales, x output chirp, transposed store
+//   output    conj, undo the scales, x output chirp, staged [n][row] and
+//             sent out by 2D tensor stores (TMA), or by a store loop
 //
-// Thread (warp w of the group, lane l) reads tensor-memory lane 32 w + l, so
-// it always holds complete complex values; every operand store is a 16-byte
-// chunk of 8 consecutive K (K-major) or M (MN-major) elements.  Rows are
+// Warps w and w + 4 of a group read tensor-memory lanes 32 (w mod 4) + l, each
+// taking half of every epilogue's columns, so a thread always holds complete
+// complex values; every operand store is a 16-byte chunk of 8 consecutive K
+// (K-major) or M (MN-major) elements.  Rows are
 // normalised by a power of two from their largest input component before the
 // first conversion (exact), which keeps FP16 in range.  The x3 precisions
 // split each operand into hi + lo parts and accumulate hi*hi + hi*lo + lo*hi.
 //
-// The kernel is persistent (one CTA per SM, tiles round-robin over the
-// groups): four groups for FP16 / BF16 (all 512 tensor-memory columns, 128
-// per group), two for the x3 precisions, whose doubled operand buffers leave
-// room for no more.  The spectrum and output-chirp loads are issued before
-// the waits for the products they follow.  Each MMA completion is awaited
-// through an mbarrier with a bounded wait; on expiry the group sets the
-// plan's device error word, waits once more (bounded), leaves its tile loop
-// and the CTA frees its tensor memory.
+// The kernels are persistent (one CTA per SM): four groups for FP16 / BF16
+// (1024 threads, all 512 tensor-memory columns, 128 per group), two for the
+// x3 precisions, whose doubled operand buffers leave room for no more.  The
+// constant image (DFT matrices, twiddles) arrives by one bulk copy that
+// overlaps the first tile's loads; groups start 1 us apart so that their
+// products do not reach the tensor core together; the spectrum and
+// output-chirp loads are issued before the waits for the products they
+// follow.  k_pass_t5 runs one pass (tiles round-robin over the groups);
+// k_views_t5 runs both passes of up to eight views, tiles claimed in order
+// from a global counter, each view's y tiles after its x tiles.  Every wait
+// (MMA completion, constant image, a y tile's dependency) is bounded; on
+// expiry the group sets the plan's device error word, waits once more
+// (bounded) where a copy may be in flight, leaves its tile loop and the CTA
+// frees its tensor memory.
 //
 // Measured on the paper-scale step (four 1024^2 views, L = 2048 both axes):
-// FP16 and BF16 89.7 us, FP16x3 157 us against 91.8 us for the FP32 pass.
-// Per tile the products take about 1.5 of ~30 thousand cycles: the pass is
-// bound by the latency of its FP32 epilogues and global loads and stores at
-// 16 warps per SM, not by the tensor cores (swizzled and unswizzled operand
-// layouts time the same).
+// FP16 and BF16 72.4 us fused (81.5 us with one launch per pass), FP16x3
+// 106-109 us, against 76.2 us for the FP32 pass.  The tensor pipe is ~10 %
+// busy: the pass is bound by the latency of a tile's chain (loads, four
+// product round trips, FP32 epilogues, output staging; 14-17 us per tile)
+// at 16 rows in flight per SM, the number that tensor memory allows.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
