@@ -589,8 +589,9 @@ def time_precision(views, holo, prec, dev, stream, flush, steps, warmup):
 
 def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm_peak, fp32_value):
     """The 4-view step with the DFT stages on tensor cores, plus single 256^2 / 1024^2 / 2048^2 views
-    (the 256^2 view's FFT length 512 has no tensor-core pass and runs in FP32); per-view error vs the
-    FP64 oracle next to the FP32 path."""
+    (the mixed-precision set) and a 512^2 view (FFT length 1024: the 32 x 32 tcgen05 split; the 256^2
+    view's FFT length 512 has no tensor-core pass and runs in FP32); per-view error vs the FP64 oracle
+    next to the FP32 path."""
     import torch
     import synth
     import paper_1001_4309_gb300 as P
@@ -607,7 +608,11 @@ def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm
                      "step_hbm_frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                      "rel_l2_vs_oracle_max": max(e["rel_l2"] for e in errs), "per_view": errs}
     singles = []
-    for h_np, vs in synth.config_c4():
+    h512 = synth.gabor_hologram(512, seed=3 * 1000 + 3, kind="bars_disks")
+    v512 = synth.view(synth.WAVELENGTH, -0.05, synth.PITCH, 2.325e-6, o1=(100e-6, -50e-6), n0=(512, 512),
+                      n1=(512, 512))
+    sets = synth.config_c4()
+    for h_np, vs in sets[:1] + [(h512, [v512])] + sets[1:]:
         h = torch.from_numpy(h_np).to(dev)
         entry = {"view": f"{vs[0]['nx0']}^2 -> {vs[0]['nx1']}^2"}
         for name, prec in precs:
@@ -627,7 +632,7 @@ def row_pass_kind(v, prec):
         L *= 2
     if prec == 0:
         return "fp32"
-    if L == 2048 and 2 * v["nx0"] <= L and 2 * v["nx1"] <= L:
+    if L in (1024, 2048) and 2 * v["nx0"] <= L and 2 * v["nx1"] <= L:
         return "tcgen05"
     if L in (2048, 4096) and prec in (1, 2):
         return "mma.sync"

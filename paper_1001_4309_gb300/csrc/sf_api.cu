@@ -91,7 +91,7 @@ struct sf_plan_s {
   std::map<int, float4*> tw;  // per-stage twiddle tables per FFT length
   int precision = SF_PREC_FP32;
   uint32_t* tc_frags = nullptr;  // per-lane DFT fragments and twiddle tables of the tensor-core pass
-  void* t5_consts = nullptr;     // DFT operands and twiddles of the tcgen05 row pass
+  void* t5_consts[2] = {nullptr, nullptr};  // DFT operands and twiddles of the tcgen05 row pass, FFT length 1024 / 2048
   int* t5_sched = nullptr;       // tile counter and per-view x-tile counts of the fused tcgen05 launch
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
   AxisCoef* axes_dev = nullptr;  // coefficient table read by the chirp and spectrum kernels
@@ -125,6 +125,15 @@ struct sf_plan_s {
   cudaStream_t split_stream = nullptr;
   cudaEvent_t split_fork = nullptr, split_join = nullptr;
 };
+
+namespace sf {
+namespace {
+// the tcgen05 constants of FFT length L, or null (no tcgen05 pass at L in this plan)
+void* t5_consts_for(const sf_plan_s* p, int L) {
+  return L == 1024 ? p->t5_consts[0] : L == 2048 ? p->t5_consts[1] : nullptr;
+}
+}  // namespace
+}  // namespace sf
 
 namespace sf {
 
@@ -632,11 +641,12 @@ cudaError_t launch_row_pass(sf_plan plan, int axis, int L, PassBatch& b, const i
                             cudaStream_t s) {
   const PassKind kind = axis == 1 ? PASS_Y : (plan->in_complex ? PASS_X_CPLX : PASS_X_REAL);
   cudaError_t e;
-  bool t5 = plan->t5_consts && t5_length_supported(L);
+  void* const t5c = t5_consts_for(plan, L);
+  bool t5 = t5c != nullptr;
   for (int k = 0; k < b.count && t5; ++k) t5 = 2 * b.d[k].n0 <= L && 2 * b.d[k].n1 <= L;
   if (t5) {
     for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[view_of[k]].hnat[axis];
-    e = launch_pass_t5(L, plan->precision, kind, b, plan->t5_consts, plan->dev_err, plan->sms, s);
+    e = launch_pass_t5(L, plan->precision, kind, b, t5c, plan->dev_err, plan->sms, s);
   } else if (plan->tc_frags && tc_length_supported(L)) {
     for (int k = 0; k < b.count; ++k) b.d[k].H = plan->views[view_of[k]].hpos[axis];
     const int G = tc_rows_per_cta(L);
@@ -1197,7 +1207,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   std::vector<size_t> off_cin(4 * n_views), off_cout(4 * n_views), off_H(4 * n_views), off_work(n_views);
   std::vector<size_t> off_hpos(2 * n_views, SIZE_MAX), off_hnat(2 * n_views, SIZE_MAX);
   const bool mma_sync_tables = precision == SF_PREC_FP16TC || precision == SF_PREC_BF16TC;
-  bool any_t5 = false;
+  bool any_t5 = false, t5_len[2] = {false, false};
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.v = views[i];
@@ -1221,11 +1231,13 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       if (precision != SF_PREC_FP32 && t5_length_supported(vs.ax[a].L)) {
         off_hnat[2 * i + a] = ar.take(sizeof(float2) * vs.ax[a].L);
         any_t5 = true;
+        t5_len[vs.ax[a].L == 2048 ? 1 : 0] = true;
       }
     }
   }
   const size_t off_frags = mma_sync_tables ? ar.take(sizeof(uint32_t) * tc_table_words()) : SIZE_MAX;
-  const size_t off_t5 = any_t5 ? ar.take(t5_const_bytes(2048, precision)) : SIZE_MAX;
+  size_t off_t5[2];
+  for (int k = 0; k < 2; ++k) off_t5[k] = t5_len[k] ? ar.take(t5_const_bytes(1024 << k, precision)) : SIZE_MAX;
   const size_t off_sched = any_t5 ? ar.take(sizeof(int) * (1 + kMaxPassBatch)) : SIZE_MAX;
   const size_t off_err = ar.take(sizeof(int));
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
@@ -1274,14 +1286,15 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     e = launch_tc_tables(p->tc_frags, precision, s);
     g_launches += 3;  // fragments and the twiddle tables of both lengths
   }
-  std::vector<unsigned char> t5_host;  // kept alive until the stream is synchronised below
   if (off_sched != SIZE_MAX) p->t5_sched = reinterpret_cast<int*>(base + off_sched);
-  if (off_t5 != SIZE_MAX && e == cudaSuccess) {
-    p->t5_consts = base + off_t5;
-    t5_host.resize(t5_const_bytes(2048, precision));
-    t5_build_consts(2048, precision, t5_host.data());
-    e = cudaMemcpyAsync(p->t5_consts, t5_host.data(), t5_host.size(), cudaMemcpyHostToDevice, s);
-  }
+  std::vector<unsigned char> t5_host[2];  // kept alive until the stream is synchronised below
+  for (int k = 0; k < 2; ++k)
+    if (off_t5[k] != SIZE_MAX && e == cudaSuccess) {
+      p->t5_consts[k] = base + off_t5[k];
+      t5_host[k].resize(t5_const_bytes(1024 << k, precision));
+      t5_build_consts(1024 << k, precision, t5_host[k].data());
+      e = cudaMemcpyAsync(p->t5_consts[k], t5_host[k].data(), t5_host[k].size(), cudaMemcpyHostToDevice, s);
+    }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1505,11 +1518,13 @@ cudaError_t execute_host_outputs(sf_plan plan, const ExecBuffers& io, bool pipel
 bool fused_t5_eligible(sf_plan p) {
   const int nv = (int)p->views.size();
   if (p->precision != SF_PREC_FP16TC && p->precision != SF_PREC_BF16TC) return false;
-  if (!p->t5_consts || !p->t5_sched || nv < 1 || nv > kMaxPassBatch / 2) return false;
+  if (!p->t5_sched || nv < 1 || nv > kMaxPassBatch / 2) return false;
+  const int L = p->views[0].ax[0].L;  // one FFT length on every axis of every view
+  if (!t5_consts_for(p, L)) return false;
   for (const ViewState& vs : p->views)
     for (int a = 0; a < 2; ++a) {
       const AxisCoef& c = vs.ax[a];
-      if (!t5_length_supported(c.L) || 2 * c.n0 > c.L || 2 * c.n1 > c.L || !vs.hnat[a]) return false;
+      if (c.L != L || 2 * c.n0 > c.L || 2 * c.n1 > c.L || !vs.hnat[a]) return false;
     }
   return true;
 }
@@ -1519,6 +1534,7 @@ bool fused_t5_eligible(sf_plan p) {
 // starting as soon as its x tiles are done.
 cudaError_t execute_fused_t5(sf_plan plan, const ExecBuffers& io, cudaStream_t s) {
   const int nv = (int)plan->views.size();
+  const int L = plan->views[0].ax[0].L;
   PassBatch b;
   std::memset(&b, 0, sizeof(b));
   for (int axis = 0; axis < 2; ++axis)
@@ -1549,7 +1565,7 @@ cudaError_t execute_fused_t5(sf_plan plan, const ExecBuffers& io, cudaStream_t s
     }
   const PassKind kx = plan->in_complex ? PASS_X_CPLX : PASS_X_REAL;
   const cudaError_t e =
-      launch_views_t5(2048, plan->precision, kx, b, nv, plan->t5_consts, plan->dev_err, plan->t5_sched, plan->sms, s);
+      launch_views_t5(L, plan->precision, kx, b, nv, t5_consts_for(plan, L), plan->dev_err, plan->t5_sched, plan->sms, s);
   ++g_launches;
   return e;
 }
@@ -1642,7 +1658,9 @@ int shifted_fresnel_execute(sf_plan plan, const void* holo, void* const* view_ou
   const bool host_out = !io.d2h.empty();
   const bool single = env_is("SF_EXECUTE_SINGLE_STREAM", "1");
   const bool pipeline = host_out && !single;
-  const bool fused = !host_out && !plan->prof[0] && !single && fused_t5_eligible(plan);
+  // SF_T5_FUSED=0 / =1: one launch per pass / the fused launch wherever eligible
+  const bool fused = !host_out && !plan->prof[0] && !single && fused_t5_eligible(plan) &&
+                     !env_is("SF_T5_FUSED", "0");
   const bool split = !fused && !host_out && !plan->prof[0] && nv >= 2 && !single;
   if (host_out || split) {
     int rc = pipeline ? ensure_pipeline_resources(plan)

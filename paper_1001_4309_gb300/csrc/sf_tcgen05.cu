@@ -100,20 +100,28 @@ struct Shape {
   static constexpr int R1 = L / kR2;
   static constexpr int KA = R1 / 2;  // nonzero n1 on input
   static constexpr int NA = R1 / 2;  // kept n1 on output
-  static_assert(R1 == 64, "the first tcgen05 row pass is built for L = 2048");
+  static_assert(R1 == 32 || R1 == 64, "tcgen05 row pass lengths: 1024 (32 x 32) and 2048 (64 x 32)");
   // real GEMM shapes (M = 128 throughout)
   static constexpr int A_K = 2 * KA, A_N = 2 * R1;    // stage A
   static constexpr int B_K = 2 * kR2, B_N = 2 * kR2;  // stages B and B^H
   static constexpr int H_K = 2 * R1, H_N = 2 * NA;    // stage A^H
   static constexpr int QB = kRows * R1 / 128;         // products per middle stage
+  static constexpr int RP = 128 / R1;                 // rows of a middle-stage product
+  // a K-major operand row holds 64 K elements (128 bytes) per column, whatever K it uses
+  static constexpr int kmaj_bytes(int rows, int k) { return rows * 128 * ((k + 63) / 64); }
   // constant image: the three DFT matrices (K-major B operands), hi then lo, then the twiddles
-  static constexpr int BA_BYTES = A_N * A_K * 2, BB_BYTES = B_N * B_K * 2, BH_BYTES = H_N * H_K * 2;
+  static constexpr int BA_BYTES = kmaj_bytes(A_N, A_K), BB_BYTES = kmaj_bytes(B_N, B_K),
+                       BH_BYTES = kmaj_bytes(H_N, H_K);
+  static_assert(H_K <= 64 || H_N == 64, "a second K column starts 8 KiB (64 rows) in");
+  static_assert(A_K <= 64 && B_K <= 64, "single-column K-major operands");
   static constexpr int MAT_BYTES = BA_BYTES + BB_BYTES + BH_BYTES;
   static constexpr int TW_LD = kR2 + 1;  // padded row of the twiddle table T[k1][n2] (float2)
   static constexpr int TW_BYTES = R1 * TW_LD * 8;
   // per-group operand buffer: the largest stage operand, also the output staging tile
   static constexpr int OP_BYTES = 128 * H_K * 2;
-  static_assert(QB * 128 * B_K * 2 <= OP_BYTES && kRows * (L / 2) * 8 <= OP_BYTES, "operand buffer");
+  static_assert(QB * 128 * B_K * 2 <= OP_BYTES && kRows * (L / 2) * 8 <= OP_BYTES &&
+                    kmaj_bytes(128, A_K) <= OP_BYTES && kmaj_bytes(128, B_K) * QB <= OP_BYTES,
+                "operand buffer");
   static constexpr int align(int b) { return (b + 1023) & ~1023; }
   static constexpr int const_bytes(bool split) { return (split ? 2 : 1) * MAT_BYTES + TW_BYTES; }
   static constexpr int op_offset(bool split) { return align(const_bytes(split)); }
@@ -161,7 +169,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, float& ra, float& rb
 
 // Store 8 values as one 16-byte chunk (hi) and, for the split precisions, the
 // chunk of their rounding remainders (lo) at the same offset of the lo buffer.
-template <int PREC>
+template <int L, int PREC>
 __device__ __forceinline__ void store8(unsigned char* hi, int off, const float (&v)[8]) {
   constexpr bool BF = Prec<PREC>::kBf16;
   float r[8];
@@ -178,7 +186,7 @@ __device__ __forceinline__ void store8(unsigned char* hi, int off, const float (
     lo.y = pack2<BF>(r[2], r[3], t[2], t[3]);
     lo.z = pack2<BF>(r[4], r[5], t[4], t[5]);
     lo.w = pack2<BF>(r[6], r[7], t[6], t[7]);
-    *reinterpret_cast<uint4*>(hi + Shape<2048>::OP_BYTES + off) = lo;
+    *reinterpret_cast<uint4*>(hi + Shape<L>::OP_BYTES + off) = lo;
   }
 }
 
@@ -404,8 +412,8 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
         re[j] = x[8 * c + j].x * s;
         im[j] = x[8 * c + j].y * s;
       }
-      store8<PREC>(op, kmaj_off(m, KH * hh + 8 * c), re);
-      store8<PREC>(op, kmaj_off(m, KA + KH * hh + 8 * c), im);
+      store8<L, PREC>(op, kmaj_off(m, KH * hh + 8 * c), re);
+      store8<L, PREC>(op, kmaj_off(m, KA + KH * hh + 8 * c), im);
     }
   }
   if (!consts_ready) {  // first tile: every thread sees the constant image before using it
@@ -431,7 +439,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   // ---- twiddle W_L^{n2 k1}; stage-B operand rows (r', k1), K = n2 (MN-major).
   // Lane (r = wq, n2 = l); warp half hh takes k1 in [R1/2 hh, R1/2 hh + R1/2).
   {
-    const int q = wq >> 1, rp = wq & 1;
+    const int q = wq / S::RP, rp = wq % S::RP;  // this warp's row r = wq: product q, row rp in it
     unsigned char* opq = op + q * 128 * S::B_K * 2;
 #pragma unroll
     for (int jj = 0; jj < R1 / 32; ++jj) {
@@ -451,8 +459,8 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
           yi[i] = y.y;
         }
         const int m = R1 * rp + 16 * j + 8 * h;
-        store8<PREC>(opq, mnmaj_off(m, l, S::B_K), yr);
-        store8<PREC>(opq, mnmaj_off(m, kR2 + l, S::B_K), yi);
+        store8<L, PREC>(opq, mnmaj_off(m, l, S::B_K), yr);
+        store8<L, PREC>(opq, mnmaj_off(m, kR2 + l, S::B_K), yi);
       }
     }
   }
@@ -468,7 +476,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   // the spectrum loads overlap the products: this thread's k1, k2 in [CH hh, CH hh + CH)
   float2 hsp[CH];
   {
-    const int k1 = 32 * (wq & 1) + l;
+    const int k1 = (32 * wq + l) % R1;  // lane (rp, k1) of a middle-stage product
 #pragma unroll
     for (int i = 0; i < CH; ++i) hsp[i] = __ldg(d.H + k1 + R1 * (CH * hh + i));
   }
@@ -496,8 +504,8 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
           yr[i] = y.x;
           yi[i] = -y.y;
         }
-        store8<PREC>(opq, kmaj_off(m, 16 * c + 8 * h), yr);
-        store8<PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h), yi);
+        store8<L, PREC>(opq, kmaj_off(m, 16 * c + 8 * h), yr);
+        store8<L, PREC>(opq, kmaj_off(m, kR2 + 16 * c + 8 * h), yi);
       }
     }
   }
@@ -516,11 +524,11 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   // ---- twiddle W_L^{n2 k1}: stage-A^H operand rows (r, n2), K = k1 (MN-major).
   // Lane (r', k1); warp half hh takes n2 in [CH hh, CH hh + CH).
   {
-    const int k1 = 32 * (wq & 1) + l;
+    const int k1 = (32 * wq + l) % R1;  // lane (rp, k1) of product q: row r = RP q + rp
     const int c = hh;
 #pragma unroll
     for (int q = 0; q < S::QB; ++q) {
-      const int r = 2 * q + (wq >> 1);
+      const int r = S::RP * q + (32 * wq + l) / R1;
       float re[16], im[16];
       umma::tmem_ld16(tm + lanes + 64 * q + 16 * c, re);
       umma::tmem_ld16(tm + lanes + 64 * q + kR2 + 16 * c, im);
@@ -536,8 +544,8 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
           yi[i] = y.y;
         }
         const int m = kR2 * r + 16 * c + 8 * h;
-        store8<PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
-        store8<PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
+        store8<L, PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
+        store8<L, PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
       }
     }
   }
@@ -788,24 +796,18 @@ void dft_operand(int R, int kin, int nout, bool bf16, uint16_t* hi, uint16_t* lo
 
 }  // namespace t5
 
-bool t5_length_supported(int L) { return L == 2048; }
+bool t5_length_supported(int L) { return L == 1024 || L == 2048; }
 bool t5_precision(int prec) {
   return prec == SF_PREC_FP16TC || prec == SF_PREC_BF16TC || prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
 }
 
-size_t t5_const_bytes(int L, int prec) {
-  (void)L;
-  const bool split = prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
-  return (size_t)t5::Shape<2048>::const_bytes(split);
-}
-
-void t5_build_consts(int L, int prec, void* host) {
-  using S = t5::Shape<2048>;
-  (void)L;
+namespace {
+template <int L>
+void build_consts_t(int prec, unsigned char* base) {
+  using S = t5::Shape<L>;
   const bool split = prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
   const bool bf16 = prec == SF_PREC_BF16TC || prec == SF_PREC_BF16X3TC;
-  unsigned char* base = static_cast<unsigned char*>(host);
-  std::memset(base, 0, t5_const_bytes(L, prec));
+  std::memset(base, 0, S::const_bytes(split));
   uint16_t* hi = reinterpret_cast<uint16_t*>(base);
   uint16_t* lo = split ? reinterpret_cast<uint16_t*>(base + S::MAT_BYTES) : nullptr;
   const int o1 = S::BA_BYTES / 2, o2 = (S::BA_BYTES + S::BB_BYTES) / 2;
@@ -815,21 +817,34 @@ void t5_build_consts(int L, int prec, void* host) {
   float2* tw = reinterpret_cast<float2*>(base + (split ? 2 : 1) * S::MAT_BYTES);
   for (int k1 = 0; k1 < S::R1; ++k1)
     for (int n2 = 0; n2 < t5::kR2; ++n2) {
-      const double ang = -2.0 * M_PI * (double)(k1 * n2) / 2048.0;
+      const double ang = -2.0 * M_PI * (double)(k1 * n2) / (double)L;
       tw[k1 * S::TW_LD + n2] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
 }
+}  // namespace
+
+size_t t5_const_bytes(int L, int prec) {
+  const bool split = prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
+  if (L == 1024) return (size_t)t5::Shape<1024>::const_bytes(split);
+  if (L == 2048) return (size_t)t5::Shape<2048>::const_bytes(split);
+  return 0;
+}
+
+void t5_build_consts(int L, int prec, void* host) {
+  if (L == 1024) build_consts_t<1024>(prec, static_cast<unsigned char*>(host));
+  if (L == 2048) build_consts_t<2048>(prec, static_cast<unsigned char*>(host));
+}
 
 cudaError_t launch_hnat(int L, const float2* Hreg, float2* Hn, cudaStream_t s) {
-  if (L != 2048) return cudaErrorInvalidValue;
-  t5::k_hnat<2048><<<1, 2048 / kE, 0, s>>>(Hreg, Hn);
+  if (L == 1024) t5::k_hnat<1024><<<1, 1024 / kE, 0, s>>>(Hreg, Hn);
+  else if (L == 2048) t5::k_hnat<2048><<<1, 2048 / kE, 0, s>>>(Hreg, Hn);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-
 cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, const void* consts, int* err, int sms,
                            cudaStream_t s) {
-  if (L != 2048) return cudaErrorInvalidValue;
+  if (!t5_length_supported(L)) return cudaErrorInvalidValue;
   t5::Args a{};
   a.consts = static_cast<const uint4*>(consts);
   a.err = err;
@@ -842,18 +857,22 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
   if (a.total_tiles == 0) return cudaSuccess;
   const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
   const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
-  switch (prec) {
-    case SF_PREC_FP16TC: return t5::launch_t<2048, SF_PREC_FP16TC>(kind, b, a, grid, s);
-    case SF_PREC_BF16TC: return t5::launch_t<2048, SF_PREC_BF16TC>(kind, b, a, grid, s);
-    case SF_PREC_FP16X3TC: return t5::launch_t<2048, SF_PREC_FP16X3TC>(kind, b, a, grid, s);
-    case SF_PREC_BF16X3TC: return t5::launch_t<2048, SF_PREC_BF16X3TC>(kind, b, a, grid, s);
+#define SF_T5_PREC_CASES(LL)                                                                  \
+  switch (prec) {                                                                              \
+    case SF_PREC_FP16TC: return t5::launch_t<LL, SF_PREC_FP16TC>(kind, b, a, grid, s);         \
+    case SF_PREC_BF16TC: return t5::launch_t<LL, SF_PREC_BF16TC>(kind, b, a, grid, s);         \
+    case SF_PREC_FP16X3TC: return t5::launch_t<LL, SF_PREC_FP16X3TC>(kind, b, a, grid, s);     \
+    case SF_PREC_BF16X3TC: return t5::launch_t<LL, SF_PREC_BF16X3TC>(kind, b, a, grid, s);     \
   }
+  if (L == 1024) SF_T5_PREC_CASES(1024)
+  if (L == 2048) SF_T5_PREC_CASES(2048)
+#undef SF_T5_PREC_CASES
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b, int nx, const void* consts, int* err,
                             int* sched, int sms, cudaStream_t s) {
-  if (L != 2048 || nx <= 0 || 2 * nx != b.count || kind_x == PASS_Y) return cudaErrorInvalidValue;
+  if (!t5_length_supported(L) || nx <= 0 || 2 * nx != b.count || kind_x == PASS_Y) return cudaErrorInvalidValue;
   t5::Args a{};
   a.consts = static_cast<const uint4*>(consts);
   a.err = err;
@@ -869,11 +888,14 @@ cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b
   const t5::FuseArgs f{sched, nx};
   const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
   const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
+  // FP16 / BF16 only (the x3 precisions run one launch per pass)
   switch (prec) {
-    case SF_PREC_FP16TC: return t5::launch_fused_t<2048, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s);
-    case SF_PREC_BF16TC: return t5::launch_fused_t<2048, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s);
-    case SF_PREC_FP16X3TC: return t5::launch_fused_t<2048, SF_PREC_FP16X3TC>(kind_x, b, a, f, grid, s);
-    case SF_PREC_BF16X3TC: return t5::launch_fused_t<2048, SF_PREC_BF16X3TC>(kind_x, b, a, f, grid, s);
+    case SF_PREC_FP16TC:
+      return L == 1024 ? t5::launch_fused_t<1024, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s)
+                       : t5::launch_fused_t<2048, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s);
+    case SF_PREC_BF16TC:
+      return L == 1024 ? t5::launch_fused_t<1024, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s)
+                       : t5::launch_fused_t<2048, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -90,11 +90,15 @@ def test_fused_launch_matches_per_pass_launches(P, c2, precision):
     h, views, _ = c2
     handle = plan(P, views, precision)
     try:
+        n0 = P.shifted_fresnel_kernel_launches()
         fused, _, _ = execute(P, handle, views, h)
+        assert P.shifted_fresnel_kernel_launches() - n0 == 1  # both passes of the four views in one launch
         _, fused_int, _ = execute(P, handle, views, h, intensity=True, complex_out=False)
         os.environ["SF_EXECUTE_SINGLE_STREAM"] = "1"
         try:
+            n0 = P.shifted_fresnel_kernel_launches()
             single, _, _ = execute(P, handle, views, h)
+            assert P.shifted_fresnel_kernel_launches() - n0 == 2  # one launch per pass
             _, single_int, _ = execute(P, handle, views, h, intensity=True, complex_out=False)
         finally:
             del os.environ["SF_EXECUTE_SINGLE_STREAM"]
@@ -118,7 +122,9 @@ def test_fused_launch_eight_views_and_repeat(P):
     h = torch.from_numpy(holo.astype(np.float32)).cuda()
     handle = plan(P, views, 1)
     try:
+        n0 = P.shifted_fresnel_kernel_launches()
         first, _, _ = execute(P, handle, views, h)
+        assert P.shifted_fresnel_kernel_launches() - n0 == 1
         again, _, _ = execute(P, handle, views, h)
     finally:
         P.shifted_fresnel_destroy(handle)

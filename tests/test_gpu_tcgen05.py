@@ -1,7 +1,8 @@
 """The tcgen05 row pass (four-step DFT products on the tensor cores) against the FP64 oracle.
 
-Axes of FFT length 2048 with input and output lengths of at most 1024 (the
-paper's 1024 -> 1024 views with 2N padding) run on this pass in every
+Axes of FFT length 2048 (64 x 32) with input and output lengths of at most
+1024 (the paper's 1024 -> 1024 views with 2N padding), and of FFT length
+1024 (32 x 32) with lengths of at most 512, run on this pass in every
 reduced precision.  Bars, per view, relative L2 against the oracle's complex
 field over every pixel:
 
@@ -129,3 +130,21 @@ def test_fp16x3_agrees_with_fp32_path(P):
     for a, b, r in zip(got, got32, ref):
         assert rel_l2(a, b) <= 1e-5
         assert rel_l2(b, r) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [FP16, FP16X3, BF16X3, BF16], ids=lambda p: NAMES[p])
+def test_length_1024_views_every_pixel(P, prec):
+    """FFT length 1024 on both axes (the 32 x 32 split): a 512 x 510 hologram (a partial last tile on
+    the x pass) into four views of 512^2, 500 x 511, 257 x 300 and 512 x 64 (partial y tiles),
+    every pixel against the oracle; FP16 / BF16 run them as one fused launch."""
+    holo = synth.gabor_hologram(512, seed=5120)[:510]
+    views = [view(WAVELENGTH, z, PITCH, p1, o1=o1, n0=(512, 510), n1=n1)
+             for z, p1, o1, n1 in ((0.03, 1.0e-6, (1e-4, -5e-5), (512, 512)),
+                                   (-0.05, 2.3e-6, (-2e-4, 1e-4), (500, 511)),
+                                   (0.08, 0.8e-6, (3e-5, 0.0), (257, 300)),
+                                   (0.12, 4.65e-6, (0.0, 2e-4), (512, 64)))]
+    got, _ = run(P, views, holo, prec)
+    errs = [rel_l2(g, oracle.forward(holo, v)) for g, v in zip(got, views)]
+    print(f"{NAMES[prec]} L=1024: per-view rel-L2 " + ", ".join(f"{e:.3e}" for e in errs))
+    check(prec, errs)
+
