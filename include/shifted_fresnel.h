@@ -58,13 +58,14 @@ extern "C" {
 #define SF_PREC_BF16TC 2   /* same with BF16 operands */
 #define SF_PREC_FP16X3TC 3 /* FP16 operands split into hi + lo parts, three products per stage */
 #define SF_PREC_BF16X3TC 4 /* BF16 operands split into hi + lo parts, three products per stage */
-/* Tensor-core precisions.  An axis of FFT length 2048 whose input and output
- * lengths are at most 1024 (the paper's 2N padding, e.g. 1024 -> 1024) runs
- * the four-step pass on tcgen05 (2048 = 64 x 32: two DFT matrix products
- * each way, operands in shared memory, FP32 accumulators in tensor memory,
- * one CTA per SM; on FP16TC / BF16TC plans whose axes all take it, execute
- * runs both passes of up to eight views in one launch); other axes of length 2048 or 4096 run radix-16/8 stages on
- * mma.sync (FP16TC and BF16TC only).  Every other axis, the adjoint and the
+/* Tensor-core precisions.  An axis of FFT length 2048 or 1024 whose input and
+ * output lengths are at most half of it (the paper's 2N padding, e.g.
+ * 1024 -> 1024 or 512 -> 512) runs the four-step pass on tcgen05 (2048 =
+ * 64 x 32, 1024 = 32 x 32: two DFT matrix products each way, operands in
+ * shared memory, FP32 accumulators in tensor memory, one CTA per SM; on
+ * FP16TC / BF16TC plans whose axes all share one such length, execute runs
+ * both passes of up to eight views in one launch); other axes of length 2048
+ * or 4096 run radix-16/8 stages on mma.sync (FP16TC and BF16TC only).  Every other axis, the adjoint and the
  * persistent batch kernel run in FP32.  The x3 precisions apply to the
  * tcgen05 axes only and run every other axis in FP32.  Chirps, twiddles,
  * kernel spectrum and accumulation stay FP32 (phases exact) in every
