@@ -1,9 +1,9 @@
 """Mixed-precision (tensor-core) row passes against the FP64 oracle.
 
-Axes of FFT length 2048 with input and output lengths of at most 1024 run
-the four-step tcgen05 pass; other axes of length 2048 or 4096 run the
-mma.sync radix-16/8 stages (FP16TC / BF16TC only); every other axis runs in
-FP32.  Bars, relative L2 per view against the oracle over every pixel:
+Axes of FFT length 2048 (1024) with input and output lengths of at most 1024
+(512) run the four-step tcgen05 pass; other axes of length 2048 or 4096 run
+the mma.sync radix-16/8 stages (FP16TC / BF16TC only); every other axis runs
+in FP32.  Bars, relative L2 per view against the oracle over every pixel:
 
 * FP16TC and BF16X3TC: 2e-3, the reduced-precision tolerance.
 * FP16X3TC: 1e-5 (on the tcgen05 axes; its other axes run in FP32).
