@@ -95,7 +95,8 @@ struct sf_plan_s {
   int* t5_sched = nullptr;       // tile counter and per-view x-tile counts of the fused tcgen05 launch
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
   AxisCoef* axes_dev = nullptr;  // coefficient table read by the chirp and spectrum kernels
-  int impl[kNumFftLengths][3] = {};  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA, 2 / 3 grid with half / twice the rows per CTA
+  // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA, 2 / 3 grid with half / twice the rows per CTA
+  int impl[kNumFftLengths][3] = {};
   int sms = 0;
   void* arena = nullptr;
   void* st_holo = nullptr;
@@ -1565,7 +1566,8 @@ cudaError_t execute_fused_t5(sf_plan plan, const ExecBuffers& io, cudaStream_t s
     }
   const PassKind kx = plan->in_complex ? PASS_X_CPLX : PASS_X_REAL;
   const cudaError_t e =
-      launch_views_t5(L, plan->precision, kx, b, nv, t5_consts_for(plan, L), plan->dev_err, plan->t5_sched, plan->sms, s);
+      launch_views_t5(L, plan->precision, kx, b, nv, t5_consts_for(plan, L), plan->dev_err, plan->t5_sched,
+                      plan->sms, s);
   ++g_launches;
   return e;
 }

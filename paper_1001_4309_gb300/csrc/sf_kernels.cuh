@@ -174,7 +174,8 @@ __device__ __forceinline__ void row_tile_src(const PassDesc& d, int row0, float2
       umma::fence_smem_to_async();  // the tile's shared-memory writes, to the tensor stores
       __syncthreads();
       if (threadIdx.x == 0) {
-        for (int j = 0; j * kOutBoxN < n1; ++j) umma::tma_store_2d(out_map, smem + j * kOutBoxN * G, 2 * row0, j * kOutBoxN);
+        for (int j = 0; j * kOutBoxN < n1; ++j)
+          umma::tma_store_2d(out_map, smem + j * kOutBoxN * G, 2 * row0, j * kOutBoxN);
         umma::bulk_commit();
         umma::bulk_wait_read();
       }
