@@ -78,6 +78,9 @@ constexpr int kR2 = 32;        // inner radix: the lanes of a warp
 constexpr int kRows = 4;       // rows per tile (one warp per row in the first stage)
 constexpr int kGroupWarps = 8;  // warps per group: two per tensor-memory lane quarter
 constexpr int kGroupThreads = 32 * kGroupWarps;
+// lane 0 of a group's last warp issues the group's tensor stores, waits for them and (fused launch)
+// releases finished x tiles, so that thread 0 (products, claims, dependency waits) never waits on them
+constexpr int kStoreTq = kGroupThreads - 32;
 // MMA completion waits: tries of at most kSuspendNs each (the waiting thread
 // sleeps in hardware instead of spinning), kSpin tries (about 1 s) in all
 constexpr uint32_t kSuspendNs = 20000;
@@ -307,7 +310,7 @@ __device__ __forceinline__ GroupCtx<L, PREC> group_setup(unsigned char* sm, cons
 template <int L, int PREC>
 __device__ __forceinline__ void group_teardown(unsigned char* sm, const GroupCtx<L, PREC>& c) {
   using S = Shape<L>;
-  if (c.tq == 0) umma::bulk_wait();
+  if (c.tq == kStoreTq) umma::bulk_wait();
   umma::fence_before_sync();
   __syncthreads();
   if (threadIdx.x < 32)
@@ -323,12 +326,24 @@ __device__ __forceinline__ int stage_idx(int n, int r) {
   return kRows * n + ((((r >> 1) ^ (n >> 2)) & 1) << 1) + (r & 1);
 }
 
+// Release of a finished x tile of a fused launch (the group's store thread):
+// its tensor stores complete, then the view's count goes up.
+__device__ __forceinline__ void signal_tile(int* ctr) {
+  umma::bulk_wait();
+  umma::fence_async_to_global();
+  __threadfence();
+  atomicAdd(ctr, 1);
+}
+
 // One tile: rows row0 .. row0 + kRows - 1 of pass d, steps 2-9 along the
 // pass's axis.  out_map: the pass's output tensor map (tensor stores), else
-// plain stores.  False when an MMA or constant-image wait gave up (err set).
+// plain stores.  signal (fused launch, x passes): the counter on which the
+// store thread releases the group's previous x tile, once this tile's input
+// loads are in flight.  False when an MMA or constant-image wait gave up (err
+// set).
 template <int L, int KIND, int PREC, bool COHERENT>
 __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned char* sm, const PassDesc& d, int row0,
-                                        const CUtensorMap* out_map, int* err) {
+                                        const CUtensorMap* out_map, int* err, int* signal = nullptr) {
   using S = Shape<L>;
   constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
   constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
@@ -378,25 +393,41 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
     const bool valid = row < d.rows;
     float2 x[KH];
     float mx = 0.f;
+    if constexpr (KIND == PASS_X_REAL) {
+      // loads first; the store thread releases the previous x tile while they are in flight
+      float u[KH];
 #pragma unroll
-    for (int i = 0; i < KH; ++i) {
-      const int n = kR2 * (KH * hh + i) + l;
-      float2 v = make_float2(0.f, 0.f);
-      if (valid && n < n0) {
-        const float2 c = __ldg(d.cin + n);
-        if constexpr (KIND == PASS_X_REAL) {
-          v = cscale(c, ld_src<COHERENT>(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + n));
-        } else {
+      for (int i = 0; i < KH; ++i) {
+        const int n = kR2 * (KH * hh + i) + l;
+        const bool in = valid && n < n0;
+        x[i] = in ? __ldg(d.cin + n) : make_float2(0.f, 0.f);
+        u[i] = in ? ld_src<COHERENT>(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + n) : 0.f;
+      }
+      if (signal && tq == kStoreTq) signal_tile(signal);
+#pragma unroll
+      for (int i = 0; i < KH; ++i) {
+        x[i] = cscale(x[i], u[i]);
+        mx = fmaxf(mx, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < KH; ++i) {
+        const int n = kR2 * (KH * hh + i) + l;
+        float2 v = make_float2(0.f, 0.f);
+        if (valid && n < n0) {
+          const float2 c = __ldg(d.cin + n);
           v = cmul(ld_src<COHERENT>(static_cast<const float2*>(d.src) + (size_t)row * d.src_ld + n), c);
         }
+        x[i] = v;
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
       }
-      x[i] = v;
-      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      if (signal && tq == kStoreTq) signal_tile(signal);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (l == 0) rowmax[gw] = mx;
-    if (tq == 0) umma::bulk_wait_read();  // the previous tile's tensor stores have read the buffer
+    // the previous tile's tensor stores have read the buffer (a release above waited for all of them)
+    if (tq == kStoreTq && !signal) umma::bulk_wait_read();
     group_bar(g);
     mx = fmaxf(mx, rowmax[gw ^ 4]);
     int e = 0;
@@ -591,7 +622,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   if (out_map) {
     // tensor stores of kOutBoxN outputs x kRows rows, clipped to the pass's rows and n1; they
     // complete in the background, and the buffer is next written after the wait above
-    if (tq == 0) {
+    if (tq == kStoreTq) {
       for (int j = 0; j * kOutBoxN < n1; ++j)
         umma::tma_store_2d(out_map, op + j * kOutBoxN * kRows * 8, 2 * row0, j * kOutBoxN);
       umma::bulk_commit();
@@ -669,6 +700,7 @@ k_views_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a, 
   extern __shared__ __align__(1024) unsigned char sm[];
   GroupCtx<L, PREC> c = group_setup<L, PREC>(sm, reinterpret_cast<const uint4*>(a.consts));
   int* const claim = reinterpret_cast<int*>(sm + Shape<L>::misc_offset(Prec<PREC>::kSplit) + 192);
+  int* pending = nullptr;  // the group's last x tile, released by its store thread at the next tile
   for (;;) {
     if (c.tq == 0) claim[c.g] = atomicAdd(f.sched, 1);
     group_bar(c.g);  // every thread reads the claim before the tile's next barrier
@@ -679,24 +711,22 @@ k_views_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a, 
     const int row0 = (tile - a.tile_off[p]) * kRows;
     const CUtensorMap* om = a.tma_store[p] ? &a.out_map[p] : nullptr;
     if (p < f.nx) {
-      if (!tile_t5<L, KIND_X, PREC, false>(c, sm, b.d[p], row0, om, a.err)) break;
-      // this tile's rows of the intermediate are written: tensor stores complete, then release
-      if (c.tq == 0) {
-        if (om) {
-          umma::bulk_wait();
-          umma::fence_async_to_global();
-        }
-        __threadfence();
-        atomicAdd(f.sched + 1 + p, 1);
-      }
+      int* const prev = pending;  // released inside the tile, once its input loads are in flight
+      pending = nullptr;
+      if (!tile_t5<L, KIND_X, PREC, false>(c, sm, b.d[p], row0, om, a.err, prev)) break;
+      pending = f.sched + 1 + p;
     } else {
       const int v = p - f.nx;
       bool w = true;
+      // the pending release first: this group may hold one of the tiles waited for
+      if (c.tq == kStoreTq && pending) signal_tile(pending);
+      pending = nullptr;
       if (c.tq == 0) w = wait_count(f.sched + 1 + v, a.tile_off[v + 1] - a.tile_off[v], a.err);
       if (!group_bar_and(c.g, w)) break;
       if (!tile_t5<L, PASS_Y, PREC, true>(c, sm, b.d[p], row0, om, a.err)) break;
     }
   }
+  if (c.tq == kStoreTq && pending) signal_tile(pending);
   group_teardown<L, PREC>(sm, c);
 }
 
