@@ -63,8 +63,8 @@ extern "C" {
  * 1024 -> 1024 or 512 -> 512) runs the four-step pass on tcgen05 (2048 =
  * 64 x 32, 1024 = 32 x 32: two DFT matrix products each way, operands in
  * shared memory, FP32 accumulators in tensor memory, one CTA per SM; on
- * FP16TC / BF16TC plans whose axes all share one such length, execute runs
- * both passes of up to eight views in one launch); other axes of length 2048
+ * FP16TC / BF16TC plans of two to eight views whose axes all share one such
+ * length, execute runs both passes in one launch); other axes of length 2048
  * or 4096 run radix-16/8 stages on mma.sync (FP16TC and BF16TC only).  Every other axis, the adjoint and the
  * persistent batch kernel run in FP32.  The x3 precisions apply to the
  * tcgen05 axes only and run every other axis in FP32.  Chirps, twiddles,
@@ -158,7 +158,7 @@ int shifted_fresnel_plan_update(sf_plan plan, const sf_view* views, int n_views,
  * x pass starting on the first half (FP32 plans).  The caller's stream waits
  * for the last copy, so the caller synchronises its stream before reading
  * host outputs.  Every view needs at least one non-NULL output.
- * With device outputs on an FP16TC or BF16TC plan of at most eight views
+ * With device outputs on an FP16TC or BF16TC plan of two to eight views
  * whose axes all run the tcgen05 pass, both passes of every view run as one
  * launch on `stream` (each view's y pass starting once its x pass is done).
  * Otherwise, with device outputs and two or more views, the views are split

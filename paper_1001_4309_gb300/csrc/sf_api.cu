@@ -1513,13 +1513,13 @@ cudaError_t execute_host_outputs(sf_plan plan, const ExecBuffers& io, bool pipel
 // Device outputs on `s` alone: every view's x pass, then every y pass, each
 // grouped by FFT length; profiling events (when attached) bracket the passes.
 // An FP16 or BF16 plan (the x3 precisions, two groups per SM, measure
-// faster with one launch per pass) whose views all run both axes on the
-// tcgen05 pass (FFT length 2048 with the 2N padding on both axes), at most
-// kMaxPassBatch / 2 views.
+// faster with one launch per pass) of two to kMaxPassBatch / 2 views (one
+// view measures faster with one launch per pass) that all run both axes on
+// the tcgen05 pass at one FFT length (2048 or 1024, with the 2N padding).
 bool fused_t5_eligible(sf_plan p) {
   const int nv = (int)p->views.size();
   if (p->precision != SF_PREC_FP16TC && p->precision != SF_PREC_BF16TC) return false;
-  if (!p->t5_sched || nv < 1 || nv > kMaxPassBatch / 2) return false;
+  if (!p->t5_sched || nv < 2 || nv > kMaxPassBatch / 2) return false;
   const int L = p->views[0].ax[0].L;  // one FFT length on every axis of every view
   if (!t5_consts_for(p, L)) return false;
   for (const ViewState& vs : p->views)

@@ -306,11 +306,14 @@ __device__ __forceinline__ GroupCtx<L, PREC> group_setup(unsigned char* sm, cons
   return c;
 }
 
-// This group's tensor stores complete, then the CTA frees its tensor memory.
+// This group's tensor stores complete, the constant-image copy has landed
+// (a CTA whose groups got no tile never waited for it), then the CTA frees
+// its tensor memory.
 template <int L, int PREC>
 __device__ __forceinline__ void group_teardown(unsigned char* sm, const GroupCtx<L, PREC>& c) {
   using S = Shape<L>;
   if (c.tq == kStoreTq) umma::bulk_wait();
+  if (threadIdx.x == 0) umma::mbar_wait(c.cbar, 0, kSpin, kSuspendNs);
   umma::fence_before_sync();
   __syncthreads();
   if (threadIdx.x < 32)
@@ -660,7 +663,11 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
   constexpr int kGroups = Prec<PREC>::kGroups;
   extern __shared__ __align__(1024) unsigned char sm[];
   GroupCtx<L, PREC> c = group_setup<L, PREC>(sm, reinterpret_cast<const uint4*>(a.consts));
-  for (int tile = blockIdx.x * kGroups + c.g; tile < a.total_tiles; tile += gridDim.x * kGroups) {
+  // tiles CTA-major (a CTA's groups on neighbouring rows) when every group has one, else group-major, so
+  // that a launch with fewer tiles than groups spreads them over every SM
+  const bool full = a.total_tiles >= (int)gridDim.x * kGroups;
+  for (int tile = full ? blockIdx.x * kGroups + c.g : c.g * gridDim.x + blockIdx.x; tile < a.total_tiles;
+       tile += gridDim.x * kGroups) {
     int p = 0;
     while (tile >= a.tile_off[p + 1]) ++p;
     if (!tile_t5<L, KIND, PREC, false>(c, sm, b.d[p], (tile - a.tile_off[p]) * kRows,
@@ -885,8 +892,7 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
   for (int k = 0; k < b.count; ++k)
     a.tma_store[k] = output_tensor_map(kind, b.d[k], t5::kRows, &a.out_map[k], true) ? 1 : 0;
   if (a.total_tiles == 0) return cudaSuccess;
-  const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
-  const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
+  const int grid = std::min(sms, a.total_tiles);  // every SM that can have a tile gets one
 #define SF_T5_PREC_CASES(LL)                                                                  \
   switch (prec) {                                                                              \
     case SF_PREC_FP16TC: return t5::launch_t<LL, SF_PREC_FP16TC>(kind, b, a, grid, s);         \
@@ -916,8 +922,7 @@ cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b
   cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(int) * (1 + nx), s);
   if (e != cudaSuccess) return e;
   const t5::FuseArgs f{sched, nx};
-  const int groups = (prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC) ? 2 : 4;
-  const int grid = std::min(sms, (a.total_tiles + groups - 1) / groups);
+  const int grid = std::min(sms, a.total_tiles);  // every SM that can have a tile gets one
   // FP16 / BF16 only (the x3 precisions run one launch per pass)
   switch (prec) {
     case SF_PREC_FP16TC:
