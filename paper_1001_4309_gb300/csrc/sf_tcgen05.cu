@@ -65,6 +65,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -685,13 +686,15 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
 // intermediate is written.  x tiles never wait, so the claims cannot
 // deadlock even when not every CTA of the grid is resident.
 struct FuseArgs {
-  int* sched;  // [0]: next tile to claim, [1 + v]: completed x tiles of view v; zero at launch
-  int nx;      // views
+  int* sched;            // [0]: next tile to claim, [1 + v]: completed x tiles of view v; zero at launch
+  int nx;                // views
+  int poison_view;       // -1; a view index makes its y tiles' dependency unsatisfiable (tests)
+  long long spin_limit;  // polls of a y tile's dependency wait before it gives up
 };
 
 // Bounded wait until *ctr >= need (acquire at GPU scope); false (err set) when it gives up.
-__device__ __forceinline__ bool wait_count(const int* ctr, int need, int* err) {
-  for (long long i = 0; i < kDepSpin; ++i) {
+__device__ __forceinline__ bool wait_count(const int* ctr, int need, int* err, long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
     if (v >= need) return true;
@@ -728,7 +731,10 @@ k_views_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a, 
       // the pending release first: this group may hold one of the tiles waited for
       if (c.tq == kStoreTq && pending) signal_tile(pending);
       pending = nullptr;
-      if (c.tq == 0) w = wait_count(f.sched + 1 + v, a.tile_off[v + 1] - a.tile_off[v], a.err);
+      if (c.tq == 0) {
+        const int need = v == f.poison_view ? 0x7fffffff : a.tile_off[v + 1] - a.tile_off[v];
+        w = wait_count(f.sched + 1 + v, need, a.err, f.spin_limit);
+      }
       if (!group_bar_and(c.g, w)) break;
       if (!tile_t5<L, PASS_Y, PREC, true>(c, sm, b.d[p], row0, om, a.err)) break;
     }
@@ -921,7 +927,10 @@ cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b
   if (a.total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(int) * (1 + nx), s);
   if (e != cudaSuccess) return e;
-  const t5::FuseArgs f{sched, nx};
+  // SF_T5_POISON_VIEW / SF_T5_SPIN_LIMIT: an unsatisfiable dependency and a short wait (tests)
+  const char* pv = std::getenv("SF_T5_POISON_VIEW");
+  const char* sl = std::getenv("SF_T5_SPIN_LIMIT");
+  const t5::FuseArgs f{sched, nx, pv && *pv ? std::atoi(pv) : -1, sl && *sl ? std::atoll(sl) : t5::kDepSpin};
   const int grid = std::min(sms, a.total_tiles);  // every SM that can have a tile gets one
   // FP16 / BF16 only (the x3 precisions run one launch per pass)
   switch (prec) {

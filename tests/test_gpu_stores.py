@@ -155,3 +155,29 @@ def test_rows_per_cta_variants_paper_scale(P, c2, impl, monkeypatch):
     for a, b in zip(got, ref):
         assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
 
+
+
+def test_fused_launch_poisoned_dependency_times_out(P, c2, monkeypatch):
+    """A y-tile dependency that the host makes unsatisfiable (view 1) ends the fused launch through its
+    bounded waits: the plan reports SF_ERR_TIMEOUT once, and the next execute gives the same bits again."""
+    import torch
+    h, views, _ = c2
+    handle = plan(P, views, 1)
+    try:
+        ref, _, _ = execute(P, handle, views, h)
+        monkeypatch.setenv("SF_T5_POISON_VIEW", "1")
+        monkeypatch.setenv("SF_T5_SPIN_LIMIT", "2000")
+        s = torch.cuda.current_stream().cuda_stream
+        outs = [torch.empty((v["ny1"], v["nx1"]), dtype=torch.complex64, device="cuda") for v in views]
+        n0 = P.shifted_fresnel_kernel_launches()
+        P.shifted_fresnel_execute(handle, h.data_ptr(), [o.data_ptr() for o in outs], stream=s)
+        assert P.shifted_fresnel_kernel_launches() - n0 == 1
+        assert P.binding.shifted_fresnel_batch_status(handle, stream=s) == P.SF_ERR_TIMEOUT
+        assert P.binding.shifted_fresnel_batch_status(handle, stream=s) == 0  # cleared
+        monkeypatch.delenv("SF_T5_POISON_VIEW")
+        monkeypatch.delenv("SF_T5_SPIN_LIMIT")
+        again, _, _ = execute(P, handle, views, h)
+    finally:
+        P.shifted_fresnel_destroy(handle)
+    for a, b in zip(again, ref):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
