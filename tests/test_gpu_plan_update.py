@@ -147,15 +147,17 @@ def test_update_then_batch(P, impl, monkeypatch):
         sf.close()
 
 
-def test_update_tensor_core_plan(P):
+@pytest.mark.parametrize("n,prec", [(1024, 1), (512, 1), (1024, 3)], ids=["2048-fp16", "1024-fp16", "2048-fp16x3"])
+def test_update_tensor_core_plan(P, n, prec):
+    """Tensor-core plans at both tcgen05 lengths (fused launch for FP16, one launch per pass for FP16X3):
+    the natural-order kernel spectra are rebuilt with the new views."""
     import torch
-    n = 1024
     mk = lambda z, p1, o: view(WAVELENGTH, z, PITCH, p1, o1=o, n0=(n, n), n1=(n, n))  # noqa: E731
     va = [mk(0.03, 4.65e-6, (0.0, 0.0)), mk(0.05, 2e-6, (1e-4, 0.0))]
     vb = [mk(0.07, 1e-6, (-2e-4, 1e-4)), mk(0.1, 0.5e-6, (3e-4, -3e-4))]
     h = torch.from_numpy(random_field(n, n, seed=6).real.astype(np.float32)).cuda()
-    fresh = P.ShiftedFresnel(vb, precision=P.SF_PREC_FP16TC)
-    sf = P.ShiftedFresnel(va, precision=P.SF_PREC_FP16TC)
+    fresh = P.ShiftedFresnel(vb, precision=prec)
+    sf = P.ShiftedFresnel(va, precision=prec)
     try:
         sf.update(vb)
         a = fresh.reconstruct(h, field=True)["field"]
