@@ -4,7 +4,8 @@
 // memory, FP32 accumulators in tensor memory), chirps, twiddles and kernel
 // spectrum applied in FP32 between them.
 //
-// Four-step split of the FFT of length L = R1 * R2 (R2 = 32, R1 = L / 32):
+// Four-step split of the FFT of length L = R1 * R2 (R2 = 32, R1 = L / 32;
+// built for L = 2048 and 1024):
 //   n = R2 n1 + n2,  k = k1 + R1 k2
 //   X[k1 + R1 k2] = sum_n2 W_R2^{n2 k2} W_L^{n2 k1} sum_n1 x[R2 n1 + n2] W_R1^{n1 k1}
 // and the inverse in the mirrored order, each inverse DFT taken as
@@ -46,17 +47,19 @@
 // overlaps the first tile's loads; groups start 1 us apart so that their
 // products do not reach the tensor core together; the spectrum and
 // output-chirp loads are issued before the waits for the products they
-// follow.  k_pass_t5 runs one pass (tiles round-robin over the groups);
-// k_views_t5 runs both passes of up to eight views, tiles claimed in order
-// from a global counter, each view's y tiles after its x tiles.  Every wait
+// follow; one store thread per group issues the tensor stores and waits for
+// them.  k_pass_t5 runs one pass (tiles round-robin over the groups, spread
+// over every SM when there are fewer tiles than groups); k_views_t5 runs both
+// passes of two to eight views, tiles claimed in order from a global counter,
+// each view's y tiles after its x tiles.  Every wait
 // (MMA completion, constant image, a y tile's dependency) is bounded; on
 // expiry the group sets the plan's device error word, waits once more
 // (bounded) where a copy may be in flight, leaves its tile loop and the CTA
 // frees its tensor memory.
 //
 // Measured on the paper-scale step (four 1024^2 views, L = 2048 both axes):
-// FP16 and BF16 72.4 us fused (81.5 us with one launch per pass), FP16x3
-// 106-109 us, against 76.2 us for the FP32 pass.  The tensor pipe is ~10 %
+// FP16 and BF16 68.5-69.3 us fused (73.4 us with one launch per pass),
+// FP16x3 100.5 us, against 76.1 us for the FP32 pass.  The tensor pipe is ~10 %
 // busy: the pass is bound by the latency of a tile's chain (loads, four
 // product round trips, FP32 epilogues, output staging; 14-17 us per tile)
 // at 16 rows in flight per SM, the number that tensor memory allows.
