@@ -534,6 +534,31 @@ def batched_runs(holo_np, views, dev, stream, flush, hbm_peak):
     sf = P.ShiftedFresnel(views, device=dev.index)
     holos = [torch.from_numpy(holo_np).to(dev) for _ in range(H)]
     entry("stream_1024_4views", "16 holograms x the 1024^2 four-view set per call", sf, views, holos, 20)
+    sf.close()
+    # the same stream on an FP16 tensor-core plan: one fused tcgen05 launch per hologram (default), or
+    # one launch per pass (SF_T5_FUSED=0)
+    import os
+    sf = P.ShiftedFresnel(views, device=dev.index, precision=P.SF_PREC_FP16TC)
+    outs = sf.alloc_batch_outputs(H, field=True)
+    t_fused = time_batch(sf, holos, outs, stream, flush, 20)
+    os.environ["SF_T5_FUSED"] = "0"
+    try:
+        # fresh output buffers: the batch replays its captured graph while the buffers stay the same
+        outs2 = sf.alloc_batch_outputs(H, field=True)
+        t_pass = time_batch(sf, holos, outs2, stream, flush, 20)
+        del outs2
+    finally:
+        os.environ.pop("SF_T5_FUSED", None)
+    n = H * len(views)
+    res["stream_1024_4views_fp16tc"] = {
+        "workload": "16 holograms x the 1024^2 four-view set per call, FP16 tensor-core plan",
+        "value": round(n / (t_fused * 1e-3), 1), "unit": UNIT, "ms_per_launch": round(t_fused, 4),
+        "per_pass_launches_value": round(n / (t_pass * 1e-3), 1),
+        "vs_fp32_batch": round(res["stream_1024_4views"]["value"] and
+                               (n / (t_fused * 1e-3)) / res["stream_1024_4views"]["value"], 3),
+        "what": "one fused tcgen05 launch per hologram on alternating streams (default) against one launch "
+                "per pass"}
+    del outs
     del holos
     sf.close()
     # small views, launch-bound: 64 holograms x one 256^2 -> 256^2 view (FFT length 512)

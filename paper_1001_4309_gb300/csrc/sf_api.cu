@@ -83,6 +83,8 @@ enum { BATCH_PERSISTENT = 0, BATCH_STREAMS = 1 };
 
 }  // namespace
 
+constexpr int kSchedInts = 1 + sf::kMaxPassBatch;  // one fused launch's schedule buffer
+
 struct sf_plan_s {
   int device = 0;
   int nx0 = 0, ny0 = 0;
@@ -92,7 +94,9 @@ struct sf_plan_s {
   int precision = SF_PREC_FP32;
   uint32_t* tc_frags = nullptr;  // per-lane DFT fragments and twiddle tables of the tensor-core pass
   void* t5_consts[2] = {nullptr, nullptr};  // DFT operands and twiddles of the tcgen05 row pass, FFT length 1024 / 2048
-  int* t5_sched = nullptr;       // tile counter and per-view x-tile counts of the fused tcgen05 launch
+  // schedule buffers of fused tcgen05 launches (tile counter, per-view x-tile counts): execute's,
+  // then one per batch stream, kSchedInts each
+  int* t5_sched = nullptr;
   int* dev_err = nullptr;        // device error word of the persistent kernels (bounded waits)
   AxisCoef* axes_dev = nullptr;  // coefficient table read by the chirp and spectrum kernels
   // row-pass kernel per (length slot, kind): 0 grid, 1 persistent TMA, 2 / 3 grid with half / twice the rows per CTA
@@ -918,6 +922,67 @@ int ensure_stream_slots(sf_plan p) {
   return SF_OK;
 }
 
+// An FP16 or BF16 plan (the x3 precisions, two groups per SM, measure
+// faster with one launch per pass) of two to kMaxPassBatch / 2 views (one
+// view measures faster with one launch per pass) that all run both axes on
+// the tcgen05 pass at one FFT length (2048 or 1024, with the 2N padding).
+bool fused_t5_eligible(sf_plan p) {
+  const int nv = (int)p->views.size();
+  if (p->precision != SF_PREC_FP16TC && p->precision != SF_PREC_BF16TC) return false;
+  if (!p->t5_sched || nv < 2 || nv > kMaxPassBatch / 2) return false;
+  const int L = p->views[0].ax[0].L;  // one FFT length on every axis of every view
+  if (!t5_consts_for(p, L)) return false;
+  for (const ViewState& vs : p->views)
+    for (int a = 0; a < 2; ++a) {
+      const AxisCoef& c = vs.ax[a];
+      if (c.L != L || 2 * c.n0 > c.L || 2 * c.n1 > c.L || !vs.hnat[a]) return false;
+    }
+  return true;
+}
+
+// Both passes of every view of a fused_t5_eligible plan as one persistent
+// tcgen05 launch: x passes read the hologram src into work[v], y passes write
+// dout / dint / dph[v] (null where not wanted); sched: this launch's schedule
+// buffer (launches that may overlap take different ones).
+cudaError_t launch_fused_views(sf_plan plan, const void* src, float2* const* work, float2* const* dout,
+                               float* const* dint, float* const* dph, int* sched, cudaStream_t s) {
+  const int nv = (int)plan->views.size();
+  const int L = plan->views[0].ax[0].L;
+  PassBatch b;
+  std::memset(&b, 0, sizeof(b));
+  for (int axis = 0; axis < 2; ++axis)
+    for (int vi = 0; vi < nv; ++vi) {
+      const ViewState& vs = plan->views[vi];
+      const AxisCoef& c = vs.ax[axis];
+      PassDesc& d = b.d[b.count++];
+      d.cin = c.cin;
+      d.cout = c.cout;
+      d.H = vs.hnat[axis];
+      d.n0 = c.n0;
+      d.n1 = c.n1;
+      if (axis == 0) {
+        d.src = src;
+        d.dst = work[vi];
+        d.rows = vs.v.ny0;
+        d.src_ld = vs.v.nx0;
+        d.dst_ld = vs.v.ny0;
+      } else {
+        d.src = work[vi];
+        d.dst = dout[vi];
+        d.inten = dint[vi];
+        d.phase = dph[vi];
+        d.rows = vs.v.nx1;
+        d.src_ld = vs.v.ny0;
+        d.dst_ld = vs.v.nx1;
+      }
+    }
+  const PassKind kx = plan->in_complex ? PASS_X_CPLX : PASS_X_REAL;
+  const cudaError_t e =
+      launch_views_t5(L, plan->precision, kx, b, nv, t5_consts_for(plan, L), plan->dev_err, sched, plan->sms, s);
+  ++g_launches;
+  return e;
+}
+
 cudaError_t enqueue_batch_streams(sf_plan plan, const void* const* holos, int n_holos, void* const* view_out,
                                   float* const* intensity, float* const* phase, cudaStream_t s) {
   BatchState& b = plan->batch;
@@ -989,6 +1054,7 @@ cudaError_t enqueue_batch_streams(sf_plan plan, const void* const* holos, int n_
   std::vector<float2*> work(nv), dout(nv);
   std::vector<float*> dint(nv), dph(nv);
   auto none = [](const int*, int) { return cudaSuccess; };
+  const bool fused = fused_t5_eligible(plan) && !env_is("SF_T5_FUSED", "0");
   for (int h = 0; h < n_holos && e == cudaSuccess; ++h) {
     for (int v = 0; v < nv; ++v) {
       const size_t i = (size_t)h * nv + v;
@@ -996,6 +1062,11 @@ cudaError_t enqueue_batch_streams(sf_plan plan, const void* const* holos, int n_
       dout[v] = view_out ? static_cast<float2*>(view_out[i]) : nullptr;
       dint[v] = intensity ? intensity[i] : nullptr;
       dph[v] = phase ? phase[i] : nullptr;
+    }
+    if (fused) {  // one launch per hologram; the two streams' launches keep separate schedule buffers
+      e = launch_fused_views(plan, holos[h], work.data(), dout.data(), dint.data(), dph.data(),
+                             plan->t5_sched + (1 + (h & 1)) * kSchedInts, b.st[h & 1]);
+      continue;
     }
     for (int axis = 0; axis < 2 && e == cudaSuccess; ++axis)
       e = launch_axis(plan, axis, holos[h], work.data(), dout.data(), dint.data(), dph.data(), kMaxPassBatch,
@@ -1239,7 +1310,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   const size_t off_frags = mma_sync_tables ? ar.take(sizeof(uint32_t) * tc_table_words()) : SIZE_MAX;
   size_t off_t5[2];
   for (int k = 0; k < 2; ++k) off_t5[k] = t5_len[k] ? ar.take(t5_const_bytes(1024 << k, precision)) : SIZE_MAX;
-  const size_t off_sched = any_t5 ? ar.take(sizeof(int) * (1 + kMaxPassBatch)) : SIZE_MAX;
+  const size_t off_sched = any_t5 ? ar.take(sizeof(int) * 3 * kSchedInts) : SIZE_MAX;
   const size_t off_err = ar.take(sizeof(int));
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
   if (cudaMalloc(&p->arena, ar.off) != cudaSuccess) {
@@ -1512,64 +1583,12 @@ cudaError_t execute_host_outputs(sf_plan plan, const ExecBuffers& io, bool pipel
 
 // Device outputs on `s` alone: every view's x pass, then every y pass, each
 // grouped by FFT length; profiling events (when attached) bracket the passes.
-// An FP16 or BF16 plan (the x3 precisions, two groups per SM, measure
-// faster with one launch per pass) of two to kMaxPassBatch / 2 views (one
-// view measures faster with one launch per pass) that all run both axes on
-// the tcgen05 pass at one FFT length (2048 or 1024, with the 2N padding).
-bool fused_t5_eligible(sf_plan p) {
-  const int nv = (int)p->views.size();
-  if (p->precision != SF_PREC_FP16TC && p->precision != SF_PREC_BF16TC) return false;
-  if (!p->t5_sched || nv < 2 || nv > kMaxPassBatch / 2) return false;
-  const int L = p->views[0].ax[0].L;  // one FFT length on every axis of every view
-  if (!t5_consts_for(p, L)) return false;
-  for (const ViewState& vs : p->views)
-    for (int a = 0; a < 2; ++a) {
-      const AxisCoef& c = vs.ax[a];
-      if (c.L != L || 2 * c.n0 > c.L || 2 * c.n1 > c.L || !vs.hnat[a]) return false;
-    }
-  return true;
-}
-
 // Device outputs of a plan that fused_t5_eligible accepts: the x and y passes
-// of every view in one persistent tcgen05 launch, each view's y tiles
-// starting as soon as its x tiles are done.
+// of every view in one persistent tcgen05 launch on the plan's first schedule
+// buffer, each view's y tiles starting as soon as its x tiles are done.
 cudaError_t execute_fused_t5(sf_plan plan, const ExecBuffers& io, cudaStream_t s) {
-  const int nv = (int)plan->views.size();
-  const int L = plan->views[0].ax[0].L;
-  PassBatch b;
-  std::memset(&b, 0, sizeof(b));
-  for (int axis = 0; axis < 2; ++axis)
-    for (int vi = 0; vi < nv; ++vi) {
-      const ViewState& vs = plan->views[vi];
-      const AxisCoef& c = vs.ax[axis];
-      PassDesc& d = b.d[b.count++];
-      d.cin = c.cin;
-      d.cout = c.cout;
-      d.H = vs.hnat[axis];
-      d.n0 = c.n0;
-      d.n1 = c.n1;
-      if (axis == 0) {
-        d.src = io.src;
-        d.dst = io.work[vi];
-        d.rows = vs.v.ny0;
-        d.src_ld = vs.v.nx0;
-        d.dst_ld = vs.v.ny0;
-      } else {
-        d.src = io.work[vi];
-        d.dst = io.dout[vi];
-        d.inten = io.dint[vi];
-        d.phase = io.dph[vi];
-        d.rows = vs.v.nx1;
-        d.src_ld = vs.v.ny0;
-        d.dst_ld = vs.v.nx1;
-      }
-    }
-  const PassKind kx = plan->in_complex ? PASS_X_CPLX : PASS_X_REAL;
-  const cudaError_t e =
-      launch_views_t5(L, plan->precision, kx, b, nv, t5_consts_for(plan, L), plan->dev_err, plan->t5_sched,
-                      plan->sms, s);
-  ++g_launches;
-  return e;
+  return launch_fused_views(plan, io.src, io.work.data(), io.dout.data(), io.dint.data(), io.dph.data(),
+                            plan->t5_sched, s);
 }
 
 cudaError_t execute_single_stream(sf_plan plan, const ExecBuffers& io, cudaStream_t s) {

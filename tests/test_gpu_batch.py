@@ -312,3 +312,27 @@ def test_batch_autotuned_implementation(P, monkeypatch):
             check_equal(outs, ref)
     finally:
         sf.close()
+
+
+@pytest.mark.parametrize("fused", ["default", "per-pass"])
+def test_tensor_core_batch_equals_per_hologram(P, fused, monkeypatch):
+    """FP16 plan of two 1024^2 views (both axes on the tcgen05 pass): the streams batch with one fused
+    launch per hologram on alternating streams (default) or one launch per pass gives the bits of
+    per-hologram execute, field and intensity."""
+    import torch
+    if fused == "per-pass":
+        monkeypatch.setenv("SF_T5_FUSED", "0")
+    n = 1024
+    vs = [view(WAVELENGTH, 0.04, PITCH, 2e-6, n0=(n, n), n1=(n, n)),
+          view(WAVELENGTH, 0.07, PITCH, 1e-6, o1=(1e-4, 0.0), n0=(n, n), n1=(n, n))]
+    sf = P.ShiftedFresnel(vs, precision=P.SF_PREC_FP16TC)
+    try:
+        holos = holograms(3, shape=(n, n), seed=40)
+        ref = per_hologram(sf, holos)
+        outs = sf.alloc_batch_outputs(3, field=True, intensity=True)
+        sf.execute_batch(holos, outs)
+        torch.cuda.synchronize()
+        assert P.shifted_fresnel_batch_status(sf.handle, torch.cuda.current_stream().cuda_stream) == P.SF_OK
+        check_equal(outs, ref)
+    finally:
+        sf.close()
