@@ -160,7 +160,9 @@ int shifted_fresnel_plan_update(sf_plan plan, const sf_view* views, int n_views,
  * host outputs.  Every view needs at least one non-NULL output.
  * With device outputs on an FP16TC or BF16TC plan of two to eight views
  * whose axes all run the tcgen05 pass, both passes of every view run as one
- * launch on `stream` (each view's y pass starting once its x pass is done).
+ * launch on `stream` (each view's y pass starting once its x pass is done;
+ * SF_T5_FUSED=0 keeps one launch per pass; the streams batch, below, runs
+ * one such launch per hologram).
  * Otherwise, with device outputs and two or more views, the views are split
  * into two halves of about equal work run on `stream` and on a plan-owned
  * second stream (x pass then y pass each), so one half's y pass overlaps the
