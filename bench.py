@@ -614,9 +614,9 @@ def time_precision(views, holo, prec, dev, stream, flush, steps, warmup):
 
 def mixed_precision(holo_np, holo, views, dev, stream, flush, a, step_bytes, hbm_peak, fp32_value):
     """The 4-view step with the DFT stages on tensor cores, plus single 256^2 / 1024^2 / 2048^2 views
-    (the mixed-precision set) and a 512^2 view (FFT length 1024: the 32 x 32 tcgen05 split; the 256^2
-    view's FFT length 512 has no tensor-core pass and runs in FP32); per-view error vs the FP64 oracle
-    next to the FP32 path."""
+    (the mixed-precision set) and a 512^2 view (FFT lengths 512, 1024, 2048 and 4096: the tcgen05 pass
+    with its 16 x 32, 32 x 32 and 64 x 32 splits, and at 4096 the mma.sync stages or FP32); per-view
+    error vs the FP64 oracle next to the FP32 path."""
     import torch
     import synth
     import paper_1001_4309_gb300 as P
@@ -657,7 +657,7 @@ def row_pass_kind(v, prec):
         L *= 2
     if prec == 0:
         return "fp32"
-    if L in (1024, 2048) and 2 * v["nx0"] <= L and 2 * v["nx1"] <= L:
+    if L in (512, 1024, 2048) and 2 * v["nx0"] <= L and 2 * v["nx1"] <= L:
         return "tcgen05"
     if L in (2048, 4096) and prec in (1, 2):
         return "mma.sync"

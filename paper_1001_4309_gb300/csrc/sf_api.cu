@@ -93,7 +93,8 @@ struct sf_plan_s {
   std::map<int, float4*> tw;  // per-stage twiddle tables per FFT length
   int precision = SF_PREC_FP32;
   uint32_t* tc_frags = nullptr;  // per-lane DFT fragments and twiddle tables of the tensor-core pass
-  void* t5_consts[2] = {nullptr, nullptr};  // DFT operands and twiddles of the tcgen05 row pass, FFT length 1024 / 2048
+  // DFT operands and twiddles of the tcgen05 row pass, FFT length 512 / 1024 / 2048
+  void* t5_consts[3] = {nullptr, nullptr, nullptr};
   // schedule buffers of fused tcgen05 launches (tile counter, per-view x-tile counts): execute's,
   // then one per batch stream, kSchedInts each
   int* t5_sched = nullptr;
@@ -135,7 +136,7 @@ namespace sf {
 namespace {
 // the tcgen05 constants of FFT length L, or null (no tcgen05 pass at L in this plan)
 void* t5_consts_for(const sf_plan_s* p, int L) {
-  return L == 1024 ? p->t5_consts[0] : L == 2048 ? p->t5_consts[1] : nullptr;
+  return L == 512 ? p->t5_consts[0] : L == 1024 ? p->t5_consts[1] : L == 2048 ? p->t5_consts[2] : nullptr;
 }
 }  // namespace
 }  // namespace sf
@@ -925,7 +926,7 @@ int ensure_stream_slots(sf_plan p) {
 // An FP16 or BF16 plan (the x3 precisions, two groups per SM, measure
 // faster with one launch per pass) of two to kMaxPassBatch / 2 views (one
 // view measures faster with one launch per pass) that all run both axes on
-// the tcgen05 pass at one FFT length (2048 or 1024, with the 2N padding).
+// the tcgen05 pass at one FFT length (2048, 1024 or 512, with the 2N padding).
 bool fused_t5_eligible(sf_plan p) {
   const int nv = (int)p->views.size();
   if (p->precision != SF_PREC_FP16TC && p->precision != SF_PREC_BF16TC) return false;
@@ -1279,7 +1280,7 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
   std::vector<size_t> off_cin(4 * n_views), off_cout(4 * n_views), off_H(4 * n_views), off_work(n_views);
   std::vector<size_t> off_hpos(2 * n_views, SIZE_MAX), off_hnat(2 * n_views, SIZE_MAX);
   const bool mma_sync_tables = precision == SF_PREC_FP16TC || precision == SF_PREC_BF16TC;
-  bool any_t5 = false, t5_len[2] = {false, false};
+  bool any_t5 = false, t5_len[3] = {false, false, false};  // FFT lengths 512, 1024, 2048
   for (int i = 0; i < n_views; ++i) {
     ViewState& vs = p->views[i];
     vs.v = views[i];
@@ -1303,13 +1304,13 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
       if (precision != SF_PREC_FP32 && t5_length_supported(vs.ax[a].L)) {
         off_hnat[2 * i + a] = ar.take(sizeof(float2) * vs.ax[a].L);
         any_t5 = true;
-        t5_len[vs.ax[a].L == 2048 ? 1 : 0] = true;
+        t5_len[vs.ax[a].L == 2048 ? 2 : vs.ax[a].L == 1024 ? 1 : 0] = true;
       }
     }
   }
   const size_t off_frags = mma_sync_tables ? ar.take(sizeof(uint32_t) * tc_table_words()) : SIZE_MAX;
-  size_t off_t5[2];
-  for (int k = 0; k < 2; ++k) off_t5[k] = t5_len[k] ? ar.take(t5_const_bytes(1024 << k, precision)) : SIZE_MAX;
+  size_t off_t5[3];
+  for (int k = 0; k < 3; ++k) off_t5[k] = t5_len[k] ? ar.take(t5_const_bytes(512 << k, precision)) : SIZE_MAX;
   const size_t off_sched = any_t5 ? ar.take(sizeof(int) * 3 * kSchedInts) : SIZE_MAX;
   const size_t off_err = ar.take(sizeof(int));
   const size_t off_axes = ar.take(sizeof(AxisCoef) * 4 * n_views);
@@ -1359,12 +1360,12 @@ int shifted_fresnel_plan(sf_plan* out, const sf_view* views, int n_views, int pr
     g_launches += 3;  // fragments and the twiddle tables of both lengths
   }
   if (off_sched != SIZE_MAX) p->t5_sched = reinterpret_cast<int*>(base + off_sched);
-  std::vector<unsigned char> t5_host[2];  // kept alive until the stream is synchronised below
-  for (int k = 0; k < 2; ++k)
+  std::vector<unsigned char> t5_host[3];  // kept alive until the stream is synchronised below
+  for (int k = 0; k < 3; ++k)
     if (off_t5[k] != SIZE_MAX && e == cudaSuccess) {
       p->t5_consts[k] = base + off_t5[k];
-      t5_host[k].resize(t5_const_bytes(1024 << k, precision));
-      t5_build_consts(1024 << k, precision, t5_host[k].data());
+      t5_host[k].resize(t5_const_bytes(512 << k, precision));
+      t5_build_consts(512 << k, precision, t5_host[k].data());
       e = cudaMemcpyAsync(p->t5_consts[k], t5_host[k].data(), t5_host[k].size(), cudaMemcpyHostToDevice, s);
     }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -17,7 +17,7 @@
 // Every product is the real GEMM D (128 x N) = A (128 x K) B (K x N) of the
 // block form [Re | Im] [[Fr, Fi], [-Fi, Fr]] of a unitary-scaled DFT matrix
 // F; a CTA holds kGroups independent groups of eight warps, and a group
-// transforms a tile of kRows = 4 rows at a time:
+// transforms a tile of TR = 4 rows at a time (8 at L = 512, see Shape):
 //
 //   stage A   rows (r, n2), K = (re, im) of n1 < R1/2, N = (re, im) of k1
 //   twiddle   W_L^{n2 k1} (FP32), to the stage-B operand (transpose via
@@ -79,7 +79,6 @@ namespace sf {
 namespace t5 {
 
 constexpr int kR2 = 32;        // inner radix: the lanes of a warp
-constexpr int kRows = 4;       // rows per tile (one warp per row in the first stage)
 constexpr int kGroupWarps = 8;  // warps per group: two per tensor-memory lane quarter
 constexpr int kGroupThreads = 32 * kGroupWarps;
 // lane 0 of a group's last warp issues the group's tensor stores, waits for them and (fused launch)
@@ -107,12 +106,18 @@ struct Shape {
   static constexpr int R1 = L / kR2;
   static constexpr int KA = R1 / 2;  // nonzero n1 on input
   static constexpr int NA = R1 / 2;  // kept n1 on output
-  static_assert(R1 == 32 || R1 == 64, "tcgen05 row pass lengths: 1024 (32 x 32) and 2048 (64 x 32)");
+  static_assert(R1 == 16 || R1 == 32 || R1 == 64,
+                "tcgen05 row pass lengths: 512 (16 x 32), 1024 (32 x 32) and 2048 (64 x 32)");
+  // rows per tile: 4 (the first product's 128 rows are 4 rows x 32 n2), 8 at R1 = 16 so that a
+  // middle-stage product still has 128 rows (8 rows x 16 k1); the first and last stages then take
+  // QA = 2 products of 128 rows
+  static constexpr int TR = R1 >= 32 ? 4 : 128 / R1;
+  static constexpr int QA = TR / 4;
   // real GEMM shapes (M = 128 throughout)
   static constexpr int A_K = 2 * KA, A_N = 2 * R1;    // stage A
   static constexpr int B_K = 2 * kR2, B_N = 2 * kR2;  // stages B and B^H
   static constexpr int H_K = 2 * R1, H_N = 2 * NA;    // stage A^H
-  static constexpr int QB = kRows * R1 / 128;         // products per middle stage
+  static constexpr int QB = TR * R1 / 128;            // products per middle stage
   static constexpr int RP = 128 / R1;                 // rows of a middle-stage product
   // a K-major operand row holds 64 K elements (128 bytes) per column, whatever K it uses
   static constexpr int kmaj_bytes(int rows, int k) { return rows * 128 * ((k + 63) / 64); }
@@ -124,11 +129,13 @@ struct Shape {
   static constexpr int MAT_BYTES = BA_BYTES + BB_BYTES + BH_BYTES;
   static constexpr int TW_LD = kR2 + 1;  // padded row of the twiddle table T[k1][n2] (float2)
   static constexpr int TW_BYTES = R1 * TW_LD * 8;
+  // operand bytes of one first-stage / last-stage product (K-major / MN-major, 128 rows)
+  static constexpr int A_PROD_BYTES = kmaj_bytes(128, A_K), AH_PROD_BYTES = 128 * H_K * 2;
+  static constexpr int cmax(int a, int b) { return a > b ? a : b; }
   // per-group operand buffer: the largest stage operand, also the output staging tile
-  static constexpr int OP_BYTES = 128 * H_K * 2;
-  static_assert(QB * 128 * B_K * 2 <= OP_BYTES && kRows * (L / 2) * 8 <= OP_BYTES &&
-                    kmaj_bytes(128, A_K) <= OP_BYTES && kmaj_bytes(128, B_K) * QB <= OP_BYTES,
-                "operand buffer");
+  static constexpr int OP_BYTES = cmax(cmax(QA * A_PROD_BYTES, QA * AH_PROD_BYTES),
+                                       cmax(QB * kmaj_bytes(128, B_K), cmax(QB * 128 * B_K * 2, TR * (L / 2) * 8)));
+  static_assert(OP_BYTES % 1024 == 0 && A_PROD_BYTES % 1024 == 0 && AH_PROD_BYTES % 1024 == 0, "1 KiB atoms");
   static constexpr int align(int b) { return (b + 1023) & ~1023; }
   static constexpr int const_bytes(bool split) { return (split ? 2 : 1) * MAT_BYTES + TW_BYTES; }
   static constexpr int op_offset(bool split) { return align(const_bytes(split)); }
@@ -325,12 +332,14 @@ __device__ __forceinline__ void group_teardown(unsigned char* sm, const GroupCtx
                        128 * Prec<PREC>::kGroups);
 }
 
-// Output staging tile: output n of row r (kRows = 4 rows, 32 bytes per n) at
-// float2 index 4 n + r with the tensor map's 32-byte swizzle applied (16-byte
+// Output staging tile: output n of row r at float2 index TR n + r.  With 4
+// rows (32 bytes per n) the tensor map's 32-byte swizzle applies (16-byte
 // chunk r / 2 XOR bit 2 of n), so a warp writing 32 consecutive n of one row
-// spreads over twice as many banks as the plain layout.
+// spreads over twice as many banks as the plain layout; 8-row tiles are plain.
+template <int TR>
 __device__ __forceinline__ int stage_idx(int n, int r) {
-  return kRows * n + ((((r >> 1) ^ (n >> 2)) & 1) << 1) + (r & 1);
+  if constexpr (TR == 4) return 4 * n + ((((r >> 1) ^ (n >> 2)) & 1) << 1) + (r & 1);
+  else return TR * n + r;
 }
 
 // Release of a finished x tile of a fused launch (the group's store thread):
@@ -342,7 +351,7 @@ __device__ __forceinline__ void signal_tile(int* ctr) {
   atomicAdd(ctr, 1);
 }
 
-// One tile: rows row0 .. row0 + kRows - 1 of pass d, steps 2-9 along the
+// One tile: rows row0 .. row0 + TR - 1 of pass d, steps 2-9 along the
 // pass's axis.  out_map: the pass's output tensor map (tensor stores), else
 // plain stores.  signal (fused launch, x passes): the counter on which the
 // store thread releases the group's previous x tile, once this tile's input
@@ -354,7 +363,11 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   using S = Shape<L>;
   constexpr bool SPLIT = Prec<PREC>::kSplit, BF = Prec<PREC>::kBf16;
   constexpr int R1 = S::R1, KA = S::KA, NA = S::NA;
-  constexpr int KH = KA / 2, NH = NA / 2, CH = kR2 / 2;  // each warp's half of n1 (in, out) and of n2 / k2
+  constexpr int TR = S::TR;
+  // 4-row tiles: warp (wq, hh) takes row wq and half hh of n1 (in and out); 8-row tiles: warp gw takes
+  // row gw = 4 hh + wq, all of n1, and hh is the first / last stage's product holding it
+  constexpr bool kHalfN1 = TR == 4;
+  constexpr int KH = kHalfN1 ? KA / 2 : KA, NH = kHalfN1 ? NA / 2 : NA, CH = kR2 / 2;
   const int g = ctx.g, tq = ctx.tq, gw = ctx.gw, wq = ctx.wq, hh = ctx.hh, l = ctx.l;
   unsigned char* const op = ctx.op;
   uint64_t* const bars = ctx.bars;
@@ -391,12 +404,16 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   };
   const int n0 = d.n0, n1 = d.n1;
 
+  const int rr = kHalfN1 ? wq : gw;      // this warp's row in the tile (first and last stage)
+  const int n1w = kHalfN1 ? KH * hh : 0;  // its first n1 on input (NH hh on output)
+  const int pa = kHalfN1 ? 0 : hh;        // its first / last stage product
+
   // ---- input x chirp (steps 2-3), row normalisation, stage-A operand (K-major).
-  // Warp (wq, hh) takes row wq, n1 in [KH hh, KH hh + KH); the row's maximum
-  // is combined with the other half's through shared memory.
+  // With 4-row tiles a row's maximum is combined with the other half's
+  // through shared memory.
   float inv_scale;
   {
-    const int row = row0 + wq;
+    const int row = row0 + rr;
     const bool valid = row < d.rows;
     float2 x[KH];
     float mx = 0.f;
@@ -405,7 +422,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
       float u[KH];
 #pragma unroll
       for (int i = 0; i < KH; ++i) {
-        const int n = kR2 * (KH * hh + i) + l;
+        const int n = kR2 * (n1w + i) + l;
         const bool in = valid && n < n0;
         x[i] = in ? __ldg(d.cin + n) : make_float2(0.f, 0.f);
         u[i] = in ? ld_src<COHERENT>(static_cast<const float*>(d.src) + (size_t)row * d.src_ld + n) : 0.f;
@@ -419,7 +436,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
     } else {
 #pragma unroll
       for (int i = 0; i < KH; ++i) {
-        const int n = kR2 * (KH * hh + i) + l;
+        const int n = kR2 * (n1w + i) + l;
         float2 v = make_float2(0.f, 0.f);
         if (valid && n < n0) {
           const float2 c = __ldg(d.cin + n);
@@ -436,7 +453,7 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
     // the previous tile's tensor stores have read the buffer (a release above waited for all of them)
     if (tq == kStoreTq && !signal) umma::bulk_wait_read();
     group_bar(g);
-    mx = fmaxf(mx, rowmax[gw ^ 4]);
+    if constexpr (kHalfN1) mx = fmaxf(mx, rowmax[gw ^ 4]);
     int e = 0;
     if (mx > 0.f) frexpf(mx, &e);
     const float s = ldexpf(1.f, -e);  // max * s in [0.5, 1)
@@ -450,8 +467,8 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
         re[j] = x[8 * c + j].x * s;
         im[j] = x[8 * c + j].y * s;
       }
-      store8<L, PREC>(op, kmaj_off(m, KH * hh + 8 * c), re);
-      store8<L, PREC>(op, kmaj_off(m, KA + KH * hh + 8 * c), im);
+      store8<L, PREC>(op + pa * S::A_PROD_BYTES, kmaj_off(m, n1w + 8 * c), re);
+      store8<L, PREC>(op + pa * S::A_PROD_BYTES, kmaj_off(m, KA + n1w + 8 * c), im);
     }
   }
   if (!consts_ready) {  // first tile: every thread sees the constant image before using it
@@ -467,24 +484,29 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   publish();
   if (tq == 0) {
     umma::fence_after_sync();
-    gemm<SPLIT, false>(tm, s_op, s_lo, S::A_K, s_ba, s_ba + LO, S::A_N, S::A_K / 16,
-                       umma::idesc_f16(128, S::A_N, BF, false, false));
+#pragma unroll
+    for (int a = 0; a < S::QA; ++a)
+      gemm<SPLIT, false>(tm + 64 * a, s_op + a * S::A_PROD_BYTES, s_lo + a * S::A_PROD_BYTES, S::A_K, s_ba,
+                         s_ba + LO, S::A_N, S::A_K / 16, umma::idesc_f16(128, S::A_N, BF, false, false));
     umma::commit(bars + g);
   }
   await();
   if (!ok) return false;
 
   // ---- twiddle W_L^{n2 k1}; stage-B operand rows (r', k1), K = n2 (MN-major).
-  // Lane (r = wq, n2 = l); warp half hh takes k1 in [R1/2 hh, R1/2 hh + R1/2).
+  // Lane (r = rr, n2 = l) of first-stage product pa; with 4-row tiles warp half hh
+  // takes k1 in [R1/2 hh, R1/2 hh + R1/2), with 8-row tiles every k1.
   {
-    const int q = wq / S::RP, rp = wq % S::RP;  // this warp's row r = wq: product q, row rp in it
+    constexpr int JW = kHalfN1 ? R1 / 32 : R1 / 16;  // 16-column chunks per warp
+    const int q = rr / S::RP, rp = rr % S::RP;        // middle-stage product and row in it
     unsigned char* opq = op + q * 128 * S::B_K * 2;
+    const uint32_t ta = tm + 64 * pa;
 #pragma unroll
-    for (int jj = 0; jj < R1 / 32; ++jj) {
-      const int j = (R1 / 32) * hh + jj;
+    for (int jj = 0; jj < JW; ++jj) {
+      const int j = (kHalfN1 ? JW * hh : 0) + jj;
       float re[16], im[16];
-      umma::tmem_ld16(tm + lanes + 16 * j, re);
-      umma::tmem_ld16(tm + lanes + R1 + 16 * j, im);
+      umma::tmem_ld16(ta + lanes + 16 * j, re);
+      umma::tmem_ld16(ta + lanes + R1 + 16 * j, im);
       umma::tmem_wait_ld();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -581,24 +603,29 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
           yr[i] = y.x;
           yi[i] = y.y;
         }
-        const int m = kR2 * r + 16 * c + 8 * h;
-        store8<L, PREC>(op, mnmaj_off(m, k1, S::H_K), yr);
-        store8<L, PREC>(op, mnmaj_off(m, R1 + k1, S::H_K), yi);
+        // row r of the tile sits in last-stage product r / 4 (one product for 4-row tiles)
+        unsigned char* const oph = op + (r / 4) * S::AH_PROD_BYTES;
+        const int m = kR2 * (r % 4) + 16 * c + 8 * h;
+        store8<L, PREC>(oph, mnmaj_off(m, k1, S::H_K), yr);
+        store8<L, PREC>(oph, mnmaj_off(m, R1 + k1, S::H_K), yi);
       }
     }
   }
   publish();
   if (tq == 0) {
     umma::fence_after_sync();
-    gemm<SPLIT, true>(tm, s_op, s_lo, S::H_K, s_bh, s_bh + LO, S::H_N, S::H_K / 16,
-                      umma::idesc_f16(128, S::H_N, BF, true, false));
+#pragma unroll
+    for (int a = 0; a < S::QA; ++a)
+      gemm<SPLIT, true>(tm + 64 * a, s_op + a * S::AH_PROD_BYTES, s_lo + a * S::AH_PROD_BYTES, S::H_K, s_bh,
+                        s_bh + LO, S::H_N, S::H_K / 16, umma::idesc_f16(128, S::H_N, BF, true, false));
     umma::commit(bars + g);
   }
-  // the output-chirp loads overlap the product: this thread's n1 in [NH hh, NH hh + NH)
+  // the output-chirp loads overlap the product: this thread's n1 in [n1w', n1w' + NH)
+  const int n1o = kHalfN1 ? NH * hh : 0;
   float2 co[NH];
 #pragma unroll
   for (int i = 0; i < NH; ++i) {
-    const int n = kR2 * (NH * hh + i) + l;
+    const int n = kR2 * (n1o + i) + l;
     co[i] = n < n1 ? __ldg(d.cout + n) : make_float2(0.f, 0.f);
   }
   await();
@@ -609,16 +636,17 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
     // the three 1/sqrt(L) stage scales (the output chirp carries the transform's 1/L)
     const float sc = inv_scale * (float)L * sqrtf((float)L);
     float2* stage = reinterpret_cast<float2*>(op);
+    const uint32_t ta = tm + 64 * pa;  // this warp's last-stage product
 #pragma unroll
     for (int c = 0; c < NH / 8; ++c) {
       float re[8], im[8];
-      umma::tmem_ld8(tm + lanes + NH * hh + 8 * c, re);
-      umma::tmem_ld8(tm + lanes + NA + NH * hh + 8 * c, im);
+      umma::tmem_ld8(ta + lanes + n1o + 8 * c, re);
+      umma::tmem_ld8(ta + lanes + NA + n1o + 8 * c, im);
       umma::tmem_wait_ld();
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int n = kR2 * (NH * hh + 8 * c + i) + l;
-        if (n < n1) stage[stage_idx(n, wq)] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[8 * c + i]);
+        const int n = kR2 * (n1o + 8 * c + i) + l;
+        if (n < n1) stage[stage_idx<TR>(n, rr)] = cmul(make_float2(re[i] * sc, -im[i] * sc), co[8 * c + i]);
       }
     }
   }
@@ -627,25 +655,25 @@ __device__ __forceinline__ bool tile_t5(GroupCtx<L, PREC>& ctx, const unsigned c
   group_bar(g);
   // ---- transposed store: output n of row r to dst[n * dst_ld + row0 + r]
   if (out_map) {
-    // tensor stores of kOutBoxN outputs x kRows rows, clipped to the pass's rows and n1; they
+    // tensor stores of kOutBoxN outputs x TR rows, clipped to the pass's rows and n1; they
     // complete in the background, and the buffer is next written after the wait above
     if (tq == kStoreTq) {
       for (int j = 0; j * kOutBoxN < n1; ++j)
-        umma::tma_store_2d(out_map, op + j * kOutBoxN * kRows * 8, 2 * row0, j * kOutBoxN);
+        umma::tma_store_2d(out_map, op + j * kOutBoxN * TR * 8, 2 * row0, j * kOutBoxN);
       umma::bulk_commit();
     }
   } else {
     const float2* stage = reinterpret_cast<const float2*>(op);
-    const int rows_here = min(kRows, d.rows - row0);
+    const int rows_here = min(TR, d.rows - row0);
     float2* const dst = d.dst;
     float* const inten = d.inten;
     float* const phase = d.phase;
     const size_t ld = (size_t)d.dst_ld;
     const bool acc = d.accumulate != 0;
-    for (int i = tq; i < n1 * kRows; i += kGroupThreads) {
-      const int n = i >> 2, r = i & 3;
+    for (int i = tq; i < n1 * TR; i += kGroupThreads) {
+      const int n = i / TR, r = i % TR;
       if (r < rows_here) {
-        const float2 u = stage[stage_idx(n, r)];
+        const float2 u = stage[stage_idx<TR>(n, r)];
         const size_t o = (size_t)n * ld + row0 + r;
         if constexpr (KIND != PASS_Y) {
           dst[o] = u;
@@ -674,7 +702,7 @@ k_pass_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a) {
        tile += gridDim.x * kGroups) {
     int p = 0;
     while (tile >= a.tile_off[p + 1]) ++p;
-    if (!tile_t5<L, KIND, PREC, false>(c, sm, b.d[p], (tile - a.tile_off[p]) * kRows,
+    if (!tile_t5<L, KIND, PREC, false>(c, sm, b.d[p], (tile - a.tile_off[p]) * Shape<L>::TR,
                                        a.tma_store[p] ? &a.out_map[p] : nullptr, a.err))
       break;
   }
@@ -721,7 +749,7 @@ k_views_t5(const __grid_constant__ PassBatch b, const __grid_constant__ Args a, 
     if (tile >= a.total_tiles) break;
     int p = 0;
     while (tile >= a.tile_off[p + 1]) ++p;
-    const int row0 = (tile - a.tile_off[p]) * kRows;
+    const int row0 = (tile - a.tile_off[p]) * Shape<L>::TR;
     const CUtensorMap* om = a.tma_store[p] ? &a.out_map[p] : nullptr;
     if (p < f.nx) {
       int* const prev = pending;  // released inside the tile, once its input loads are in flight
@@ -842,7 +870,11 @@ void dft_operand(int R, int kin, int nout, bool bf16, uint16_t* hi, uint16_t* lo
 
 }  // namespace t5
 
-bool t5_length_supported(int L) { return L == 1024 || L == 2048; }
+bool t5_length_supported(int L) { return L == 512 || L == 1024 || L == 2048; }
+
+namespace {
+int t5_tile_rows(int L) { return L == 512 ? t5::Shape<512>::TR : 4; }
+}  // namespace
 bool t5_precision(int prec) {
   return prec == SF_PREC_FP16TC || prec == SF_PREC_BF16TC || prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
 }
@@ -871,18 +903,21 @@ void build_consts_t(int prec, unsigned char* base) {
 
 size_t t5_const_bytes(int L, int prec) {
   const bool split = prec == SF_PREC_FP16X3TC || prec == SF_PREC_BF16X3TC;
+  if (L == 512) return (size_t)t5::Shape<512>::const_bytes(split);
   if (L == 1024) return (size_t)t5::Shape<1024>::const_bytes(split);
   if (L == 2048) return (size_t)t5::Shape<2048>::const_bytes(split);
   return 0;
 }
 
 void t5_build_consts(int L, int prec, void* host) {
+  if (L == 512) build_consts_t<512>(prec, static_cast<unsigned char*>(host));
   if (L == 1024) build_consts_t<1024>(prec, static_cast<unsigned char*>(host));
   if (L == 2048) build_consts_t<2048>(prec, static_cast<unsigned char*>(host));
 }
 
 cudaError_t launch_hnat(int L, const float2* Hreg, float2* Hn, cudaStream_t s) {
-  if (L == 1024) t5::k_hnat<1024><<<1, 1024 / kE, 0, s>>>(Hreg, Hn);
+  if (L == 512) t5::k_hnat<512><<<1, 512 / kE, 0, s>>>(Hreg, Hn);
+  else if (L == 1024) t5::k_hnat<1024><<<1, 1024 / kE, 0, s>>>(Hreg, Hn);
   else if (L == 2048) t5::k_hnat<2048><<<1, 2048 / kE, 0, s>>>(Hreg, Hn);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -895,11 +930,12 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
   a.consts = static_cast<const uint4*>(consts);
   a.err = err;
   a.tile_off[0] = 0;
-  for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + t5::kRows - 1) / t5::kRows;
+  const int TR = t5_tile_rows(L);
+  for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + TR - 1) / TR;
   for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
   a.total_tiles = a.tile_off[b.count];
   for (int k = 0; k < b.count; ++k)
-    a.tma_store[k] = output_tensor_map(kind, b.d[k], t5::kRows, &a.out_map[k], true) ? 1 : 0;
+    a.tma_store[k] = output_tensor_map(kind, b.d[k], TR, &a.out_map[k], TR == 4) ? 1 : 0;
   if (a.total_tiles == 0) return cudaSuccess;
   const int grid = std::min(sms, a.total_tiles);  // every SM that can have a tile gets one
 #define SF_T5_PREC_CASES(LL)                                                                  \
@@ -909,6 +945,7 @@ cudaError_t launch_pass_t5(int L, int prec, PassKind kind, const PassBatch& b, c
     case SF_PREC_FP16X3TC: return t5::launch_t<LL, SF_PREC_FP16X3TC>(kind, b, a, grid, s);     \
     case SF_PREC_BF16X3TC: return t5::launch_t<LL, SF_PREC_BF16X3TC>(kind, b, a, grid, s);     \
   }
+  if (L == 512) SF_T5_PREC_CASES(512)
   if (L == 1024) SF_T5_PREC_CASES(1024)
   if (L == 2048) SF_T5_PREC_CASES(2048)
 #undef SF_T5_PREC_CASES
@@ -922,11 +959,12 @@ cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b
   a.consts = static_cast<const uint4*>(consts);
   a.err = err;
   a.tile_off[0] = 0;
-  for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + t5::kRows - 1) / t5::kRows;
+  const int TR = t5_tile_rows(L);
+  for (int k = 0; k < b.count; ++k) a.tile_off[k + 1] = a.tile_off[k] + (b.d[k].rows + TR - 1) / TR;
   for (int k = b.count; k < kMaxPassBatch; ++k) a.tile_off[k + 1] = a.tile_off[k];
   a.total_tiles = a.tile_off[b.count];
   for (int k = 0; k < b.count; ++k)
-    a.tma_store[k] = output_tensor_map(k < nx ? kind_x : PASS_Y, b.d[k], t5::kRows, &a.out_map[k], true) ? 1 : 0;
+    a.tma_store[k] = output_tensor_map(k < nx ? kind_x : PASS_Y, b.d[k], TR, &a.out_map[k], TR == 4) ? 1 : 0;
   if (a.total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(int) * (1 + nx), s);
   if (e != cudaSuccess) return e;
@@ -938,11 +976,13 @@ cudaError_t launch_views_t5(int L, int prec, PassKind kind_x, const PassBatch& b
   // FP16 / BF16 only (the x3 precisions run one launch per pass)
   switch (prec) {
     case SF_PREC_FP16TC:
-      return L == 1024 ? t5::launch_fused_t<1024, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s)
-                       : t5::launch_fused_t<2048, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s);
+      return L == 512    ? t5::launch_fused_t<512, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s)
+             : L == 1024 ? t5::launch_fused_t<1024, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s)
+                         : t5::launch_fused_t<2048, SF_PREC_FP16TC>(kind_x, b, a, f, grid, s);
     case SF_PREC_BF16TC:
-      return L == 1024 ? t5::launch_fused_t<1024, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s)
-                       : t5::launch_fused_t<2048, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s);
+      return L == 512    ? t5::launch_fused_t<512, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s)
+             : L == 1024 ? t5::launch_fused_t<1024, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s)
+                         : t5::launch_fused_t<2048, SF_PREC_BF16TC>(kind_x, b, a, f, grid, s);
   }
   return cudaErrorInvalidValue;
 }

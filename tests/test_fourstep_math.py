@@ -8,7 +8,7 @@ conj(DFT(conj(.))), and every DFT matrix carries a 1/sqrt(R) scale.  These
 tests restate that formulation in float64 -- with the operand packing of the
 real products ([Re | Im] against [[Fr, Fi], [-Fi, Fr]]) and the row / lane
 order the kernel uses -- and check it against the circular convolution of
-numpy's FFT, for both built lengths.  They also check the position-to-
+numpy's FFT, for the three built lengths.  They also check the position-to-
 frequency map by which the kernel spectrum is put in natural order (the FP32
 network's radix-16 decimation-in-frequency digits), against a stage-by-stage
 emulation of such a network.  They test the design's index mathematics, not
@@ -82,10 +82,10 @@ def four_step_rows(X, Hn, L):
     return out * np.sqrt(L) / L
 
 
-@pytest.mark.parametrize("L", [1024, 2048])
+@pytest.mark.parametrize("L", [512, 1024, 2048])
 def test_four_step_products_equal_the_circular_convolution(L):
     rng = np.random.default_rng(L)
-    rows = 4
+    rows = 8 if L == 512 else 4  # the kernel's tile rows
     X = np.zeros((rows, L), complex)
     X[:, :L // 2] = rng.standard_normal((rows, L // 2)) + 1j * rng.standard_normal((rows, L // 2))
     h = np.exp(1j * np.pi * rng.uniform(0, 1e-3) * (np.arange(L) - L // 2) ** 2)  # any kernel
@@ -96,7 +96,7 @@ def test_four_step_products_equal_the_circular_convolution(L):
     assert err < 1e-12, err
 
 
-@pytest.mark.parametrize("L", [1024, 2048])
+@pytest.mark.parametrize("L", [512, 1024, 2048])
 def test_four_step_pruned_inputs_and_outputs(L):
     """Only n1 < R1 / 2 enters and leaves: inputs beyond L / 2 are ignored (they are the zero padding),
     and the kept outputs are exactly the first L / 2 of the circular convolution."""

@@ -1,9 +1,10 @@
 """The tcgen05 row pass (four-step DFT products on the tensor cores) against the FP64 oracle.
 
 Axes of FFT length 2048 (64 x 32) with input and output lengths of at most
-1024 (the paper's 1024 -> 1024 views with 2N padding), and of FFT length
-1024 (32 x 32) with lengths of at most 512, run on this pass in every
-reduced precision.  Bars, per view, relative L2 against the oracle's complex
+1024 (the paper's 1024 -> 1024 views with 2N padding), of FFT length 1024
+(32 x 32) with lengths of at most 512, and of FFT length 512 (16 x 32, tiles
+of 8 rows) with lengths of at most 256, run on this pass in every reduced
+precision.  Bars, per view, relative L2 against the oracle's complex
 field over every pixel:
 
 * FP16TC, and BF16X3TC (BF16 hi + lo, three products): 2e-3, the
@@ -146,5 +147,22 @@ def test_length_1024_views_every_pixel(P, prec):
     got, _ = run(P, views, holo, prec)
     errs = [rel_l2(g, oracle.forward(holo, v)) for g, v in zip(got, views)]
     print(f"{NAMES[prec]} L=1024: per-view rel-L2 " + ", ".join(f"{e:.3e}" for e in errs))
+    check(prec, errs)
+
+
+@pytest.mark.parametrize("prec", [FP16, FP16X3, BF16X3, BF16], ids=lambda p: NAMES[p])
+def test_length_512_views_every_pixel(P, prec):
+    """FFT length 512 on both axes (the 16 x 32 split, tiles of 8 rows with two products in the first
+    and last stage): a 256 x 250 hologram (a partial last tile on the x pass) into four views of 256^2,
+    250 x 255, 129 x 100 and 256 x 32, every pixel against the oracle."""
+    holo = synth.gabor_hologram(256, seed=2560)[:250]
+    views = [view(WAVELENGTH, z, PITCH, p1, o1=o1, n0=(256, 250), n1=n1)
+             for z, p1, o1, n1 in ((0.02, 2.0e-6, (5e-5, -2e-5), (256, 256)),
+                                   (-0.04, 4.0e-6, (-1e-4, 5e-5), (250, 255)),
+                                   (0.06, 1.5e-6, (1e-5, 0.0), (129, 100)),
+                                   (0.09, 4.65e-6, (0.0, 1e-4), (256, 32)))]
+    got, _ = run(P, views, holo, prec)
+    errs = [rel_l2(g, oracle.forward(holo, v)) for g, v in zip(got, views)]
+    print(f"{NAMES[prec]} L=512: per-view rel-L2 " + ", ".join(f"{e:.3e}" for e in errs))
     check(prec, errs)
 
