@@ -58,10 +58,10 @@ extern "C" {
 #define SF_PREC_BF16TC 2   /* same with BF16 operands */
 #define SF_PREC_FP16X3TC 3 /* FP16 operands split into hi + lo parts, three products per stage */
 #define SF_PREC_BF16X3TC 4 /* BF16 operands split into hi + lo parts, three products per stage */
-/* Tensor-core precisions.  An axis of FFT length 2048 or 1024 whose input and
- * output lengths are at most half of it (the paper's 2N padding, e.g.
- * 1024 -> 1024 or 512 -> 512) runs the four-step pass on tcgen05 (2048 =
- * 64 x 32, 1024 = 32 x 32: two DFT matrix products each way, operands in
+/* Tensor-core precisions.  An axis of FFT length 2048, 1024 or 512 whose
+ * input and output lengths are at most half of it (the paper's 2N padding,
+ * e.g. 1024 -> 1024, 512 -> 512, 256 -> 256) runs the four-step pass on
+ * tcgen05 (64 x 32, 32 x 32, 16 x 32: two DFT matrix products each way, operands in
  * shared memory, FP32 accumulators in tensor memory, one CTA per SM; on
  * FP16TC / BF16TC plans of two to eight views whose axes all share one such
  * length, execute runs both passes in one launch); other axes of length 2048

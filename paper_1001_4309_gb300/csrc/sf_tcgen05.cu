@@ -5,7 +5,7 @@
 // spectrum applied in FP32 between them.
 //
 // Four-step split of the FFT of length L = R1 * R2 (R2 = 32, R1 = L / 32;
-// built for L = 2048 and 1024):
+// built for L = 2048, 1024 and 512):
 //   n = R2 n1 + n2,  k = k1 + R1 k2
 //   X[k1 + R1 k2] = sum_n2 W_R2^{n2 k2} W_L^{n2 k1} sum_n1 x[R2 n1 + n2] W_R1^{n1 k1}
 // and the inverse in the mirrored order, each inverse DFT taken as
